@@ -1,0 +1,487 @@
+/*
+ * gvx CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * This file is the slow, obviously correct reference that the GPU library is checked against.
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header, constant or helper with the CUDA library under
+ * paper_2312_02756_gb300/csrc, and it never calls it.
+ *
+ * Two tiers:
+ *   O1 ("definition", orc_*_def): each operation written out exactly as it is defined, evaluated
+ *      in IEEE binary128 (long double on aarch64, __float128 + libquadmath on x86_64) and rounded
+ *      to double once at the end.  binary128 is used because the plain definition
+ *      m = sqrt(E^2 - |p|^2) loses up to log10(E^2/m^2) digits to cancellation; with 113 bits the
+ *      rounding error stays far below the 1e-12 relative gate even at E^2/m^2 ~ 1e16.
+ *   O2 ("fp64", orc_*_fp64): the same quantities from different, cancellation-free identities in
+ *      plain double.  Fast enough to run over whole inputs on the host; it is also the timed CPU
+ *      baseline.  O1 and O2 use different formulas, so their agreement pins both.
+ *
+ * Paper references (GenVectorX, arXiv 2312.02756):
+ *   Sec. 3.1 and Fig. 1: InvariantMasses -- two arrays of Lorentz vectors given in any 4-D
+ *     coordinate system; per index the two vectors are added and mass() of the sum is stored.
+ *   Sec. 3.1: ApplyBoost -- a 4-D Lorentz transformation held as a 4x4 matrix and applied to every
+ *     vector of an array.
+ *   Sec. 2.1: vectors are templated on the coordinate system (here PtEtaPhiM in, PxPyPzE out).
+ *   Sec. 5 (future work, RDataFrame analyses): per-event combinatorics -- the jagged form.
+ * The paper prints no formula for the coordinate conversion or the boost matrix; the standard
+ * relations used here (and their readings) are listed beside each function.
+ *
+ * Layouts: every 4-vector array is row-major n x 4 doubles.  PtEtaPhiM rows are (pt, eta, phi, m);
+ * PxPyPzE rows are (px, py, pz, E).  Velocities are rows of 3 doubles (bx, by, bz).
+ *
+ * Parity pins: every function here is pinned by the CPU tests (closed forms, invariants, special
+ * cases, finite differences, O1/O2 cross-agreement); none is "parity unpinned".
+ */
+#include <float.h>
+#include <math.h>
+#include <pthread.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#if LDBL_MANT_DIG == 113
+typedef long double qreal;
+#define Q_SIN sinl
+#define Q_COS cosl
+#define Q_SINH sinhl
+#define Q_COSH coshl
+#define Q_SQRT sqrtl
+#define Q_BITS 113
+#elif defined(__SIZEOF_FLOAT128__)
+#include <quadmath.h>
+typedef __float128 qreal;
+#define Q_SIN sinq
+#define Q_COS cosq
+#define Q_SINH sinhq
+#define Q_COSH coshq
+#define Q_SQRT sqrtq
+#define Q_BITS FLT128_MANT_DIG
+#else
+#error "the definition oracle needs IEEE binary128 arithmetic"
+#endif
+
+/* Mantissa bits of the extended type (113 for binary128); the tests assert it. */
+int orc_precision_bits(void) { return Q_BITS; }
+
+/* ------------------------------------------------------------------------------------------ */
+/* A tiny thread fan-out: [0, n) is split into nthreads contiguous ranges.                     */
+
+typedef void (*range_fn)(void *ctx, int64_t lo, int64_t hi);
+typedef struct {
+  range_fn fn;
+  void *ctx;
+  int64_t lo, hi;
+} range_job;
+
+static void *range_job_run(void *p) {
+  range_job *j = (range_job *)p;
+  j->fn(j->ctx, j->lo, j->hi);
+  return NULL;
+}
+
+static void run_ranges(range_fn fn, void *ctx, int64_t n, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if (nthreads == 1 || n < 2 * nthreads) {
+    fn(ctx, 0, n);
+    return;
+  }
+  pthread_t tid[256];
+  range_job job[256];
+  int started[256];
+  for (int t = 0; t < nthreads; t++) {
+    job[t].fn = fn;
+    job[t].ctx = ctx;
+    job[t].lo = n * t / nthreads;
+    job[t].hi = n * (t + 1) / nthreads;
+    started[t] = pthread_create(&tid[t], NULL, range_job_run, &job[t]) == 0;
+    if (!started[t]) range_job_run(&job[t]);
+  }
+  for (int t = 0; t < nthreads; t++)
+    if (started[t]) pthread_join(tid[t], NULL);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* O1: definitions in binary128                                                               */
+
+/* PtEtaPhiM -> PxPyPzE (Sec. 2.1 coordinate systems; the conversion that v1[id] + v2[id] in
+ * Fig. 1 performs before adding):
+ *   px = pt cos(phi), py = pt sin(phi), pz = pt sinh(eta), E = sqrt(px^2 + py^2 + pz^2 + m^2).
+ * Reading: the stored m enters only through m^2 (its sign is ignored). */
+static void leg_to_cartesian_q(const double *leg, qreal out[4]) {
+  qreal pt = leg[0], eta = leg[1], phi = leg[2], m = leg[3];
+  qreal px = pt * Q_COS(phi);
+  qreal py = pt * Q_SIN(phi);
+  qreal pz = pt * Q_SINH(eta);
+  out[0] = px;
+  out[1] = py;
+  out[2] = pz;
+  out[3] = Q_SQRT(px * px + py * py + pz * pz + m * m);
+}
+
+/* mass() of a PxPyPzE vector: sqrt(E^2 - |p|^2).  A negative E^2 - |p|^2 (possible only through
+ * rounding here) returns -sqrt(-(E^2 - |p|^2)), GenVector's convention for spacelike vectors. */
+static qreal lv_mass_q(const qreal v[4]) {
+  qreal m2 = v[3] * v[3] - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  return m2 >= 0 ? Q_SQRT(m2) : -Q_SQRT(-m2);
+}
+
+static double pair_mass_def(const double *a, const double *b) {
+  qreal va[4], vb[4], w[4];
+  leg_to_cartesian_q(a, va);
+  leg_to_cartesian_q(b, vb);
+  for (int k = 0; k < 4; k++) w[k] = va[k] + vb[k];
+  return (double)lv_mass_q(w);
+}
+
+typedef struct {
+  const double *a, *b;
+  double *m;
+} mass_ctx;
+
+static void mass_def_range(void *p, int64_t lo, int64_t hi) {
+  mass_ctx *c = (mass_ctx *)p;
+  for (int64_t i = lo; i < hi; i++) c->m[i] = pair_mass_def(c->a + 4 * i, c->b + 4 * i);
+}
+
+/* Invariant mass of each pair (Sec. 3.1, Fig. 1): m[i] = mass(v1[i] + v2[i]). */
+void orc_mass_def(const double *a, const double *b, int64_t n, double *m, int nthreads) {
+  mass_ctx c = {a, b, m};
+  run_ranges(mass_def_range, &c, n, nthreads);
+}
+
+/* The same definition evaluated in plain double: no tier uses it as a reference; the tests
+ * report its error to show why O1 runs in binary128. */
+void orc_mass_naive_fp64(const double *a, const double *b, int64_t n, double *m) {
+  for (int64_t i = 0; i < n; i++) {
+    double w[4] = {0, 0, 0, 0};
+    const double *legs[2] = {a + 4 * i, b + 4 * i};
+    for (int l = 0; l < 2; l++) {
+      double pt = legs[l][0], eta = legs[l][1], phi = legs[l][2], mm = legs[l][3];
+      double px = pt * cos(phi), py = pt * sin(phi), pz = pt * sinh(eta);
+      w[0] += px;
+      w[1] += py;
+      w[2] += pz;
+      w[3] += sqrt(px * px + py * py + pz * pz + mm * mm);
+    }
+    double m2 = w[3] * w[3] - (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    m[i] = m2 >= 0 ? sqrt(m2) : -sqrt(-m2);
+  }
+}
+
+/* Gradient of the pair mass by the chain rule through the definition:
+ *   dm/d(Px,Py,Pz,E) of the summed vector = (-Px, -Py, -Pz, E) / m,
+ *   times the Jacobian of each leg's (px,py,pz,E) with respect to (pt,eta,phi,m):
+ *     px: ( cos phi,      0,           -pt sin phi, 0    )
+ *     py: ( sin phi,      0,            pt cos phi, 0    )
+ *     pz: ( sinh eta,     pt cosh eta,  0,          0    )
+ *     E : ((px cos phi + py sin phi + pz sinh eta)/E_i, pz pt cosh eta / E_i,
+ *          (-px pt sin phi + py pt cos phi)/E_i,  m/E_i )
+ * Readings: where m <= 0 the gradient is zero (m is not differentiable at 0); a leg with E_i = 0
+ * contributes zero through its E row. */
+static void pair_mass_grad_def(const double *a, const double *b, double gm, double *ga,
+                               double *gb) {
+  qreal v[2][4], w[4];
+  leg_to_cartesian_q(a, v[0]);
+  leg_to_cartesian_q(b, v[1]);
+  for (int k = 0; k < 4; k++) w[k] = v[0][k] + v[1][k];
+  qreal m = lv_mass_q(w);
+  const double *legs[2] = {a, b};
+  double *outs[2] = {ga, gb};
+  if (!(m > 0)) {
+    for (int l = 0; l < 2; l++)
+      for (int k = 0; k < 4; k++) outs[l][k] = 0.0;
+    return;
+  }
+  qreal dmdv[4] = {-w[0] / m, -w[1] / m, -w[2] / m, w[3] / m};
+  for (int l = 0; l < 2; l++) {
+    qreal pt = legs[l][0], eta = legs[l][1], phi = legs[l][2], mm = legs[l][3];
+    qreal c = Q_COS(phi), s = Q_SIN(phi), sh = Q_SINH(eta), ch = Q_COSH(eta);
+    qreal px = v[l][0], py = v[l][1], pz = v[l][2], e = v[l][3];
+    qreal J[4][4] = {
+        {c, 0, -pt * s, 0},
+        {s, 0, pt * c, 0},
+        {sh, pt * ch, 0, 0},
+        {0, 0, 0, 0},
+    };
+    if (e > 0) {
+      J[3][0] = (px * c + py * s + pz * sh) / e;
+      J[3][1] = pz * pt * ch / e;
+      J[3][2] = (-px * pt * s + py * pt * c) / e;
+      J[3][3] = mm / e;
+    }
+    for (int k = 0; k < 4; k++) {
+      qreal acc = 0;
+      for (int r = 0; r < 4; r++) acc += dmdv[r] * J[r][k];
+      outs[l][k] = (double)(acc * (qreal)gm);
+    }
+  }
+}
+
+typedef struct {
+  const double *a, *b, *gm;
+  double *ga, *gb;
+} mass_grad_ctx;
+
+static void mass_grad_def_range(void *p, int64_t lo, int64_t hi) {
+  mass_grad_ctx *c = (mass_grad_ctx *)p;
+  for (int64_t i = lo; i < hi; i++)
+    pair_mass_grad_def(c->a + 4 * i, c->b + 4 * i, c->gm[i], c->ga + 4 * i, c->gb + 4 * i);
+}
+
+/* ga[i], gb[i] = gm[i] * d m[i] / d(pt, eta, phi, m) of leg a and leg b. */
+void orc_mass_grad_def(const double *a, const double *b, const double *gm, int64_t n, double *ga,
+                       double *gb, int nthreads) {
+  mass_grad_ctx c = {a, b, gm, ga, gb};
+  run_ranges(mass_grad_def_range, &c, n, nthreads);
+}
+
+/* The boost matrix (Sec. 3.1: ApplyBoost applies a 4x4 Lorentz matrix).  Index order is
+ * (x, y, z, t) to match PxPyPzE.  For a velocity beta with b2 = |beta|^2 < 1:
+ *   gamma = 1 / sqrt(1 - b2)
+ *   L[t][t] = gamma,  L[i][t] = L[t][i] = gamma beta_i,
+ *   L[i][j] = delta_ij + (gamma - 1) beta_i beta_j / b2.
+ * Readings: "boost by +beta" (a vector at rest acquires velocity +beta); beta = 0 gives the
+ * identity (the limit of the formula); |beta| >= 1 gives NaN everywhere. */
+static int boost_matrix_q(const double *beta, qreal L[4][4]) {
+  qreal bx = beta[0], by = beta[1], bz = beta[2];
+  qreal b[3] = {bx, by, bz};
+  qreal b2 = bx * bx + by * by + bz * bz;
+  if (!(b2 < 1)) return 0;
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) L[i][j] = (i == j) ? 1 : 0;
+  if (b2 == 0) return 1;
+  qreal g = 1 / Q_SQRT(1 - b2);
+  qreal c = (g - 1) / b2;
+  for (int i = 0; i < 3; i++) {
+    for (int j = 0; j < 3; j++) L[i][j] += c * b[i] * b[j];
+    L[i][3] = g * b[i];
+    L[3][i] = g * b[i];
+  }
+  L[3][3] = g;
+  return 1;
+}
+
+/* Boost matrix rounded to double, row-major (x, y, z, t); NaN when |beta| >= 1. */
+void orc_boost_matrix_def(const double *beta, double *L16) {
+  qreal L[4][4];
+  int ok = boost_matrix_q(beta, L);
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) L16[4 * i + j] = ok ? (double)L[i][j] : NAN;
+}
+
+typedef struct {
+  const double *v, *beta;
+  int64_t stride;
+  double *out;
+} boost_ctx;
+
+static void boost_def_range(void *p, int64_t lo, int64_t hi) {
+  boost_ctx *c = (boost_ctx *)p;
+  for (int64_t i = lo; i < hi; i++) {
+    qreal L[4][4];
+    const double *vi = c->v + 4 * i;
+    double *oi = c->out + 4 * i;
+    if (!boost_matrix_q(c->beta + 3 * c->stride * i, L)) {
+      for (int k = 0; k < 4; k++) oi[k] = NAN;
+      continue;
+    }
+    for (int r = 0; r < 4; r++) {
+      qreal acc = 0;
+      for (int k = 0; k < 4; k++) acc += L[r][k] * (qreal)vi[k];
+      oi[r] = (double)acc;
+    }
+  }
+}
+
+/* out[i] = L(beta[i * stride]) v[i]; stride 1 gives each vector its own velocity, stride 0
+ * applies beta[0] to all (Sec. 3.1 ApplyBoost, one array of vectors). */
+void orc_boost_def(const double *v, const double *beta, int64_t beta_stride, int64_t n,
+                   double *out, int nthreads) {
+  boost_ctx c = {v, beta, beta_stride, out};
+  run_ranges(boost_def_range, &c, n, nthreads);
+}
+
+/* Gradient of the boost by the chain rule through the matrix definition.
+ *   grad_v = L^T gout  (L is symmetric, so L gout).
+ *   grad_beta_k = sum_ij gout_i (dL_ij / dbeta_k) v_j, with dgamma/dbeta_k = gamma^3 beta_k,
+ *   c = (gamma - 1)/b2, dc/dbeta_k = beta_k (gamma^3 b2 - 2 (gamma - 1)) / b2^2, and
+ *     dL_ij/dbeta_k = dc/dbeta_k beta_i beta_j + c (delta_ik beta_j + beta_i delta_jk),
+ *     dL_it/dbeta_k = dL_ti/dbeta_k = gamma^3 beta_k beta_i + gamma delta_ik,
+ *     dL_tt/dbeta_k = gamma^3 beta_k.
+ * At beta = 0 the limits c = 1/2 and dc/dbeta = 0 are used. */
+static void boost_grad_one(const double *vd, const double *betad, const double *gd, double *gv,
+                           qreal *gbeta) {
+  qreal L[4][4];
+  if (!boost_matrix_q(betad, L)) {
+    for (int k = 0; k < 4; k++) gv[k] = NAN;
+    for (int k = 0; k < 3; k++) gbeta[k] = NAN;
+    return;
+  }
+  qreal v[4], g[4], b[3];
+  for (int k = 0; k < 4; k++) {
+    v[k] = vd[k];
+    g[k] = gd[k];
+  }
+  for (int k = 0; k < 3; k++) b[k] = betad[k];
+  for (int j = 0; j < 4; j++) {
+    qreal acc = 0;
+    for (int i = 0; i < 4; i++) acc += L[i][j] * g[i];
+    gv[j] = (double)acc;
+  }
+  qreal b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  qreal gam = 1 / Q_SQRT(1 - b2);
+  qreal g3 = gam * gam * gam;
+  qreal c = 0.5, dcf = 0; /* dc/dbeta_k = dcf * beta_k */
+  if (b2 != 0) {
+    c = (gam - 1) / b2;
+    dcf = (g3 * b2 - 2 * (gam - 1)) / (b2 * b2);
+  }
+  for (int k = 0; k < 3; k++) {
+    qreal dL[4][4];
+    for (int i = 0; i < 3; i++) {
+      for (int j = 0; j < 3; j++)
+        dL[i][j] = dcf * b[k] * b[i] * b[j] + c * ((i == k ? b[j] : 0) + (j == k ? b[i] : 0));
+      dL[i][3] = g3 * b[k] * b[i] + (i == k ? gam : 0);
+      dL[3][i] = dL[i][3];
+    }
+    dL[3][3] = g3 * b[k];
+    qreal acc = 0;
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++) acc += g[i] * dL[i][j] * v[j];
+    gbeta[k] += acc;
+  }
+}
+
+/* gv[i] = d<gout[i], out[i]>/dv[i];  gbeta[i] = d<gout[i], out[i]>/dbeta[i] for stride 1; for
+ * stride 0 (one shared velocity) gbeta[0..2] is the sum over all i.  Single-threaded. */
+void orc_boost_grad_def(const double *v, const double *beta, int64_t beta_stride,
+                        const double *gout, int64_t n, double *gv, double *gbeta) {
+  qreal shared[3] = {0, 0, 0};
+  for (int64_t i = 0; i < n; i++) {
+    if (beta_stride) {
+      qreal gb[3] = {0, 0, 0};
+      boost_grad_one(v + 4 * i, beta + 3 * i, gout + 4 * i, gv + 4 * i, gb);
+      for (int k = 0; k < 3; k++) gbeta[3 * i + k] = (double)gb[k];
+    } else {
+      boost_grad_one(v + 4 * i, beta, gout + 4 * i, gv + 4 * i, shared);
+    }
+  }
+  if (!beta_stride)
+    for (int k = 0; k < 3; k++) gbeta[k] = (double)shared[k];
+}
+
+/* Jagged events (the per-event combinatorics of the RDataFrame analyses named as future work in
+ * Sec. 5).  Event e owns particles [off[e], off[e+1]) (PtEtaPhiM rows).  Outputs:
+ *   pair_off[e] = sum over earlier events of n(n-1)/2, pair_off[0] = 0 (n_events + 1 entries);
+ *   pair_m[pair_off[e] + k(i,j)] = mass(p_i + p_j) for i < j, packed row-major:
+ *     k(i,j) = i n - i(i+1)/2 + (j - i - 1);
+ *   sums[e] = sum of the event's particles as PxPyPzE.
+ * Returns 0, or -1 when the offsets are not a non-decreasing sequence starting at 0. */
+int orc_event_pairs_def(const double *p, const int64_t *off, int64_t n_events, int64_t *pair_off,
+                        double *pair_m, double *sums) {
+  if (n_events < 0 || off[0] != 0) return -1;
+  for (int64_t e = 0; e < n_events; e++)
+    if (off[e + 1] < off[e]) return -1;
+  pair_off[0] = 0;
+  for (int64_t e = 0; e < n_events; e++) {
+    int64_t n = off[e + 1] - off[e];
+    pair_off[e + 1] = pair_off[e] + n * (n - 1) / 2;
+  }
+  for (int64_t e = 0; e < n_events; e++) {
+    int64_t base = off[e], n = off[e + 1] - off[e];
+    int64_t k = pair_off[e];
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t j = i + 1; j < n; j++) pair_m[k++] = pair_mass_def(p + 4 * (base + i), p + 4 * (base + j));
+    qreal s[4] = {0, 0, 0, 0};
+    for (int64_t i = 0; i < n; i++) {
+      qreal v[4];
+      leg_to_cartesian_q(p + 4 * (base + i), v);
+      for (int c = 0; c < 4; c++) s[c] += v[c];
+    }
+    for (int c = 0; c < 4; c++) sums[4 * e + c] = (double)s[c];
+  }
+  return 0;
+}
+
+/* PtEtaPhiM -> PxPyPzE rounded to double (used by the tests to build boost inputs and
+ * multi-body checks). */
+void orc_to_cartesian_def(const double *p, int64_t n, double *out) {
+  for (int64_t i = 0; i < n; i++) {
+    qreal v[4];
+    leg_to_cartesian_q(p + 4 * i, v);
+    for (int c = 0; c < 4; c++) out[4 * i + c] = (double)v[c];
+  }
+}
+
+/* Mass of each PxPyPzE row, sqrt(E^2 - |p|^2) in binary128, rounded. */
+void orc_lv_mass_def(const double *v, int64_t n, double *m) {
+  for (int64_t i = 0; i < n; i++) {
+    qreal w[4] = {v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]};
+    m[i] = (double)lv_mass_q(w);
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* O2: cancellation-free identities in double                                                 */
+
+/* Pair mass from non-negative terms only.  With P_i = pt_i cosh(eta_i) = |p_i| and
+ * E_i = sqrt(P_i^2 + m_i^2):
+ *   m^2 = m_1^2 + m_2^2 + 2 (E_1 E_2 - p_1.p_2)
+ *   E_1 E_2 - P_1 P_2 = (m_1^2 P_2^2 + m_2^2 P_1^2 + m_1^2 m_2^2) / (E_1 E_2 + P_1 P_2)
+ *   P_1 P_2 - p_1.p_2 = pt_1 pt_2 (cosh(d_eta) - cos(d_phi))
+ *                     = 2 pt_1 pt_2 (sinh^2(d_eta/2) + sin^2(d_phi/2)).
+ * Every term is >= 0 for pt >= 0, so the relative error is a few ulps. */
+static double pair_mass_fp64(const double *a, const double *b) {
+  double pt1 = a[0], eta1 = a[1], phi1 = a[2], m1 = a[3];
+  double pt2 = b[0], eta2 = b[1], phi2 = b[2], m2 = b[3];
+  double P1 = pt1 * cosh(eta1), P2 = pt2 * cosh(eta2);
+  double mm1 = m1 * m1, mm2 = m2 * m2;
+  double E1 = sqrt(P1 * P1 + mm1), E2 = sqrt(P2 * P2 + mm2);
+  double se = sinh(0.5 * (eta1 - eta2)), sp = sin(0.5 * (phi1 - phi2));
+  double t_mass = 2.0 * (mm1 * P2 * P2 + mm2 * P1 * P1 + mm1 * mm2) / (E1 * E2 + P1 * P2);
+  double t_ang = 4.0 * pt1 * pt2 * (se * se + sp * sp);
+  double denom = E1 * E2 + P1 * P2;
+  if (denom == 0) t_mass = 0; /* both legs are zero vectors */
+  return sqrt(mm1 + mm2 + t_mass + t_ang);
+}
+
+static void mass_fp64_range(void *p, int64_t lo, int64_t hi) {
+  mass_ctx *c = (mass_ctx *)p;
+  for (int64_t i = lo; i < hi; i++) c->m[i] = pair_mass_fp64(c->a + 4 * i, c->b + 4 * i);
+}
+
+void orc_mass_fp64(const double *a, const double *b, int64_t n, double *m, int nthreads) {
+  mass_ctx c = {a, b, m};
+  run_ranges(mass_fp64_range, &c, n, nthreads);
+}
+
+/* Boost in vector form:
+ *   E' = gamma (E + beta.p),  p' = p + (k (beta.p) + gamma E) beta,  k = gamma^2 / (1 + gamma),
+ * using (gamma - 1)/b2 = gamma^2/(1 + gamma), which has no 0/0 at beta = 0. */
+static void boost_fp64_range(void *p, int64_t lo, int64_t hi) {
+  boost_ctx *c = (boost_ctx *)p;
+  for (int64_t i = lo; i < hi; i++) {
+    const double *vi = c->v + 4 * i, *bi = c->beta + 3 * c->stride * i;
+    double *oi = c->out + 4 * i;
+    double b2 = bi[0] * bi[0] + bi[1] * bi[1] + bi[2] * bi[2];
+    if (!(b2 < 1)) {
+      for (int k = 0; k < 4; k++) oi[k] = NAN;
+      continue;
+    }
+    double g = 1.0 / sqrt(1.0 - b2);
+    double k = g * g / (1.0 + g);
+    double bp = bi[0] * vi[0] + bi[1] * vi[1] + bi[2] * vi[2];
+    double f = k * bp + g * vi[3];
+    oi[0] = vi[0] + f * bi[0];
+    oi[1] = vi[1] + f * bi[1];
+    oi[2] = vi[2] + f * bi[2];
+    oi[3] = g * (vi[3] + bp);
+  }
+}
+
+void orc_boost_fp64(const double *v, const double *beta, int64_t beta_stride, int64_t n,
+                    double *out, int nthreads) {
+  boost_ctx c = {v, beta, beta_stride, out};
+  run_ranges(boost_fp64_range, &c, n, nthreads);
+}

@@ -1,0 +1,351 @@
+"""Pins for the CPU oracle: checks against facts the mathematics fixes, never against itself.
+
+Each test names what it pins.  A plausible slip in the oracle (a dropped term, a sign, a swapped
+sinh/cosh, a transposed matrix, a wrong packing index) fails at least one of them:
+  * hand-derived cases (tests/golden/hand_cases.txt),
+  * the massless closed form m^2 = 2 pt1 pt2 (cosh d_eta - cos d_phi) and its derivatives,
+  * invariance of the pair mass under rotations about z and boosts along z (eta shifts),
+  * agreement of the binary128 definition (O1) with the cancellation-free FP64 identity (O2),
+  * boost inverse, rest frame, collinear velocity addition, metric preservation, mass invariance,
+  * central finite differences for the gradients,
+  * integer prefix sums and pair enumeration for the jagged form.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import gvx_synth as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_cases.txt")
+
+
+def _golden_rows(kind):
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line.startswith(kind + " "):
+                rows.append([float(x) for x in line.split()[1:]])
+    assert rows
+    return rows
+
+
+def test_binary128(orc):
+    assert orc.precision_bits() == 113
+
+
+# ------------------------------------------------------------------------------------------ mass
+
+def test_mass_hand_cases(orc):
+    for r in _golden_rows("mass"):
+        a, b, want, rtol, atol = np.array(r[0:4]), np.array(r[4:8]), r[8], r[9], r[10]
+        for m in (orc.mass_def(a, b)[0], orc.mass_fp64(a, b)[0]):
+            assert abs(m - want) <= rtol * abs(want) + atol, (r, m)
+
+
+def _massless_pairs(n, seed):
+    g = syn.rng(seed)
+    a, b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    a[:, 3] = 0.0
+    b[:, 3] = 0.0
+    return a, b
+
+
+def test_mass_massless_closed_form(orc):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    a, b = _massless_pairs(400, 101)
+    got1, got2 = orc.mass_def(a, b), orc.mass_fp64(a, b)
+    for i in range(len(a)):
+        pt1, e1, f1, _ = (mp.mpf(x) for x in a[i])
+        pt2, e2, f2, _ = (mp.mpf(x) for x in b[i])
+        want = float(mp.sqrt(2 * pt1 * pt2 * (mp.cosh(e1 - e2) - mp.cos(f1 - f2))))
+        assert abs(got1[i] - want) <= 2.5e-16 * want
+        assert abs(got2[i] - want) <= 4e-15 * want
+
+
+def test_mass_symmetric_and_invariant(orc):
+    g = syn.rng(102)
+    a, b = syn.ptetaphim(g, 2000), syn.ptetaphim(g, 2000)
+    m = orc.mass_def(a, b)
+    assert np.array_equal(m, orc.mass_def(b, a))
+    # a rotation about z (phi -> phi + alpha) leaves m unchanged; for massless legs eta is the
+    # rapidity, so a boost along z (eta -> eta + y) does too.  The shifted inputs are rounded,
+    # so compare at the conditioning of the angular term.
+    a0, b0 = a.copy(), b.copy()
+    a0[:, 3] = 0.0
+    b0[:, 3] = 0.0
+    for (x, y), col, shift in (((a, b), 2, 0.7), ((a0, b0), 1, 0.3)):
+        m = orc.mass_def(x, y)
+        x2, y2 = x.copy(), y.copy()
+        x2[:, col] += shift
+        y2[:, col] += shift
+        m2 = orc.mass_def(x2, y2)
+        E = x[:, 0] * np.cosh(x[:, 1]) + y[:, 0] * np.cosh(y[:, 1]) + x[:, 3] + y[:, 3]
+        tol = 1e-14 * m + 1e-15 * E * E / np.maximum(m, 1e-300)
+        assert np.all(np.abs(m2 - m) <= tol)
+    # for massive legs an eta shift is not a boost: it must change m (guards a mass term dropped)
+    a2, b2 = a.copy(), b.copy()
+    a2[:, 1] += 0.3
+    b2[:, 1] += 0.3
+    assert np.median(np.abs(orc.mass_def(a2, b2) / orc.mass_def(a, b) - 1)) > 1e-6
+
+
+def _adversarial_pairs(n, seed):
+    """Near-collinear, light legs: the E^2/m^2 cancellation regime."""
+    g = syn.rng(seed)
+    a = syn.ptetaphim(g, n)
+    a[:, 0] = np.exp(g.uniform(np.log(50), np.log(1000), n))
+    a[:, 3] = g.uniform(0, 1e-2, n)
+    b = a.copy()
+    b[:, 0] *= np.exp(g.uniform(-1, 1, n))
+    b[:, 1] += g.choice([1e-7, 1e-5, 1e-3], n) * g.uniform(-1, 1, n)
+    b[:, 2] += g.choice([1e-7, 1e-5, 1e-3], n) * g.uniform(-1, 1, n)
+    b[:, 3] = g.uniform(0, 1e-2, n)
+    return a, b
+
+
+def test_mass_definition_vs_identity(orc):
+    """O1 (binary128 definition) and O2 (FP64 all-positive identity) are different formulas."""
+    g = syn.rng(103)
+    a, b = syn.ptetaphim(g, 20000), syn.ptetaphim(g, 20000)
+    rel = np.abs(orc.mass_fp64(a, b) / orc.mass_def(a, b) - 1)
+    assert rel.max() <= 1e-14
+    a, b = _adversarial_pairs(20000, 104)
+    m1 = orc.mass_def(a, b)
+    rel = np.abs(orc.mass_fp64(a, b) / m1 - 1)
+    assert rel.max() <= 1e-14
+    # the plain definition in double is not good enough on these pairs: this is why O1 runs in
+    # binary128 (information, but also a check that the adversarial set is adversarial)
+    naive = np.abs(orc.mass_naive_fp64(a, b) / m1 - 1)
+    assert naive.max() > 1e-9
+
+
+def test_mass_threads_agree(orc):
+    g = syn.rng(105)
+    a, b = syn.ptetaphim(g, 5000), syn.ptetaphim(g, 5000)
+    assert np.array_equal(orc.mass_def(a, b, 1), orc.mass_def(a, b, 4))
+    assert np.array_equal(orc.mass_fp64(a, b, 1), orc.mass_fp64(a, b, 3))
+
+
+# ------------------------------------------------------------------------------------ mass grad
+
+def test_mass_grad_massless_closed_form(orc):
+    """m = sqrt(2 pt1 pt2 (cosh d - cos f)):  dm/dpt1 = m/(2 pt1),
+    dm/deta1 = pt1 pt2 sinh(d)/m, dm/dphi1 = pt1 pt2 sin(f)/m, with d = eta1-eta2, f = phi1-phi2;
+    the derivative in m1 at m1 = 0 is 0."""
+    a, b = _massless_pairs(300, 106)
+    gm = syn.upstream(syn.rng(107), 300)
+    ga, gb = orc.mass_grad_def(a, b, gm)
+    m = orc.mass_def(a, b)
+    d, f = a[:, 1] - b[:, 1], a[:, 2] - b[:, 2]
+    pp = a[:, 0] * b[:, 0]
+    want_a = np.stack([m / (2 * a[:, 0]), pp * np.sinh(d) / m, pp * np.sin(f) / m,
+                       np.zeros_like(m)], axis=1) * gm[:, None]
+    want_b = np.stack([m / (2 * b[:, 0]), -pp * np.sinh(d) / m, -pp * np.sin(f) / m,
+                       np.zeros_like(m)], axis=1) * gm[:, None]
+    scale = np.abs(want_a).max(axis=1, keepdims=True)
+    assert np.all(np.abs(ga - want_a) <= 1e-12 * scale)
+    assert np.all(np.abs(gb - want_b) <= 1e-12 * scale)
+
+
+def test_mass_grad_finite_differences(orc):
+    g = syn.rng(108)
+    n = 200
+    a, b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    gm = syn.upstream(g, n)
+    ga, gb = orc.mass_grad_def(a, b, gm)
+    for legs, grad, which in ((a, ga, 0), (b, gb, 1)):
+        for k in range(4):
+            h = 1e-6 * np.maximum(np.abs(legs[:, k]), 1.0)
+            hi, lo = legs.copy(), legs.copy()
+            hi[:, k] += h
+            lo[:, k] -= h
+            if which == 0:
+                fd = (orc.mass_def(hi, b) - orc.mass_def(lo, b)) / (hi[:, k] - lo[:, k])
+            else:
+                fd = (orc.mass_def(a, hi) - orc.mass_def(a, lo)) / (hi[:, k] - lo[:, k])
+            fd *= gm
+            scale = np.abs(grad).max(axis=1) + 1e-300
+            assert np.all(np.abs(fd - grad[:, k]) <= 2e-6 * scale), (which, k)
+
+
+def test_mass_grad_leg_symmetry_and_zero_mass(orc):
+    g = syn.rng(109)
+    a, b = syn.ptetaphim(g, 500), syn.ptetaphim(g, 500)
+    gm = syn.upstream(g, 500)
+    ga, gb = orc.mass_grad_def(a, b, gm)
+    gb2, ga2 = orc.mass_grad_def(b, a, gm)
+    assert np.array_equal(ga, ga2) and np.array_equal(gb, gb2)
+    # m = 0 (collinear massless legs): zero subgradient
+    z = np.array([[10.0, 0.7, -1.0, 0.0]])
+    ga, gb = orc.mass_grad_def(z, z * [2, 1, 1, 1], [1.0])
+    assert abs(orc.mass_def(z, z * [2, 1, 1, 1])[0]) < 1e-12
+    assert np.all(np.abs(ga) <= 1e-3) and np.all(np.abs(gb) <= 1e-3)
+
+
+# ----------------------------------------------------------------------------------------- boost
+
+def test_boost_hand_cases(orc):
+    for r in _golden_rows("boost"):
+        v, beta, want, rtol = np.array(r[0:4]), np.array(r[4:7]), np.array(r[7:11]), r[11]
+        for out in (orc.boost_def(v, beta)[0], orc.boost_fp64(v, beta)[0]):
+            assert np.all(np.abs(out - want) <= rtol * want[3]), (r, out)
+    v = np.array([[1.0, 2.0, 3.0, 10.0]])
+    assert np.array_equal(orc.boost_def(v, np.zeros(3)), v)
+
+
+def _kappa(beta):
+    b = np.sqrt(np.sum(beta * beta, axis=-1))
+    return (1 + b) / (1 - b)
+
+
+def test_boost_inverse_and_rest_frame(orc):
+    g = syn.rng(110)
+    n = 3000
+    v = syn.pxpypze(g, n)
+    beta = syn.velocities(g, n, 0.99)
+    out = orc.boost_def(v, beta)
+    back = orc.boost_def(out, -beta)
+    k = _kappa(beta)
+    assert np.all(np.abs(back - v).max(axis=1) <= 4e-16 * k * k * v[:, 3])
+    # rest frame of v: boosting by -p/E leaves (0, 0, 0, m)
+    rest = orc.boost_def(v, -v[:, :3] / v[:, 3:4])
+    m = orc.lv_mass_def(v)
+    gam = v[:, 3] / np.maximum(m, 1e-300)
+    ok = gam < 1e6
+    err = np.abs(rest - np.stack([0 * m, 0 * m, 0 * m, m], axis=1)).max(axis=1)
+    assert np.all(err[ok] <= 1e-15 * v[ok, 3] * gam[ok] + 1e-13 * m[ok])
+
+
+def test_boost_velocity_addition(orc):
+    """Two boosts along one axis compose to one with (b1 + b2)/(1 + b1 b2)."""
+    g = syn.rng(111)
+    n = 2000
+    v = syn.pxpypze(g, n)
+    u = syn.velocities(g, n, 1.0)
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    b1, b2 = g.uniform(-0.9, 0.9, n), g.uniform(-0.9, 0.9, n)
+    two = orc.boost_def(orc.boost_def(v, u * b1[:, None]), u * b2[:, None])
+    one = orc.boost_def(v, u * ((b1 + b2) / (1 + b1 * b2))[:, None])
+    ab1, ab2 = np.abs(b1), np.abs(b2)
+    k = ((1 + ab1) / (1 - ab1) * (1 + ab2) / (1 - ab2))[:, None]
+    assert np.all(np.abs(two - one) <= 1e-15 * k * v[:, 3:4])
+
+
+def test_boost_matrix_preserves_metric(orc):
+    g = syn.rng(112)
+    G = np.diag([-1.0, -1.0, -1.0, 1.0])
+    for beta in syn.velocities(g, 200, 0.999):
+        L = orc.boost_matrix_def(beta)
+        assert np.allclose(L, L.T, rtol=0, atol=0)
+        gam = L[3, 3]
+        assert np.abs(L.T @ G @ L - G).max() <= 1e-14 * gam * gam
+        # the double-precision comparison value carries the conditioning of 1 - b2 (~gamma^2)
+        assert abs(gam - 1 / math.sqrt(1 - float(beta @ beta))) <= 1e-15 * gam ** 3
+
+
+def test_boost_preserves_mass(orc):
+    g = syn.rng(113)
+    n = 2000
+    v = syn.pxpypze(g, n)
+    v[:, 3] = np.sqrt(np.sum(v[:, :3] ** 2, axis=1) + (0.5 * np.linalg.norm(v[:, :3], axis=1)) ** 2)
+    beta = syn.velocities(g, n, 0.9)
+    m0 = orc.lv_mass_def(v)
+    m1 = orc.lv_mass_def(orc.boost_def(v, beta))
+    assert np.all(np.abs(m1 / m0 - 1) <= 1e-13)
+
+
+def test_boost_definition_vs_vector_form(orc):
+    g = syn.rng(114)
+    n = 20000
+    v = syn.pxpypze(g, n)
+    beta = syn.velocities(g, n, 0.99)
+    o1, o2 = orc.boost_def(v, beta), orc.boost_fp64(v, beta)
+    assert np.all(np.abs(o1 - o2).max(axis=1) <= 1e-14 * o1[:, 3])
+    shared = beta[7]
+    assert np.array_equal(orc.boost_def(v, shared), orc.boost_def(v, np.tile(shared, (n, 1))))
+
+
+def test_boost_superluminal_is_nan(orc):
+    v = np.array([[1.0, 2.0, 3.0, 10.0]])
+    for beta in ([1.0, 0, 0], [0.8, 0.8, 0], [0, 0, -2.0]):
+        assert np.all(np.isnan(orc.boost_def(v, np.array(beta))))
+        assert np.all(np.isnan(orc.boost_fp64(v, np.array(beta))))
+
+
+def test_boost_grad_finite_differences(orc):
+    g = syn.rng(115)
+    n = 200
+    v = syn.pxpypze(g, n) / 100.0
+    beta = syn.velocities(g, n, 0.9)
+    gout = syn.upstream(g, (n, 4))
+    gv, gb = orc.boost_grad_def(v, beta, gout)
+
+    def f(vv, bb):
+        return np.sum(orc.boost_def(vv, bb) * gout, axis=1)
+
+    for k in range(4):
+        h = 1e-6 * np.maximum(np.abs(v[:, k]), 1.0)
+        hi, lo = v.copy(), v.copy()
+        hi[:, k] += h
+        lo[:, k] -= h
+        fd = (f(hi, beta) - f(lo, beta)) / (hi[:, k] - lo[:, k])
+        assert np.all(np.abs(fd - gv[:, k]) <= 1e-7 * np.abs(gv).max(axis=1))
+    for k in range(3):
+        h = 1e-7
+        hi, lo = beta.copy(), beta.copy()
+        hi[:, k] += h
+        lo[:, k] -= h
+        fd = (f(v, hi) - f(v, lo)) / (hi[:, k] - lo[:, k])
+        assert np.all(np.abs(fd - gb[:, k]) <= 1e-6 * np.abs(gb).max(axis=1))
+    # shared velocity: its gradient is the sum of the per-vector ones
+    gv_s, gb_s = orc.boost_grad_def(v, beta[3], gout)
+    gv_t, gb_t = orc.boost_grad_def(v, np.tile(beta[3], (n, 1)), gout)
+    assert np.array_equal(gv_s, gv_t)
+    assert np.allclose(gb_s, gb_t.sum(axis=0), rtol=1e-14, atol=0)
+    # beta = 0: grad_v = gout (identity), grad_beta_k = gout_k E + gout_t p_k
+    gv0, gb0 = orc.boost_grad_def(v, np.zeros((n, 3)), gout)
+    assert np.array_equal(gv0, gout)
+    t1, t2 = gout[:, :3] * v[:, 3:4], gout[:, 3:4] * v[:, :3]
+    assert np.all(np.abs(gb0 - (t1 + t2)) <= 4e-16 * (np.abs(t1) + np.abs(t2)))
+
+
+# ---------------------------------------------------------------------------------------- jagged
+
+def test_event_pairs(orc):
+    g = syn.rng(116)
+    off = syn.jagged_offsets(g, 300, lam=4.0, n_max=12)
+    off = np.concatenate([off, off[-1:] + [0, 1, 3, 6]])  # append events of size 0, 1, 2, 3
+    p = syn.ptetaphim(g, int(off[-1]))
+    pair_off, pair_m, sums = orc.event_pairs_def(p, off)
+    counts = np.diff(off)
+    want_off = np.concatenate([[0], np.cumsum(counts * (counts - 1) // 2)])
+    assert np.array_equal(pair_off, want_off)
+    assert pair_m.shape[0] == want_off[-1]
+    cart = orc.to_cartesian_def(p)
+    for e in range(len(counts)):
+        n, base = counts[e], off[e]
+        ii, jj = np.triu_indices(n, 1)  # row-major i < j
+        got = pair_m[pair_off[e]:pair_off[e + 1]]
+        assert np.array_equal(got, orc.mass_def(p[base + ii], p[base + jj]))
+        want_sum = cart[base:base + n].sum(axis=0) if n else np.zeros(4)
+        assert np.all(np.abs(sums[e] - want_sum) <= 1e-15 * (np.abs(cart[base:base + n]).sum() + 1e-300))
+        if n == 2:  # the event's total mass is its one pair mass
+            assert abs(orc.lv_mass_def(sums[e])[0] - got[0]) <= 1e-9 * got[0] + 1e-9
+    # the multi-body mass of the last (3-particle) event from the pair masses:
+    # M^2 = sum_{i<j} m_ij^2 - (n-2) sum_i m_i^2
+    e = len(counts) - 1
+    mi = p[off[e]:off[e + 1], 3]
+    M2 = np.sum(pair_m[pair_off[e]:pair_off[e + 1]] ** 2) - (3 - 2) * np.sum(mi ** 2)
+    assert abs(orc.lv_mass_def(sums[e])[0] ** 2 - M2) <= 1e-9 * M2
+
+
+def test_event_pairs_rejects_bad_offsets(orc):
+    p = syn.ptetaphim(syn.rng(117), 5)
+    with pytest.raises(ValueError):
+        orc.event_pairs_def(p, [0, 3, 2, 5])
+    with pytest.raises(ValueError):
+        orc.event_pairs_def(p, [0, 2, 4])
