@@ -177,8 +177,9 @@ void orc_mass_naive_fp64(const double *a, const double *b, int64_t n, double *m)
  *     pz: ( sinh eta,     pt cosh eta,  0,          0    )
  *     E : ((px cos phi + py sin phi + pz sinh eta)/E_i, pz pt cosh eta / E_i,
  *          (-px pt sin phi + py pt cos phi)/E_i,  m/E_i )
- * Readings: where m <= 0 the gradient is zero (m is not differentiable at 0); a leg with E_i = 0
- * contributes zero through its E row. */
+ * Readings: where m <= 0 the gradient is zero (m is not differentiable at 0).  A massless leg
+ * (m_i = 0) has E_i = pt cosh(eta), whose derivatives are used as they stand, so that a leg at
+ * pt = 0, m = 0 gets the one-sided (pt >= 0) derivative and dE/dm = 0. */
 static void pair_mass_grad_def(const double *a, const double *b, double gm, double *ga,
                                double *gb) {
   qreal v[2][4], w[4];
@@ -204,7 +205,11 @@ static void pair_mass_grad_def(const double *a, const double *b, double gm, doub
         {sh, pt * ch, 0, 0},
         {0, 0, 0, 0},
     };
-    if (e > 0) {
+    if (mm == 0) {
+      /* massless leg: E = pt cosh(eta), differentiable for pt >= 0 including pt = 0 */
+      J[3][0] = ch;
+      J[3][1] = pt * sh;
+    } else {
       J[3][0] = (px * c + py * s + pz * sh) / e;
       J[3][1] = pz * pt * ch / e;
       J[3][2] = (-px * pt * s + py * pt * c) / e;
