@@ -1,0 +1,500 @@
+#!/usr/bin/env python3
+"""Benchmark of the gvx hot path on GB300.
+
+One step = the FP64 workload at N = 2^26: invariant mass of 2^26 PtEtaPhiM pairs in SoA, the
+same in AoS (32-byte structs), and the boost of 2^26 PxPyPzE vectors, each by its own velocity
+(GenVectorX Sec. 4: "invariant masses from two arrays of particles" and "boosting of one
+array").  Inputs are resident in HBM and larger than L2, so no flush is needed between steps.
+
+Printed on rank 0 as one JSON line: whole-job outputs/s (pair masses + boosted vectors), the
+roofline of the dominant kernel (per-launch CUDA events on the launching stream), the CPU
+oracle's throughput on the host cores, the end-to-end rate with host buffers (copies inside the
+timed region), SM clocks sampled during the timed region, and the other forms of the method
+(FP32, jagged events, forward+backward) measured on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gvx|reference]
+Under torchrun (N > 1) each rank runs an independent replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "inv-mass & boost vectors/s at N=2^26 FP64/FP32, % roofline; fwd+bwd vs fwd"
+UNIT = "vectors/s"
+N_FULL = 1 << 26
+WORKLOAD = ("FP64 invariant mass of 2^26 PtEtaPhiM pairs in SoA and in AoS, plus FP64 boost of "
+            "2^26 PxPyPzE vectors by per-vector beta (|beta| <= 0.99)")
+BYTES_MASS_F64 = 72    # 2 legs x 4 doubles in + 1 double out, per pair
+BYTES_BOOST_F64 = 88   # 4 doubles in + 3 doubles beta + 4 doubles out, per vector
+BYTES_MASS_F32 = 36
+BYTES_BOOST_F32 = 44
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------- workload
+
+def make_inputs(n, seed_stream=1):
+    import gvx_synth as syn
+    g = syn.rng(seed_stream)
+    a, b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    v, beta = syn.pxpypze(g, n), syn.velocities(g, n, 0.99)
+    return a, b, v, beta
+
+
+def cpu_oracle_rate(a, b, v, beta, reps=1):
+    """O2 (FP64 oracle) over the given rows on all host cores: outputs/s for the step's mix
+    (two mass launches + one boost launch)."""
+    import oracle
+    cores = _cores()
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.mass_fp64(a, b, nthreads=cores)
+    t_mass = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.boost_fp64(v, beta, nthreads=cores)
+    t_boost = (time.perf_counter() - t0) / reps
+    n = a.shape[0]
+    return 3 * n / (2 * t_mass + t_boost), cores, t_mass, t_boost
+
+
+class Step:
+    """The timed step: mass SoA, mass AoS, boost, called through the C ABI with preallocated
+    outputs, one CUDA-event pair around every launch."""
+
+    def __init__(self, torch, gvx, a, b, v, beta):
+        from paper_2312_02756_gb300 import _lib
+        self.torch, self.lib, self._lib = torch, gvx.load_library(), _lib
+        n = a.shape[0]
+        self.n = n
+        dev = "cuda"
+        self.a_soa = torch.as_tensor(a.T.copy()).to(dev)
+        self.b_soa = torch.as_tensor(b.T.copy()).to(dev)
+        self.a_aos = torch.as_tensor(a).to(dev)
+        self.b_aos = torch.as_tensor(b).to(dev)
+        self.v = torch.as_tensor(v.T.copy()).to(dev)
+        self.beta = torch.as_tensor(beta.T.copy()).to(dev)
+        self.m1 = torch.empty(n, dtype=torch.float64, device=dev)
+        self.m2 = torch.empty(n, dtype=torch.float64, device=dev)
+        self.out = torch.empty((4, n), dtype=torch.float64, device=dev)
+        L = _lib.LV
+        mk = lambda t, layout, k: self._lv(t, layout, k)
+        self.lv = [mk(self.a_soa, 0, 4), mk(self.b_soa, 0, 4), mk(self.a_aos, 1, 4),
+                   mk(self.b_aos, 1, 4), mk(self.v, 0, 4), mk(self.beta, 0, 3),
+                   mk(self.out, 0, 4)]
+        self.names = ["mass_f64_soa", "mass_f64_aos", "boost_f64_soa"]
+        self.events = None
+
+    @staticmethod
+    def _lv(t, layout, k):
+        from paper_2312_02756_gb300 import _lib
+        x = _lib.LV()
+        x.layout = layout
+        if layout == 1:
+            x.c[0] = t.data_ptr()
+        else:
+            for i in range(k):
+                x.c[i] = t[i].data_ptr()
+        return x
+
+    def __call__(self, stream, ev=None):
+        lib, r, P = self.lib, ctypes.byref, ctypes.c_void_p
+        s = P(stream.cuda_stream)
+        lv = self.lv
+        calls = [
+            lambda: lib.gvx_invariant_mass(r(lv[0]), r(lv[1]), P(self.m1.data_ptr()), self.n, 0, s),
+            lambda: lib.gvx_invariant_mass(r(lv[2]), r(lv[3]), P(self.m2.data_ptr()), self.n, 0, s),
+            lambda: lib.gvx_boost(r(lv[4]), r(lv[5]), 1, r(lv[6]), self.n, 0, s),
+        ]
+        for k, call in enumerate(calls):
+            if ev is not None:
+                ev[k][0].record(stream)
+            st = call()
+            if ev is not None:
+                ev[k][1].record(stream)
+            self._lib.check(st, self.names[k])
+
+
+def time_loop(torch, fn, stream, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+# ---------------------------------------------------------------------------------------- forms
+
+def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms):
+    """FP32, jagged and forward+backward forms, each timed alone on the same GPU."""
+    import gvx_synth as syn
+    from paper_2312_02756_gb300 import _lib
+    lib = gvx.load_library()
+    stream = torch.cuda.current_stream()
+    s = ctypes.c_void_p(stream.cuda_stream)
+    r, P = ctypes.byref, ctypes.c_void_p
+    res = {}
+    # FP32: half the particles light and hard; boost with |beta| <= 0.999999
+    g = syn.rng(2)
+    a = torch.as_tensor(syn.to_f32(syn.ptetaphim_light_mix(g, N_FULL)).T.copy()).cuda()
+    b = torch.as_tensor(syn.to_f32(syn.ptetaphim_light_mix(g, N_FULL)).T.copy()).cuda()
+    m = torch.empty(N_FULL, dtype=torch.float32, device="cuda")
+    la, lb = Step._lv(a, 0, 4), Step._lv(b, 0, 4)
+    t_m = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass(
+        r(la), r(lb), P(m.data_ptr()), N_FULL, 1, s)), stream, steps, warmup)
+    del a, b, m
+    v = torch.as_tensor(syn.to_f32(syn.pxpypze(g, N_FULL)).T.copy()).cuda()
+    be = torch.as_tensor(syn.to_f32(syn.velocities(g, N_FULL, 0.999999)).T.copy()).cuda()
+    o = torch.empty_like(v)
+    lv_, lbe, lo = Step._lv(v, 0, 4), Step._lv(be, 0, 3), Step._lv(o, 0, 4)
+    t_b = time_loop(torch, lambda: _lib.check(lib.gvx_boost(
+        r(lv_), r(lbe), 1, r(lo), N_FULL, 1, s)), stream, steps, warmup)
+    del v, be, o
+    torch.cuda.empty_cache()
+    res["fp32"] = {
+        "workload": "FP32 mass of 2^26 pairs (half light, pt up to 5 TeV) + FP32 boost of 2^26 "
+                    "vectors, |beta| <= 0.999999, SoA",
+        "mass_ms": t_m, "boost_ms": t_b,
+        "mass_pairs_per_s": N_FULL / (t_m * 1e-3), "boost_vectors_per_s": N_FULL / (t_b * 1e-3),
+        "mass_GBps": BYTES_MASS_F32 * N_FULL / (t_m * 1e-3) / 1e9,
+        "boost_GBps": BYTES_BOOST_F32 * N_FULL / (t_b * 1e-3) / 1e9,
+        "mass_speedup_vs_fp64": fp64_mass_ms / t_m,
+    }
+    # jagged: 2^20 events, Poisson(8) multiplicities, one persistent launch in a CUDA graph
+    g = syn.rng(3)
+    off = syn.jagged_offsets(g, 1 << 20)
+    p = torch.as_tensor(syn.ptetaphim(g, int(off[-1]))).cuda()
+    c = np.diff(off)
+    n_pairs = int(np.sum(c * (c - 1) // 2))
+    doff = torch.as_tensor(off).cuda()
+    shape, (te, nt), _ = gvx.autotune_event_pair_masses(p, doff, n_pairs, reps=3, cache=False)
+    graph = gvx.EventPairMassesGraph(p, doff, n_pairs)
+    t_j = time_loop(torch, lambda: graph.launch(stream), stream, steps, warmup)
+    status = gvx.device_status()
+    graph.close()
+    del p, doff, graph
+    torch.cuda.empty_cache()
+    jag_bytes = 32 * int(off[-1]) + 8 * n_pairs + 8 * (len(off)) * 2 + 32 * (len(off) - 1)
+    res["jagged"] = {
+        "workload": "2^20 events, multiplicity Poisson(8) clamped to [0,64]; all in-event pair "
+                    "masses + per-event sums; one persistent kernel replayed as a CUDA graph",
+        "ms": t_j, "pairs": n_pairs, "particles": int(off[-1]),
+        "pairs_per_s": n_pairs / (t_j * 1e-3), "events_per_s": (len(off) - 1) / (t_j * 1e-3),
+        "GBps": jag_bytes / (t_j * 1e-3) / 1e9, "shape": {"events_per_tile": te, "threads": nt},
+        "pairs_per_s_vs_fp64_mass": (n_pairs / (t_j * 1e-3)) / fp64_pairs_per_s,
+        "device_status": status,
+    }
+    # forward + backward, FP64 and FP32, N = 2^24
+    n = 1 << 24
+    out = {}
+    for dt, code, tdt in (("f64", 0, torch.float64), ("f32", 1, torch.float32)):
+        g = syn.rng(4)
+        a = torch.as_tensor(syn.ptetaphim(g, n).T.copy(), dtype=tdt).cuda()
+        b = torch.as_tensor(syn.ptetaphim(g, n).T.copy(), dtype=tdt).cuda()
+        gm = torch.as_tensor(syn.upstream(g, n), dtype=tdt).cuda()
+        m = torch.empty(n, dtype=tdt, device="cuda")
+        ga, gb = torch.empty_like(a), torch.empty_like(b)
+        la, lb, lga, lgb = (Step._lv(t, 0, 4) for t in (a, b, ga, gb))
+        fwd = lambda: _lib.check(lib.gvx_invariant_mass(r(la), r(lb), P(m.data_ptr()), n, code, s))
+        bwd = lambda: _lib.check(lib.gvx_invariant_mass_bwd(
+            r(la), r(lb), P(gm.data_ptr()), r(lga), r(lgb), n, code, s))
+        t_f = time_loop(torch, fwd, stream, steps, warmup)
+        t_fb = time_loop(torch, lambda: (fwd(), bwd()), stream, steps, warmup)
+        del a, b, gm, m, ga, gb
+        v = torch.as_tensor(syn.pxpypze(g, n).T.copy(), dtype=tdt).cuda()
+        be = torch.as_tensor(syn.velocities(g, n, 0.99).T.copy(), dtype=tdt).cuda()
+        go = torch.as_tensor(syn.upstream(g, (n, 4)).T.copy(), dtype=tdt).cuda()
+        o, gv, gbe = torch.empty_like(v), torch.empty_like(v), torch.empty_like(be)
+        lv_, lbe, lgo, lo, lgv, lgbe = (Step._lv(t, 0, k) for t, k in
+                                        ((v, 4), (be, 3), (go, 4), (o, 4), (gv, 4), (gbe, 3)))
+        bf = lambda: _lib.check(lib.gvx_boost(r(lv_), r(lbe), 1, r(lo), n, code, s))
+        bb = lambda: _lib.check(lib.gvx_boost_bwd(r(lv_), r(lbe), 1, r(lgo), r(lgv), r(lgbe), n,
+                                                  code, None, 0, s))
+        t_bf = time_loop(torch, bf, stream, steps, warmup)
+        t_bfb = time_loop(torch, lambda: (bf(), bb()), stream, steps, warmup)
+        del v, be, go, o, gv, gbe
+        torch.cuda.empty_cache()
+        out[dt] = {"mass_fwd_ms": t_f, "mass_fwd_bwd_ms": t_fb, "mass_ratio": t_fb / t_f,
+                   "mass_fwd_bwd_GBps": 208 * n / (t_fb * 1e-3) / 1e9 * (1 if code == 0 else 0.5),
+                   "boost_fwd_ms": t_bf, "boost_fwd_bwd_ms": t_bfb, "boost_ratio": t_bfb / t_bf}
+    out["workload"] = "N = 2^24 pairs / vectors, SoA, upstream gradients uniform in [-1, 1]"
+    res["fwd_bwd"] = out
+    return res
+
+
+# ------------------------------------------------------------------------------------------ e2e
+
+def e2e(torch, step, a, b, v, beta, steps=3, warmup=1):
+    """Same step through the C ABI with pinned HOST buffers: every step copies its inputs
+    host -> device, runs the three kernels and copies the outputs device -> host."""
+    stream = torch.cuda.current_stream()
+    pin = lambda x: torch.as_tensor(x).pin_memory()
+    ha_soa, hb_soa = pin(a.T.copy()), pin(b.T.copy())
+    ha_aos, hb_aos = pin(a), pin(b)
+    hv, hbeta = pin(v.T.copy()), pin(beta.T.copy())
+    hm1 = torch.empty(step.n, dtype=torch.float64).pin_memory()
+    hm2 = torch.empty(step.n, dtype=torch.float64).pin_memory()
+    hout = torch.empty((4, step.n), dtype=torch.float64).pin_memory()
+    pairs = [(step.a_soa, ha_soa), (step.b_soa, hb_soa), (step.a_aos, ha_aos),
+             (step.b_aos, hb_aos), (step.v, hv), (step.beta, hbeta)]
+    outs = [(hm1, step.m1), (hm2, step.m2), (hout, step.out)]
+    h2d = sum(h.numel() * h.element_size() for _, h in pairs)
+    d2h = sum(h.numel() * h.element_size() for h, _ in outs)
+
+    def one():
+        for d, h in pairs:
+            d.copy_(h, non_blocking=True)
+        step(stream)
+        for h, d in outs:
+            h.copy_(d, non_blocking=True)
+
+    ms = time_loop(torch, one, stream, steps, warmup)
+    return {"value": 3 * step.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "how": "pinned host buffers, cudaMemcpyAsync in and out every step, same stream"}
+
+
+# ----------------------------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    sample = 1 << 24
+    a, b, v, beta = make_inputs(sample)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(a[:1 << 16], b[:1 << 16], v[:1 << 16], beta[:1 << 16])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rate, cores, _, _ = cpu_oracle_rate(a, b, v, beta)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 3 * sample / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_FULL},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: 2^24 pairs twice (the SoA and AoS launches) and "
+                                   "2^24 boosts through the FP64 oracle tier O2 on all host "
+                                   "cores; the GPU workload is 2^26 of each"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gvx(args):
+    import torch
+    import paper_2312_02756_gb300 as gvx
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    gvx.load_library()
+    a, b, v, beta = make_inputs(N_FULL)
+    step = Step(torch, gvx, a, b, v, beta)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step(stream)
+    torch.cuda.synchronize()
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)]
+          for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    uuid = getattr(props, "uuid", None)
+    clocks = ClockSampler(("GPU-%s" % uuid) if uuid else torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(stream, ev[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_kernel = [statistics.mean(ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps))
+                  for j in range(3)]
+    units = 3 * N_FULL
+    value = units * world / (ms * 1e-3)
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    kern = {}
+    for name, t, nb in zip(step.names, per_kernel, (BYTES_MASS_F64, BYTES_MASS_F64,
+                                                    BYTES_BOOST_F64)):
+        kern[name] = {"ms": t, "GBps": nb * N_FULL / (t * 1e-3) / 1e9,
+                      "outputs_per_s": N_FULL / (t * 1e-3)}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    achieved = kern[dom]["GBps"]
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": (achieved / hbm) if hbm else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+                if hbm else "fallback 6800 GB/s",
+                "traffic": None,
+                "algorithmic_bytes_per_unit": BYTES_MASS_F64 if "mass" in dom else BYTES_BOOST_F64}
+    if not hbm:
+        roofline["peak"] = 6800.0
+        roofline["frac"] = achieved / 6800.0
+    traffic = _profile_traffic(dom)
+    if traffic is not None:
+        roofline["traffic"] = traffic
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_FULL, "layouts": ["soa", "aos", "soa"],
+                   "l2": "no flush: every launch reads >= 3.7 GB, far above the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "kernels": kern, "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clk,
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(torch, step, a, b, v, beta)
+    if rank == 0 and not args.no_cpu:
+        rate, cores, tm, tb = cpu_oracle_rate(a, b, v, beta)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "the whole 2^26 workload (mass twice, boost once) through the FP64 oracle "
+                      "tier O2 on all host cores: mass %.0f ms, boost %.0f ms" % (tm * 1e3, tb * 1e3)}
+    del step
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_forms:
+        line["forms"] = forms(torch, gvx, max(3, args.steps // 2), 2,
+                              N_FULL / (per_kernel[0] * 1e-3), per_kernel[0])
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _profile_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one exists for the
+    current kernel build (profiles/traffic.json, written by hand from an ncu capture)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    entry = data.get(kernel)
+    return entry.get("bytes_per_launch") if isinstance(entry, dict) else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gvx", choices=["gvx", "reference"])
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gvx(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * gvx -- Lorentz-vector kernels for one GB300 (sm_103a): C ABI.
+ *
+ * The operations follow GenVectorX (arXiv 2312.02756):
+ *   - InvariantMasses (Sec. 3.1, Fig. 1): two arrays of Lorentz vectors in PtEtaPhiM
+ *     coordinates; for each index i the vectors are added and the mass of the sum is stored.
+ *   - ApplyBoost (Sec. 3.1): a Lorentz boost, held in the paper as a 4x4 matrix, applied to
+ *     every vector of a PxPyPzE array.
+ *   - The jagged per-event form (all pair masses and the summed 4-vector of each event) serves
+ *     the RDataFrame-style analyses named as the next target in Sec. 5.
+ *   - The *_bwd entry points are the adjoints (vector-Jacobian products) of the above.
+ *
+ * Conventions shared by every entry point
+ *   Memory:  every pointer is caller-owned DEVICE memory (cudaMalloc, torch, ...) unless the
+ *            name ends in _host.  The library allocates no device memory; the few calls that
+ *            need scratch take a caller-provided workspace and have a *_workspace size query.
+ *   Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *            Every call only enqueues work on `stream` and returns without synchronising
+ *            (the _host variants and gvx_device_status synchronise, as documented).
+ *   Sizes:   element counts are int64_t; n = 0 is valid and launches nothing.
+ *   Errors:  arguments are validated on the host before anything is enqueued; a failed check
+ *            returns its gvx_status and enqueues nothing.  GVX_ERR_CUDA means a launch or a copy
+ *            was refused by the CUDA runtime (cudaGetLastError is cleared and its code kept for
+ *            gvx_last_cuda_error).  Conditions only the device can see (a jagged output that
+ *            does not fit, a bounded wait that timed out) are recorded in a device status word
+ *            read by gvx_device_status.
+ *   Values:  the mass of a PtEtaPhiM vector enters only through m^2 (its sign is ignored); pt is
+ *            a magnitude (pt >= 0; negative pt is outside the domain).  A velocity with
+ *            |beta| >= 1 yields NaN in every output component of that vector.
+ *
+ * Layout of a Lorentz-vector array (gvx_lv):
+ *   GVX_SOA: c[0..3] point to four separate arrays of n scalars (pt, eta, phi, m) or
+ *            (px, py, pz, E); each must be aligned to its scalar size.
+ *   GVX_AOS: c[0] points to n packed structs of four scalars in the same order (32 bytes per
+ *            vector in FP64, 16 in FP32); c[0] must be aligned to the struct size.
+ * Velocities (beta) use the same struct with three components: SoA c[0..2], or AoS with
+ * n packed triples (24 / 12 bytes, aligned to the scalar size).
+ */
+#ifndef GVX_H
+#define GVX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GVX_OK = 0,
+  GVX_ERR_NULL = 1,       /* a required pointer is NULL */
+  GVX_ERR_SIZE = 2,       /* a negative or unsupported size */
+  GVX_ERR_DTYPE = 3,      /* dtype is not GVX_F64 or GVX_F32 */
+  GVX_ERR_LAYOUT = 4,     /* layout is not GVX_SOA or GVX_AOS */
+  GVX_ERR_ALIGN = 5,      /* a pointer is not aligned as its layout requires */
+  GVX_ERR_OFFSETS = 6,    /* jagged offsets are malformed (device-detected) */
+  GVX_ERR_WORKSPACE = 7,  /* workspace NULL or smaller than the size query returned */
+  GVX_ERR_CUDA = 8,       /* the CUDA runtime refused a launch or copy */
+  GVX_ERR_TIMEOUT = 9,    /* a bounded device-side wait gave up (device-detected) */
+  GVX_ERR_CAPACITY = 10,  /* a jagged output is larger than its buffer (device-detected) */
+  GVX_ERR_ARG = 11        /* any other invalid argument */
+} gvx_status;
+
+typedef enum { GVX_F64 = 0, GVX_F32 = 1 } gvx_dtype;
+typedef enum { GVX_SOA = 0, GVX_AOS = 1 } gvx_layout;
+
+typedef struct {
+  void *c[4];     /* see "Layout of a Lorentz-vector array" above */
+  int32_t layout; /* gvx_layout */
+} gvx_lv;
+
+/* Library version, "major.minor.patch". */
+const char *gvx_version(void);
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char *gvx_status_string(int32_t status);
+
+/* The cudaError_t behind the last GVX_ERR_CUDA returned on this host thread (0 if none). */
+int32_t gvx_last_cuda_error(void);
+
+/*
+ * Invariant mass of pairs (Sec. 3.1, Fig. 1: m[i] = (v1[i] + v2[i]).mass()).
+ *   a, b:   n PtEtaPhiM vectors each (layouts may differ), scalars of `dtype`.
+ *   m:      n outputs of `dtype`.  m[i] = sqrt(E^2 - |P|^2) of the summed vector, computed from
+ *           non-negative terms only, so m[i] >= 0 and the result keeps its relative accuracy for
+ *           light, collinear pairs.
+ *   dtype:  GVX_F64 (relative error <= 1e-12 against the exact value) or GVX_F32 (FP32 in and
+ *           out; error stated per output by the test suite).
+ * Returns GVX_OK or a validation error; asynchronous on `stream`.
+ */
+gvx_status gvx_invariant_mass(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n, int32_t dtype,
+                              void *stream);
+
+/*
+ * Adjoint of gvx_invariant_mass: grad_a[i] = grad_m[i] * dm[i]/d(pt, eta, phi, m) of leg a, and
+ * likewise grad_b.  grad_a and grad_b are written (not accumulated) in their own layouts.  Where
+ * m[i] = 0 the gradient is 0 (m is not differentiable there).
+ */
+gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *grad_m,
+                                  gvx_lv *grad_a, gvx_lv *grad_b, int64_t n, int32_t dtype,
+                                  void *stream);
+
+/*
+ * Lorentz boost (Sec. 3.1 ApplyBoost): out[i] = L(beta_i) v[i] for PxPyPzE vectors, with
+ *   gamma = 1/sqrt(1 - beta^2), E' = gamma (E + beta.p),
+ *   p' = p + (gamma^2/(1 + gamma) (beta.p) + gamma E) beta
+ * (the symmetric 4x4 matrix of the paper applied without being stored; "boost by +beta": a
+ * vector at rest acquires velocity +beta).
+ *   v, out:       n vectors (out may alias v only if it has the same layout and pointers).
+ *   beta:         3-component velocity array (SoA c[0..2] or AoS triples).
+ *   beta_stride:  1 = one velocity per vector; 0 = beta[0] applies to every vector.
+ * In FP32, 1 - beta^2 is formed from exact products so that gamma keeps FP32 accuracy as
+ * |beta| -> 1.
+ */
+gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, gvx_lv *out,
+                     int64_t n, int32_t dtype, void *stream);
+
+/* Bytes of workspace gvx_boost_bwd needs (0 unless beta_stride == 0). */
+size_t gvx_boost_bwd_workspace(int64_t n, int64_t beta_stride, int32_t dtype);
+
+/*
+ * Adjoint of gvx_boost for the upstream gradient grad_out (n PxPyPzE-shaped vectors):
+ *   grad_v[i]    = L(beta_i)^T grad_out[i]   (L is symmetric),
+ *   grad_beta[i] = d <grad_out[i], L(beta_i) v[i]> / d beta_i.
+ * beta_stride 0: grad_beta holds one velocity, the sum over i, reduced deterministically through
+ * `workspace` (gvx_boost_bwd_workspace bytes; may be NULL when that is 0).
+ */
+gvx_status gvx_boost_bwd(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride,
+                         const gvx_lv *grad_out, gvx_lv *grad_v, gvx_lv *grad_beta, int64_t n,
+                         int32_t dtype, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace gvx_event_pair_masses needs for n_events events. */
+size_t gvx_event_pair_masses_workspace(int64_t n_events);
+
+/*
+ * Jagged events (FP64).  Event e owns PtEtaPhiM particles [offsets[e], offsets[e+1]).
+ *   particles:     n_particles vectors (SoA or AoS, FP64).
+ *   offsets:       n_events + 1 int64, offsets[0] = 0, non-decreasing, last = n_particles.
+ *   pair_offsets:  out, n_events + 1 int64: exclusive running sum of n_e (n_e - 1)/2.
+ *   pair_m:        out, the masses of all pairs i < j of every event, event after event, each
+ *                  event's pairs in row-major order k(i,j) = i n - i(i+1)/2 + (j - i - 1).
+ *   pair_capacity: length of pair_m; if the total is larger, nothing beyond it is written and
+ *                  GVX_ERR_CAPACITY is recorded in the device status word.
+ *   event_sum:     out, n_events PxPyPzE vectors (SoA or AoS): the sum of each event's particles.
+ *   workspace:     gvx_event_pair_masses_workspace(n_events) bytes of device memory.
+ * Events with more than 64 particles are supported (processed by a slower branch).  Malformed
+ * offsets are detected on the device and recorded as GVX_ERR_OFFSETS.  One launch.
+ */
+gvx_status gvx_event_pair_masses(const gvx_lv *particles, const int64_t *offsets, int64_t n_events,
+                                 int64_t n_particles, int64_t *pair_offsets, double *pair_m,
+                                 int64_t pair_capacity, gvx_lv *event_sum, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+
+/*
+ * Tile shapes of the jagged kernel.  The kernel is compiled for gvx_event_pair_masses_num_shapes()
+ * (events per tile, threads per CTA) shapes; which one a call uses is looked up per device and
+ * per power-of-two bucket of n_events (a default shape until a bucket is tuned or set).
+ */
+int32_t gvx_event_pair_masses_num_shapes(void);
+gvx_status gvx_event_pair_masses_shape(int32_t shape, int32_t *events_per_tile, int32_t *threads);
+int32_t gvx_event_pair_masses_get_shape(int64_t n_events);
+gvx_status gvx_event_pair_masses_set_shape(int64_t n_events, int32_t shape);
+
+/*
+ * Autotuner: runs gvx_event_pair_masses with every shape (one warm-up and `reps` timed runs
+ * each, CUDA events on `stream`), records the fastest for the bucket of n_events on the current
+ * device and returns it in *best_shape (mean time in *best_ms).  Synchronises `stream`; writes
+ * the same outputs as gvx_event_pair_masses.
+ */
+gvx_status gvx_event_pair_masses_autotune(const gvx_lv *particles, const int64_t *offsets,
+                                          int64_t n_events, int64_t n_particles,
+                                          int64_t *pair_offsets, double *pair_m,
+                                          int64_t pair_capacity, gvx_lv *event_sum,
+                                          void *workspace, size_t workspace_bytes, int32_t reps,
+                                          void *stream, int32_t *best_shape, float *best_ms);
+
+/*
+ * Captured form of gvx_event_pair_masses: the whole call (the workspace reset and the one
+ * persistent kernel) recorded once into a CUDA graph for these exact pointers and sizes, with the
+ * shape selected for n_events at creation.  gvx_graph_launch replays it on any stream (one graph
+ * launch per call); the pointed-to buffers must stay valid until gvx_graph_destroy.  Creating the
+ * graph runs the call once (synchronously, on a private stream).
+ */
+typedef struct gvx_graph_s *gvx_graph;
+gvx_status gvx_event_pair_masses_graph_create(const gvx_lv *particles, const int64_t *offsets,
+                                              int64_t n_events, int64_t n_particles,
+                                              int64_t *pair_offsets, double *pair_m,
+                                              int64_t pair_capacity, gvx_lv *event_sum,
+                                              void *workspace, size_t workspace_bytes,
+                                              gvx_graph *out);
+gvx_status gvx_graph_launch(gvx_graph graph, void *stream);
+gvx_status gvx_graph_destroy(gvx_graph graph);
+
+/*
+ * Test hook (fault injection on the host side of one launch).  While enabled on this host thread,
+ * gvx_event_pair_masses starts its tile counter at 1: tile 0 is never processed, so the tiles
+ * after it wait for a prefix that never comes, give up after their bounded wait (about 1 s),
+ * record GVX_ERR_TIMEOUT and finish.  The outputs of such a call are not meaningful.
+ */
+void gvx_testing_skip_first_tile(int32_t enable);
+
+/*
+ * Synchronises `stream`, copies the device status word to *host_status (a gvx_status value:
+ * GVX_OK, or the first device-detected error since the last call) and clears it.
+ */
+gvx_status gvx_device_status(void *stream, int32_t *host_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GVX_H */

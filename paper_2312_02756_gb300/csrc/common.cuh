@@ -1,0 +1,96 @@
+// Device-side helpers shared by the kernel translation units: layout-aware loads and stores of
+// 4-vectors and velocities, and the launch-shape rule.
+#pragma once
+
+#include <stdint.h>
+
+#include "gvx_internal.h"
+
+namespace gvx {
+
+template <typename T>
+struct V4 {
+  T x, y, z, w;
+};
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+
+// Streaming (evict-first) loads: every input element is read exactly once.
+__device__ __forceinline__ double ld_s(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_s(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_s(double *p, double v) { __stcs(p, v); }
+__device__ __forceinline__ void st_s(float *p, float v) { __stcs(p, v); }
+
+template <typename T, int LAYOUT>
+__device__ __forceinline__ V4<T> ld4(const Lv &v, int64_t i) {
+  if constexpr (LAYOUT == GVX_SOA) {
+    return {ld_s((const T *)v.c[0] + i), ld_s((const T *)v.c[1] + i), ld_s((const T *)v.c[2] + i),
+            ld_s((const T *)v.c[3] + i)};
+  } else if constexpr (sizeof(T) == 8) {
+    const double2 *p = (const double2 *)v.c[0] + 2 * i;
+    double2 a = __ldcs(p), b = __ldcs(p + 1);
+    return {a.x, a.y, b.x, b.y};
+  } else {
+    float4 a = __ldcs((const float4 *)v.c[0] + i);
+    return {a.x, a.y, a.z, a.w};
+  }
+}
+
+template <typename T, int LAYOUT>
+__device__ __forceinline__ void st4(const LvOut &v, int64_t i, V4<T> x) {
+  if constexpr (LAYOUT == GVX_SOA) {
+    st_s((T *)v.c[0] + i, x.x);
+    st_s((T *)v.c[1] + i, x.y);
+    st_s((T *)v.c[2] + i, x.z);
+    st_s((T *)v.c[3] + i, x.w);
+  } else if constexpr (sizeof(T) == 8) {
+    double2 *p = (double2 *)v.c[0] + 2 * i;
+    __stcs(p, make_double2(x.x, x.y));
+    __stcs(p + 1, make_double2(x.z, x.w));
+  } else {
+    __stcs((float4 *)v.c[0] + i, make_float4(x.x, x.y, x.z, x.w));
+  }
+}
+
+// Velocities: SoA c[0..2] or packed triples at c[0].  `i` is already multiplied by the stride.
+template <typename T, int LAYOUT>
+__device__ __forceinline__ V3<T> ld3(const Lv &v, int64_t i) {
+  if constexpr (LAYOUT == GVX_SOA) {
+    return {ld_s((const T *)v.c[0] + i), ld_s((const T *)v.c[1] + i), ld_s((const T *)v.c[2] + i)};
+  } else {
+    const T *p = (const T *)v.c[0] + 3 * i;
+    return {ld_s(p), ld_s(p + 1), ld_s(p + 2)};
+  }
+}
+
+template <typename T, int LAYOUT>
+__device__ __forceinline__ void st3(const LvOut &v, int64_t i, V3<T> x) {
+  if constexpr (LAYOUT == GVX_SOA) {
+    st_s((T *)v.c[0] + i, x.x);
+    st_s((T *)v.c[1] + i, x.y);
+    st_s((T *)v.c[2] + i, x.z);
+  } else {
+    T *p = (T *)v.c[0] + 3 * i;
+    st_s(p, x.x);
+    st_s(p + 1, x.y);
+    st_s(p + 2, x.z);
+  }
+}
+
+// Grid for a grid-stride elementwise kernel: enough CTAs to fill every SM `per_sm` times,
+// never more than the work needs.
+inline unsigned grid_for(int64_t n, int threads, int per_sm) {
+  int64_t need = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms() * per_sm;
+  int64_t g = need < cap ? need : cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// Record a device-detected error (the first one since the last read wins).
+__device__ __forceinline__ void raise_status(int32_t *word, int32_t code) {
+  atomicCAS(word, 0, code);
+}
+
+}  // namespace gvx

@@ -1,0 +1,42 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gvx.h"
+
+namespace gvx {
+
+// Device-side view of one Lorentz-vector (or velocity) array.
+struct Lv {
+  const void *c[4];
+  int32_t layout;  // GVX_SOA / GVX_AOS
+};
+struct LvOut {
+  void *c[4];
+  int32_t layout;
+};
+
+inline Lv as_in(const gvx_lv &v) { return Lv{{v.c[0], v.c[1], v.c[2], v.c[3]}, v.layout}; }
+inline LvOut as_out(const gvx_lv &v) { return LvOut{{v.c[0], v.c[1], v.c[2], v.c[3]}, v.layout}; }
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
+// Device status word (one per device, in device memory owned by the library).
+int32_t *device_status_word();
+
+cudaError_t launch_mass(const Lv &a, const Lv &b, void *m, int64_t n, int dtype,
+                        cudaStream_t s);
+cudaError_t launch_mass_bwd(const Lv &a, const Lv &b, const void *gm, const LvOut &ga,
+                            const LvOut &gb, int64_t n, int dtype, cudaStream_t s);
+cudaError_t launch_boost(const Lv &v, const Lv &beta, int64_t beta_stride, const LvOut &out,
+                         int64_t n, int dtype, cudaStream_t s);
+size_t boost_bwd_workspace(int64_t n, int64_t beta_stride, int dtype);
+cudaError_t launch_boost_bwd(const Lv &v, const Lv &beta, int64_t beta_stride, const Lv &gout,
+                             const LvOut &gv, const LvOut &gbeta, int64_t n, int dtype,
+                             void *ws, cudaStream_t s);
+size_t event_pairs_workspace(int64_t n_events);
+
+}  // namespace gvx

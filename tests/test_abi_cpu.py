@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for sm_103a, loads, exports
+every entry point include/gvx.h declares, and rejects invalid arguments before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2312_02756_gb300 as gvx
+    return gvx.load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gvx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(gvx_[a-z0-9_]+)\s*\(", src))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2312_02756_gb300 import _lib
+    declared = _declared()
+    assert declared == set(_lib.EXPORTS)
+    for name in declared:
+        assert getattr(lib, name) is not None
+
+
+def test_version_and_status_strings(lib):
+    assert re.match(rb"^\d+\.\d+\.\d+$", lib.gvx_version())
+    for code in range(12):
+        assert lib.gvx_status_string(code).startswith(b"GVX_")
+    assert lib.gvx_status_string(99) == b"unknown gvx status"
+
+
+def _lv(layout=0, ptrs=(0, 0, 0, 0)):
+    from paper_2312_02756_gb300._lib import LV
+    v = LV()
+    v.layout = layout
+    for k, p in enumerate(ptrs):
+        v.c[k] = p
+    return v
+
+
+def test_mass_validation(lib):
+    good = _lv(0, (64, 128, 192, 256))
+    r = ctypes.byref
+    assert lib.gvx_invariant_mass(r(good), r(good), 512, 10, 7, None) == 3   # dtype
+    assert lib.gvx_invariant_mass(r(good), r(good), 512, -1, 0, None) == 2   # size
+    assert lib.gvx_invariant_mass(r(good), r(good), 512, 0, 0, None) == 0    # n = 0: no-op
+    assert lib.gvx_invariant_mass(None, r(good), 512, 10, 0, None) == 1      # null
+    assert lib.gvx_invariant_mass(r(_lv(0)), r(good), 512, 10, 0, None) == 1
+    assert lib.gvx_invariant_mass(r(good), r(good), None, 10, 0, None) == 1
+    assert lib.gvx_invariant_mass(r(_lv(0, (64, 128, 196, 256))), r(good), 512, 10, 0, None) == 5
+    assert lib.gvx_invariant_mass(r(good), r(good), 516, 10, 0, None) == 5   # misaligned out
+    assert lib.gvx_invariant_mass(r(_lv(1, (48, 0, 0, 0))), r(good), 512, 10, 0, None) == 5
+    assert lib.gvx_invariant_mass(r(_lv(2, (64, 0, 0, 0))), r(good), 512, 10, 0, None) == 4
+    assert lib.gvx_invariant_mass_bwd(r(good), r(good), 512, r(good), None, 10, 0, None) == 1
+
+
+def test_boost_validation(lib):
+    r = ctypes.byref
+    v = _lv(0, (64, 128, 192, 256))
+    beta = _lv(1, (8, 0, 0, 0))
+    assert lib.gvx_boost(r(v), r(beta), 2, r(v), 10, 0, None) == 11          # stride
+    assert lib.gvx_boost(r(v), r(_lv(0, (8, 16, 0, 0))), 1, r(v), 10, 0, None) == 1
+    assert lib.gvx_boost(r(v), r(_lv(1, (4, 0, 0, 0))), 1, r(v), 10, 0, None) == 5
+    assert lib.gvx_boost(r(v), r(beta), 1, r(v), 0, 0, None) == 0
+    assert lib.gvx_boost_bwd(r(v), r(beta), 3, r(v), r(v), r(beta), 10, 0, None, 0, None) == 11
+
+
+def test_jagged_validation(lib):
+    r = ctypes.byref
+    p = _lv(1, (256, 0, 0, 0))
+    sums = _lv(1, (512, 0, 0, 0))
+    ws_need = lib.gvx_event_pair_masses_workspace(1000)
+    assert ws_need == 256 + 8 * ((1000 + 63) // 64)
+    assert lib.gvx_event_pair_masses_workspace(0) == 0
+    args = lambda n_ev, off, ws, wsb: (r(p), off, n_ev, 100, 1024, 2048, 50, r(sums), ws, wsb, None)
+    assert lib.gvx_event_pair_masses(*args(-1, 64, 4096, ws_need)) == 2
+    assert lib.gvx_event_pair_masses(*args(1000, None, 4096, ws_need)) == 1
+    assert lib.gvx_event_pair_masses(*args(1000, 68, 4096, ws_need)) == 5
+    assert lib.gvx_event_pair_masses(*args(1000, 64, 4096, ws_need - 8)) == 7
+    assert lib.gvx_event_pair_masses(*args(1000, 64, None, ws_need)) == 7
+    assert lib.gvx_event_pair_masses(*args(1000, 64, 4100, ws_need)) == 5
+    assert lib.gvx_event_pair_masses_set_shape(1000, 99) == 11
+    n = lib.gvx_event_pair_masses_num_shapes()
+    assert n >= 2
+    te, nt = ctypes.c_int32(), ctypes.c_int32()
+    for s in range(n):
+        assert lib.gvx_event_pair_masses_shape(s, r(te), r(nt)) == 0
+        assert 0 < te.value <= nt.value and nt.value % 32 == 0
+    assert lib.gvx_event_pair_masses_shape(n, r(te), r(nt)) == 11
+    assert lib.gvx_graph_launch(None, None) == 1
+    assert lib.gvx_graph_destroy(None) == 0
+    assert lib.gvx_device_status(None, None) == 1
+
+
+def test_no_cpu_fallback_in_package():
+    """The product path has no CPU or oracle route: the package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2312_02756_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"(import\s+oracle|from\s+oracle|liboracle|gvx_oracle)", src), f

@@ -1,0 +1,113 @@
+"""GPU parity of gvx_boost against the binary128 definition oracle (O1: the 4x4 matrix built
+and applied in binary128).
+
+Error measure (per vector, normwise): max_k |x'_k - ref_k| / E'_ref -- a component can vanish,
+the energy cannot (E' >= |p'|).  FP64 gate 1e-12; FP32 error measured and bounded.
+"""
+import numpy as np
+import pytest
+
+import gvx_synth as syn
+from helpers import TOL_F64, dev, host, normwise, summary, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+N0 = 65_536
+N_FULL = 1 << 26
+
+
+def _run(v, beta, lv="aos", lb="aos", dtype=None):
+    import paper_2312_02756_gb300 as gvx
+    bt = dev(beta, lb, dtype) if beta.ndim == 2 else dev(beta.reshape(1, 3), "aos", dtype)[0]
+    out = gvx.boost(dev(v, lv, dtype), bt)
+    return host(out, lv)
+
+
+@pytest.mark.parametrize("lv,lb", [("aos", "aos"), ("soa", "soa"), ("soa", "aos"), ("aos", "soa")])
+def test_boost_f64_small_workload(orc, lv, lb):
+    torch_cuda()
+    g = syn.rng(3)
+    v, beta = syn.pxpypze(g, N0), syn.velocities(g, N0, 0.99)
+    ref = orc.boost_def(v, beta, nthreads=8)
+    out = _run(v, beta, lv, lb)
+    err = normwise(out, ref, ref[:, 3])
+    print("FP64 boost vs O1 (%s/%s): %s" % (lv, lb, summary(err)))
+    assert err.max() <= TOL_F64
+
+
+def test_boost_f64_shared_velocity_and_edges(orc):
+    torch_cuda()
+    g = syn.rng(4)
+    n = 10_007
+    v = syn.pxpypze(g, n)
+    for beta in (np.array([0.3, -0.5, 0.2]), np.zeros(3), np.array([0.0, 0.0, 0.999999])):
+        out = _run(v, beta)
+        ref = orc.boost_def(v, beta, nthreads=8)
+        if not beta.any():
+            assert np.array_equal(out, v)  # identity, bit for bit
+        assert normwise(out, ref, ref[:, 3]).max() <= TOL_F64
+    # |beta| close to 1 per vector, and superluminal velocities -> NaN
+    beta = syn.velocities(g, n, 0.999999)
+    beta[::97] *= 1.0 / np.linalg.norm(beta[::97], axis=1, keepdims=True)  # |beta| = 1
+    beta[1::97] *= 1.5 / np.linalg.norm(beta[1::97], axis=1, keepdims=True)
+    out, ref = _run(v, beta), orc.boost_def(v, beta, nthreads=8)
+    fin = np.isfinite(ref[:, 3])
+    assert np.array_equal(np.isnan(out).all(axis=1), ~fin)
+    assert normwise(out[fin], ref[fin], ref[fin, 3]).max() <= TOL_F64
+    # rest frame: boosting by -p/E gives (0, 0, 0, m)
+    w = v[:1000]
+    rest = _run(w, -w[:, :3] / w[:, 3:4])
+    assert np.all(normwise(rest, orc.boost_def(w, -w[:, :3] / w[:, 3:4]), w[:, 3]) <= 1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 3, 33, 257, 65_539])
+def test_boost_f64_ragged(orc, n):
+    torch_cuda()
+    g = syn.rng(20 + n)
+    v, beta = syn.pxpypze(g, n), syn.velocities(g, n, 0.99)
+    ref = orc.boost_def(v, beta)
+    for lv in ("aos", "soa"):
+        assert normwise(_run(v, beta, lv, lv), ref, ref[:, 3]).max() <= TOL_F64
+
+
+def test_boost_f64_full_size_sampled(orc):
+    torch = torch_cuda()
+    import paper_2312_02756_gb300 as gvx
+    g = syn.rng(1)
+    v, beta = syn.pxpypze(g, N_FULL), syn.velocities(g, N_FULL, 0.99)
+    idx = np.sort(syn.rng(102).choice(N_FULL, 1 << 16, replace=False))
+    ref = orc.boost_def(v[idx], beta[idx], nthreads=8)
+    dv, db = dev(v, "soa"), dev(beta, "soa")
+    out = gvx.boost(dv, db)
+    torch.cuda.synchronize()
+    del dv, db
+    oh = host(out, "soa")
+    del out
+    torch.cuda.empty_cache()
+    assert np.all(np.isfinite(oh))
+    assert normwise(oh[idx], ref, ref[:, 3]).max() <= TOL_F64
+
+
+def test_boost_f32_error_per_output(orc):
+    """FP32 vectors, |beta| up to 0.999999 (gamma ~ 707): 1 - beta^2 from exact FP32 products."""
+    torch = torch_cuda()
+    g = syn.rng(5)
+    n = 1 << 20
+    v32 = syn.to_f32(syn.pxpypze(g, n))
+    b32 = syn.to_f32(syn.velocities(g, n, 0.999999))
+    ok = np.sum(b32.astype(np.float64) ** 2, axis=1) < 1
+    ref = orc.boost_def(v32.astype(np.float64), b32.astype(np.float64), nthreads=8)
+    # forward error bound of the vector form with every operation rounded to FP32: each output
+    # component is a sum of terms bounded by gamma (E + |beta| |p|), so
+    #   |x'_k - ref_k| <= c u gamma (E + |beta| |p|),  u = 2^-24;  c = 16 covers the ~8 roundings
+    vd, bd = v32.astype(np.float64)[ok], b32.astype(np.float64)[ok]
+    gam = 1 / np.sqrt(1 - np.sum(bd * bd, axis=1))
+    scale = gam * (vd[:, 3] + np.linalg.norm(bd, axis=1) * np.linalg.norm(vd[:, :3], axis=1))
+    for lv in ("aos", "soa"):
+        out = _run(v32, b32, lv, lv, torch.float32)
+        assert out.dtype == np.float32
+        err = normwise(out[ok], ref[ok], ref[ok, 3])
+        print("FP32 boost vs O1 (%s), relative to E': %s" % (lv, summary(err)))
+        print("   in units of u gamma (E + |beta||p|): %s"
+              % summary(normwise(out[ok], ref[ok], scale * 2.0 ** -24)))
+        assert np.all(normwise(out[ok], ref[ok], scale) <= 16 * 2.0 ** -24)
