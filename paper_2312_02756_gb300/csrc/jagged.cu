@@ -376,6 +376,7 @@ cudaError_t launch_event_pairs_shape(int shape, const Lv &p, const int64_t *off,
   A.counter = (unsigned int *)ws;
   A.desc = (unsigned long long *)((char *)ws + kWsHeader);
   A.status = device_status_word();
+  if (!A.status) return cudaErrorInvalidSymbol;
   const bool k = skip_first_tile;
   if (p.layout == GVX_SOA && sums.layout == GVX_SOA)
     return launch_any_shape<GVX_SOA, GVX_SOA>(shape, A, k, s);
