@@ -38,11 +38,15 @@ __global__ void __launch_bounds__(256) mass_kernel(Lv a, Lv b, T *__restrict__ m
 template <typename T>
 __device__ __forceinline__ V4<T> leg_grad(const Leg<T> &s, const Leg<T> &o, T S, T sdeta, T sdphi,
                                           T scale) {
+  // X = P_s E_o / E_s - P_o.  Its denominator vanishes (with E_s > 0) only when P_o = 0 and
+  // either E_o = 0 (the other leg is the zero vector) or P_s = 0 (both legs at rest); X = 0 there.
   T X;
-  if (s.E > (T)0)
-    X = (s.P * s.P * o.q - o.P * o.P * s.q) / ((s.P * o.E + o.P * s.E) * s.E);
-  else
+  if (s.E > (T)0) {
+    T den = (s.P * o.E + o.P * s.E) * s.E;
+    X = den > (T)0 ? (s.P * s.P * o.q - o.P * o.P * s.q) / den : (T)0;
+  } else {
     X = (o.E + o.P) > (T)0 ? o.q / (o.E + o.P) : (T)0;
+  }
   T ch = cosh_(s.eta), sh = sinh_(s.eta);
   V4<T> g;
   g.x = scale * ((T)4 * o.pt * S + (T)2 * ch * X);

@@ -18,8 +18,12 @@ N_FULL = 1 << 26
 
 def _run(v, beta, lv="aos", lb="aos", dtype=None):
     import paper_2312_02756_gb300 as gvx
-    bt = dev(beta, lb, dtype) if beta.ndim == 2 else dev(beta.reshape(1, 3), "aos", dtype)[0]
-    out = gvx.boost(dev(v, lv, dtype), bt)
+    if beta.ndim == 2:
+        bt = dev(beta, lb, dtype)
+        out = gvx.boost(dev(v, lv, dtype), bt, layout=lv, beta_layout=lb)
+    else:
+        bt = dev(beta.reshape(1, 3), "aos", dtype)[0]
+        out = gvx.boost(dev(v, lv, dtype), bt, layout=lv)
     return host(out, lv)
 
 

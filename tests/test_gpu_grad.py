@@ -22,7 +22,7 @@ def _mass_grads(a, b, gm, layout="aos", dtype=None):
     torch = torch_cuda()
     ta = dev(a, layout, dtype).requires_grad_(True)
     tb = dev(b, layout, dtype).requires_grad_(True)
-    m = gvx.invariant_mass(ta, tb)
+    m = gvx.invariant_mass(ta, tb, layout, layout)
     m.backward(torch.as_tensor(gm, dtype=m.dtype, device="cuda"))
     return host(ta.grad, layout), host(tb.grad, layout), m.detach().cpu().numpy()
 
@@ -111,7 +111,7 @@ def _boost_grads(v, beta, gout, layout="aos", dtype=None):
         tb = dev(beta.reshape(1, 3), "aos", dtype)[0].detach().requires_grad_(True)
     else:
         tb = dev(beta, layout, dtype).requires_grad_(True)
-    out = gvx.boost(tv, tb)
+    out = gvx.boost(tv, tb, layout=layout, beta_layout=None if beta.ndim == 1 else layout)
     out.backward(dev(gout, layout, dtype))
     gb = tb.grad.cpu().numpy() if beta.ndim == 1 else host(tb.grad, layout)
     return host(tv.grad, layout), gb

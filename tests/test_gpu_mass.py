@@ -41,7 +41,7 @@ def test_mass_f64_small_workload(cfg0, la, lb):
     torch_cuda()
     import paper_2312_02756_gb300 as gvx
     a, b, ref = cfg0
-    m = gvx.invariant_mass(dev(a, la), dev(b, lb)).cpu().numpy()
+    m = gvx.invariant_mass(dev(a, la), dev(b, lb), la, lb).cpu().numpy()
     _check_f64(m, ref, a, b)
     print("FP64 mass vs O1 (%s/%s): %s" % (la, lb, summary(rel_err(m, ref))))
 
@@ -53,7 +53,7 @@ def test_mass_f64_ragged_sizes(orc, n):
     g = syn.rng(10 + n)
     a, b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
     for layout in ("soa", "aos"):
-        m = gvx.invariant_mass(dev(a, layout), dev(b, layout)).cpu().numpy()
+        m = gvx.invariant_mass(dev(a, layout), dev(b, layout), layout, layout).cpu().numpy()
         assert m.shape == (n,)
         _check_f64(m, orc.mass_def(a, b, nthreads=8), a, b)
 
@@ -64,7 +64,7 @@ def test_mass_f64_edge_cases(orc):
     a, b = edge_pairs()
     ref = orc.mass_def(a, b)
     for layout in ("soa", "aos"):
-        m = gvx.invariant_mass(dev(a, layout), dev(b, layout)).cpu().numpy()
+        m = gvx.invariant_mass(dev(a, layout), dev(b, layout), layout, layout).cpu().numpy()
         _check_f64(m, ref, a, b)
     # adversarial near-collinear light pairs: the plain FP64 form loses up to 1e-8 here
     from test_oracle_pins import _adversarial_pairs
@@ -87,7 +87,7 @@ def test_mass_f64_full_size_sampled(orc):
     ref = orc.mass_def(a[idx], b[idx], nthreads=8)
     for layout in ("soa", "aos"):
         da, db = dev(a, layout), dev(b, layout)
-        m = gvx.invariant_mass(da, db)
+        m = gvx.invariant_mass(da, db, layout, layout)
         torch.cuda.synchronize()
         del da, db
         mh = m.cpu().numpy()
@@ -108,7 +108,7 @@ def test_mass_f32_error_per_output(orc):
     b32 = syn.to_f32(syn.ptetaphim_light_mix(g, n))
     ref = orc.mass_def(a32.astype(np.float64), b32.astype(np.float64), nthreads=8)
     for layout in ("soa", "aos"):
-        m = gvx.invariant_mass(dev(a32, layout), dev(b32, layout)).cpu().numpy()
+        m = gvx.invariant_mass(dev(a32, layout), dev(b32, layout), layout, layout).cpu().numpy()
         assert m.dtype == np.float32
         err = rel_err(m, ref)
         print("FP32 mass vs O1 (%s): %s" % (layout, summary(err)))
