@@ -488,7 +488,11 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n-log2", type=int, default=26,
+                    help="problem size for profiling captures only (the benchmark is 2^26)")
     args = ap.parse_args()
+    global N_FULL
+    N_FULL = 1 << args.n_log2
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
