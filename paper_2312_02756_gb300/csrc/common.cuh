@@ -88,6 +88,23 @@ inline unsigned grid_for(int64_t n, int threads, int per_sm) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Grid for a grid-stride kernel that keeps every SM full: the CTAs that can be resident at
+// once (occupancy query, cached per kernel by the caller's static), never more than the work.
+template <typename Kernel>
+inline unsigned resident_grid(Kernel k, int threads, size_t smem, int64_t n, int *cache) {
+  if (*cache <= 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    *cache = per_sm;
+  }
+  int64_t need = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms() * *cache;
+  int64_t g = need < cap ? need : cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
 // Record a device-detected error (the first one since the last read wins).
 __device__ __forceinline__ void raise_status(int32_t *word, int32_t code) {
   atomicCAS(word, 0, code);

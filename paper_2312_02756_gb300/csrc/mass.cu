@@ -7,9 +7,16 @@
 //             + 4 pt1 pt2 (sinh^2(d_eta/2) + sin^2(d_phi/2)),
 // with P_i = pt_i cosh(eta_i) = |p_i| and E_i = sqrt(P_i^2 + m_i^2): a relative error of a few
 // ulps whatever the cancellation in the plain form.
+//
+// FP64 forward: the identity is evaluated in float-float on the FP32 pipe (mass_ff.cuh) -- a
+// GB300 SM retires ~80x more FP32 than FP64 operations -- with the FP64 evaluation kept for the
+// rare lanes outside the float-float domain (huge |eta|, extreme scale ratios).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
+#include "mass_ff.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
@@ -23,6 +30,38 @@ __global__ void __launch_bounds__(256) mass_kernel(Lv a, Lv b, T *__restrict__ m
     Leg<T> lb = make_leg(ld4<T, LB>(b, i));
     st_s(m + i, sqrt_(pair_terms(la, lb).m2));
   }
+}
+
+// Shared-memory copy of the elementary-function tables (3 KB), taken once per CTA from the
+// kernel parameter.
+__device__ __forceinline__ void stage_tables(const ffm::Tables &src, ffm::Tables *dst) {
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
+  uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(ffm::Tables) / 4); k += blockDim.x) d[k] = s[k];
+  __syncthreads();
+}
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(256) mass_f64_kernel(Lv a, Lv b, double *__restrict__ m, int64_t n,
+                                                       const __grid_constant__ ffm::Tables tab) {
+  __shared__ ffm::Tables T;
+  stage_tables(tab, &T);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    V4<double> x = ld4<double, LA>(a, i);
+    V4<double> y = ld4<double, LB>(b, i);
+    double out;
+    if (!ffm::pair_mass_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T, &out))
+      out = sqrt(pair_terms(make_leg(x), make_leg(y)).m2);
+    st_s(m + i, out);
+  }
+}
+
+const ffm::Tables &host_tables() {
+  static ffm::Tables t;
+  static std::once_flag once;
+  std::call_once(once, [] { ffm::build_tables(&t); });
+  return t;
 }
 
 // Adjoint.  With S = sinh^2(d_eta/2) + sin^2(d_phi/2) and
@@ -82,6 +121,29 @@ __global__ void __launch_bounds__(256) mass_bwd_kernel(Lv a, Lv b, const T *__re
   }
 }
 
+template <int LA, int LB>
+void launch_mass_f64_l(const Lv &a, const Lv &b, double *m, int64_t n, cudaStream_t s) {
+  static int occ[64];
+  const int threads = 256;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  unsigned grid = resident_grid(mass_f64_kernel<LA, LB>, threads, 0, n, &occ[dev & 63]);
+  mass_f64_kernel<LA, LB><<<grid, threads, 0, s>>>(a, b, m, n, host_tables());
+}
+
+cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaStream_t s) {
+  double *mo = (double *)m;
+  if (a.layout == GVX_SOA && b.layout == GVX_SOA)
+    launch_mass_f64_l<GVX_SOA, GVX_SOA>(a, b, mo, n, s);
+  else if (a.layout == GVX_SOA)
+    launch_mass_f64_l<GVX_SOA, GVX_AOS>(a, b, mo, n, s);
+  else if (b.layout == GVX_SOA)
+    launch_mass_f64_l<GVX_AOS, GVX_SOA>(a, b, mo, n, s);
+  else
+    launch_mass_f64_l<GVX_AOS, GVX_AOS>(a, b, mo, n, s);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_mass_t(const Lv &a, const Lv &b, void *m, int64_t n, cudaStream_t s) {
   const int threads = 256;
@@ -131,8 +193,7 @@ cudaError_t launch_mass_bwd_t(const Lv &a, const Lv &b, const void *gm, const Lv
 }  // namespace
 
 cudaError_t launch_mass(const Lv &a, const Lv &b, void *m, int64_t n, int dtype, cudaStream_t s) {
-  return dtype == GVX_F64 ? launch_mass_t<double>(a, b, m, n, s)
-                          : launch_mass_t<float>(a, b, m, n, s);
+  return dtype == GVX_F64 ? launch_mass_f64(a, b, m, n, s) : launch_mass_t<float>(a, b, m, n, s);
 }
 
 cudaError_t launch_mass_bwd(const Lv &a, const Lv &b, const void *gm, const LvOut &ga,

@@ -1,0 +1,70 @@
+// Host build of the library's float-float arithmetic (paper_2312_02756_gb300/csrc/ff.cuh and
+// mass_ff.cuh) for the CPU tests: the same source the kernels compile, called over arrays.
+#include <math.h>
+#include <stdint.h>
+
+#include "../paper_2312_02756_gb300/csrc/ff.cuh"
+#include "../paper_2312_02756_gb300/csrc/mass_ff.cuh"
+
+using namespace gvx::ffm;
+
+static const Tables &tables() {
+  static Tables t;
+  static bool init = false;
+  if (!init) {
+    build_tables(&t);
+    init = true;
+  }
+  return t;
+}
+
+extern "C" {
+
+int64_t ffh_mass(const double *a, const double *b, int64_t n, double *m, uint8_t *ok) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = a + 4 * i, *y = b + 4 * i;
+    double out = NAN;
+    bool f = pair_mass_ff(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], tables(), &out);
+    ok[i] = f;
+    m[i] = out;
+    c += f;
+  }
+  return c;
+}
+
+// op: 0 cosh, 1 sinh, 2 sin_q1, 3 round trip double -> ff -> double, 4 sqrt, 5 sqr
+void ffh_unary(int op, const double *x, int64_t n, double *out, uint8_t *ok) {
+  for (int64_t i = 0; i < n; i++) {
+    bool f = true;
+    ff v = from_double(x[i], &f);
+    ff r;
+    switch (op) {
+      case 0: r = cosh(v, tables()); break;
+      case 1: r = sinh(v, tables()); break;
+      case 2: r = sin_q1(v, tables()); break;
+      case 3: r = v; break;
+      case 4: r = sqrt(v); break;
+      default: r = sqr(v); break;
+    }
+    out[i] = to_double(r);
+    ok[i] = f;
+  }
+}
+
+// op: 0 exact difference, 1 mul, 2 div, 3 add
+void ffh_binary(int op, const double *x, const double *y, int64_t n, double *out, uint8_t *ok) {
+  for (int64_t i = 0; i < n; i++) {
+    bool f = true;
+    ff r;
+    if (op == 0) {
+      r = diff(x[i], y[i], &f);
+    } else {
+      ff a = from_double(x[i], &f), b = from_double(y[i], &f);
+      r = op == 1 ? mul(a, b) : op == 2 ? div(a, b) : add(a, b);
+    }
+    out[i] = to_double(r);
+    ok[i] = f;
+  }
+}
+}
