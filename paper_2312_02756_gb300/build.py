@@ -21,7 +21,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libgvx_%s.so" % platform.machine())
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-              "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
+              "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC, "-I" + BUILD]
+TABLES = os.path.join(BUILD, "gvx_tables.inc")
 
 
 def nvcc() -> str:
@@ -42,7 +43,15 @@ def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(INCLUDE, "gvx.h"))
     files.append(os.path.abspath(__file__))
+    files.append(os.path.join(PKG, "gen_tables.py"))
+    files.append(TABLES)
     return files
+
+
+def generate_tables(path: str = None) -> str:
+    """Write the elementary-function tables the float-float kernels include."""
+    from . import gen_tables
+    return gen_tables.write(path or TABLES)
 
 
 def _stale(target, deps):
@@ -55,6 +64,7 @@ def _stale(target, deps):
 def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) -> str:
     """Compile (if stale) and return the path of the shared library."""
     os.makedirs(BUILD, exist_ok=True)
+    generate_tables()
     deps = _deps()
     if not force and not _stale(LIB_PATH, deps):
         return LIB_PATH
@@ -88,5 +98,10 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
 
 
 if __name__ == "__main__":
+    if __package__ in (None, ""):
+        sys.path.insert(0, ROOT)
+        from paper_2312_02756_gb300 import build as _self
+        sys.exit(print(_self.build(force="--force" in sys.argv,
+                                   ptxas_verbose="--ptxas-v" in sys.argv, quiet=False)))
     print(build(force="--force" in sys.argv, ptxas_verbose="--ptxas-v" in sys.argv,
                 quiet=False))

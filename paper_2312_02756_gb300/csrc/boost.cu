@@ -6,9 +6,15 @@
 //   E' = gamma (E + bp),      p' = p + (k bp + gamma E) beta.
 // 1 - b2 is formed from exact squares (fma) and error-free sums, so gamma keeps the working
 // precision as |beta| -> 1 instead of losing log10(1/(1 - b2)) digits.
+//
+// FP64: gamma and k come from float-float arithmetic on the FP32 pipe (1 - b2 exactly in 64-bit
+// fixed point, then sqrt and two reciprocals), and only the ten multiply-adds that combine
+// them with the vector run on the FP64 pipe: those sums cancel when a vector is boosted towards
+// its rest frame, and keep FP64 rounding there.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace gvx {
 namespace {
@@ -62,6 +68,23 @@ __device__ __forceinline__ V4<T> apply_boost(V3<T> b, BoostCoef<T> c, V4<T> v) {
   return {fma(f, b.x, v.x), fma(f, b.y, v.y), fma(f, b.z, v.z), c.g * (v.w + bp)};
 }
 
+// gamma = 1/s and k = gamma^2/(1 + gamma) = gamma/(1 + s), s = sqrt(1 - b2), in ff; the FP64
+// compensated evaluation outside the fast-path range |beta| <= 0.99998.
+template <typename T>
+__device__ __forceinline__ BoostCoef<T> boost_coef_fast(V3<T> b) {
+  if constexpr (sizeof(T) == 8) {
+    bool ok = true;
+    ffm::ff omb = ffm::one_minus_sq3(b.x, b.y, b.z, &ok);
+    if (ok) {
+      ffm::ff s = ffm::sqrt(omb);
+      ffm::ff g = ffm::recip(s);
+      ffm::ff k = ffm::mul(g, ffm::recip(ffm::add_same(ffm::make(1.0f), s)));
+      return {ffm::to_double(g), ffm::to_double(k), true};
+    }
+  }
+  return boost_coef(b);
+}
+
 template <typename T, int LV, int LBETA, int LOUT, bool SHARED>
 __global__ void __launch_bounds__(256) boost_kernel(Lv v, Lv beta, LvOut out, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -69,12 +92,12 @@ __global__ void __launch_bounds__(256) boost_kernel(Lv v, Lv beta, LvOut out, in
   BoostCoef<T> c0;
   if (SHARED) {
     b0 = ld3<T, LBETA>(beta, 0);
-    c0 = boost_coef(b0);
+    c0 = boost_coef_fast(b0);
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     V4<T> x = ld4<T, LV>(v, i);
     V3<T> b = SHARED ? b0 : ld3<T, LBETA>(beta, i);
-    BoostCoef<T> c = SHARED ? c0 : boost_coef(b);
+    BoostCoef<T> c = SHARED ? c0 : boost_coef_fast(b);
     st4<T, LOUT>(out, i, apply_boost(b, c, x));
   }
 }

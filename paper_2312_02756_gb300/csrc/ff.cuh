@@ -119,6 +119,27 @@ GVX_HD float i2f(int32_t i) {
   return (float)i;
 #endif
 }
+GVX_HD uint32_t dhi(double d) {
+#if defined(__CUDA_ARCH__)
+  return (uint32_t)__double2hiint(d);
+#else
+  return (uint32_t)(d2u(d) >> 32);
+#endif
+}
+GVX_HD uint32_t dlo(double d) {
+#if defined(__CUDA_ARCH__)
+  return (uint32_t)__double2loint(d);
+#else
+  return (uint32_t)d2u(d);
+#endif
+}
+GVX_HD double hilo2d(uint32_t hi, uint32_t lo) {
+#if defined(__CUDA_ARCH__)
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  return u2d(((uint64_t)hi << 32) | lo);
+#endif
+}
 GVX_HD int clz64(uint64_t x) {
 #if defined(__CUDA_ARCH__)
   return __clzll((long long)x);
@@ -149,9 +170,13 @@ GVX_HD ff two_prod(float a, float b) {
 }
 
 // ---- ff arithmetic --------------------------------------------------------------------------
+// Results of add/mul may be left unnormalized (|lo| up to ~2^-22 |hi|): every consumer below
+// reads hi and lo separately, so the value hi + lo keeps its precision; renorm() restores
+// |lo| <= ulp(hi)/2 where a comparison or a conversion needs it.
 
 GVX_HD ff make(float x) { return {x, 0.0f}; }
 GVX_HD ff neg(ff x) { return {-x.hi, -x.lo}; }
+GVX_HD ff renorm(ff x) { return fast_two_sum(x.hi, x.lo); }
 // exact scaling by a power of two
 GVX_HD ff scale(ff x, float p2) { return {fmul(x.hi, p2), fmul(x.lo, p2)}; }
 
@@ -162,211 +187,176 @@ GVX_HD ff add(ff x, ff y) {
   s = fast_two_sum(s.hi, fadd(s.lo, t.hi));
   return fast_two_sum(s.hi, fadd(s.lo, t.lo));
 }
-// x + y for operands of the same sign (no cancellation): cheaper, same accuracy there
+// x + y for operands of the same sign (no cancellation)
 GVX_HD ff add_same(ff x, ff y) {
   ff s = two_sum(x.hi, y.hi);
   return fast_two_sum(s.hi, fadd(s.lo, fadd(x.lo, y.lo)));
 }
-// ff + float of the same sign
-GVX_HD ff add_same_f(ff x, float y) {
-  ff s = two_sum(x.hi, y);
-  return fast_two_sum(s.hi, fadd(s.lo, x.lo));
+// x + y where |y| <= |x| / 2^10 or so (a small correction): no renormalization of the result
+GVX_HD ff add_small(ff x, ff y) {
+  ff s = fast_two_sum(x.hi, y.hi);
+  return {s.hi, fadd(s.lo, fadd(x.lo, y.lo))};
 }
 GVX_HD ff mul(ff x, ff y) {
   ff p = two_prod(x.hi, y.hi);
-  float e = ffma(x.hi, y.lo, p.lo);
-  e = ffma(x.lo, y.hi, e);
-  return fast_two_sum(p.hi, e);
+  return {p.hi, ffma(x.lo, y.hi, ffma(x.hi, y.lo, p.lo))};
 }
 GVX_HD ff mul_f(ff x, float f) {
   ff p = two_prod(x.hi, f);
-  return fast_two_sum(p.hi, ffma(x.lo, f, p.lo));
+  return {p.hi, ffma(x.lo, f, p.lo)};
 }
 GVX_HD ff sqr(ff x) {
   ff p = two_prod(x.hi, x.hi);
-  return fast_two_sum(p.hi, ffma(fadd(x.hi, x.hi), x.lo, p.lo));
+  return {p.hi, ffma(fadd(x.hi, x.hi), x.lo, p.lo)};
 }
-// x / y, y != 0: approximate quotient q1, then two corrections from ff remainders.
+// 1/a to within 1 ulp: hardware approximation and one Newton step.
+GVX_HD float frcp(float a) {
+  float r = fdiv_approx(1.0f, a);
+  return ffma(r, ffma(-a, r, 1.0f), r);
+}
+// 1/sqrt(a) to within ~1 ulp, a > 0: hardware approximation and one Newton step.
+GVX_HD float frsq(float a) {
+  float r = frsqrt_approx(a);
+  return ffma(fmul(0.5f, r), ffma(-a, fmul(r, r), 1.0f), r);
+}
+// x / y, y != 0: q1 = x.hi / y.hi to ~1 ulp, one correction from the ff remainder.
 GVX_HD ff div(ff x, ff y) {
-  float q1 = fdiv_approx(x.hi, y.hi);
-  ff r = add(x, neg(mul_f(y, q1)));
-  ff q = fast_two_sum(q1, fdiv_approx(r.hi, y.hi));
-  ff r2 = add(x, neg(mul(y, q)));
-  return fast_two_sum(q.hi, fadd(q.lo, fdiv_approx(r2.hi, y.hi)));
+  float ry = frcp(y.hi);
+  float q1 = fmul(x.hi, ry);
+  ff p = two_prod(q1, y.hi);
+  float r = fadd(fsub(fsub(x.hi, p.hi), p.lo), ffma(-q1, y.lo, x.lo));
+  return fast_two_sum(q1, fmul(r, ry));
 }
-// sqrt(x), x >= 0: s = x.hi * rsqrt(x.hi), then one correction with the ff residual x - s^2.
+// sqrt(x), x >= 0: s = x.hi / sqrt(x.hi) to ~1 ulp, one correction from the ff residual.
 GVX_HD ff sqrt(ff x) {
   if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
-  float rs = frsqrt_approx(x.hi);
+  float rs = frsq(x.hi);
   float s = fmul(x.hi, rs);
   ff p = two_prod(s, s);
-  ff r = add(x, neg(p));
-  float c = fmul(fmul(r.hi, rs), 0.5f);
-  ff y = fast_two_sum(s, c);
-  // second correction (the first leaves ~2^-45 when rsqrt is off by 2 ulps)
-  ff r2 = add(x, neg(sqr(y)));
-  return fast_two_sum(y.hi, fadd(y.lo, fmul(fmul(r2.hi, rs), 0.5f)));
+  float r = fadd(fsub(fsub(x.hi, p.hi), p.lo), x.lo);
+  return fast_two_sum(s, fmul(fmul(r, rs), 0.5f));
+}
+// 1/x, x != 0
+GVX_HD ff recip(ff x) {
+  float y = frcp(x.hi);
+  ff p = two_prod(y, x.hi);
+  float e = fsub(fsub(1.0f, p.hi), ffma(y, x.lo, p.lo));
+  return fast_two_sum(y, fmul(y, e));
 }
 
 // ---- conversions ----------------------------------------------------------------------------
 
-// d * 2^-shift -> ff.  hi = the value rounded to 24 bits (integer rounding of the fraction),
-// lo = the rounded remainder.  *ok is cleared unless d is 0 or the scaled magnitude lies in
-// [2^-74, 2^126) (so that lo is a normal float and hi cannot overflow); NaN/Inf clear it too.
+// d * 2^-shift -> ff, from the two 32-bit words of d.  hi = the value rounded to 24 bits (integer
+// rounding of the fraction), lo = the rounded remainder.  *ok is cleared unless d is 0 or the
+// scaled magnitude lies in [2^-74, 2^126) (so that lo is a normal float and hi cannot overflow);
+// NaN and Inf clear it too.
 GVX_HD ff from_double(double d, bool *ok, int shift = 0) {
-  uint64_t b = d2u(d);
-  uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-  int e = (int)((b >> 52) & 0x7ff);
-  uint64_t frac = b & 0xfffffffffffffull;
+  uint32_t wh = dhi(d), wl = dlo(d);
+  uint32_t sign = wh & 0x80000000u;
+  int e = (int)((wh >> 20) & 0x7ffu);
   if (e == 0) {
-    if (frac != 0) *ok = false;
+    if ((wh & 0xfffffu) | wl) *ok = false;
     return {u2f(sign), 0.0f};
   }
-  if (e == 0x7ff) *ok = false;
-  int ef = e - 1023 + 127 - shift;  // float biased exponent of hi
+  int ef = e - 896 - shift;  // float biased exponent of hi
   if (ef < 53 || ef > 252) {
     *ok = false;
     ef = 127;
   }
-  uint32_t top = (uint32_t)(frac >> 29);
-  uint32_t rbit = (uint32_t)(frac >> 28) & 1u;
+  uint32_t top = ((wh & 0xfffffu) << 3) | (wl >> 29);
+  uint32_t rbit = (wl >> 28) & 1u;
   uint32_t hib = (sign | ((uint32_t)ef << 23) | top) + rbit;  // a carry moves into the exponent
-  int32_t rem = (int32_t)(uint32_t)(frac & 0x1fffffffu) - (int32_t)(rbit << 29);
-  float lo = fmul(i2f(rem), pow2f(ef - 127 - 52));
+  int32_t rem = (int32_t)(wl & 0x1fffffffu) - (int32_t)(rbit << 29);
+  float lo = fmul(i2f(rem), pow2f(ef - 179));
   return {u2f(hib), sign ? -lo : lo};
 }
 
 // Biased exponent field of a double (0 for zero and denormals).
-GVX_HD int dexp(double d) { return (int)((d2u(d) >> 52) & 0x7ff); }
+GVX_HD int dexp(double d) { return (int)((dhi(d) >> 20) & 0x7ffu); }
 
 // f * 2^shift -> double exactly, by bits (denormal floats flushed to zero; Inf/NaN kept).
 GVX_HD double f2d_bits(float f, int shift = 0) {
   uint32_t u = f2u(f);
-  uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  uint32_t sign = u & 0x80000000u;
   uint32_t ef = (u >> 23) & 0xffu;
-  if (ef == 0) return u2d(sign);
-  uint64_t ed = ef == 0xffu ? 0x7ffull : (uint64_t)((int)ef - 127 + 1023 + shift);
-  return u2d(sign | (ed << 52) | ((uint64_t)(u & 0x7fffffu) << 29));
+  if (ef == 0) return hilo2d(sign, 0u);
+  uint32_t ed = ef == 0xffu ? 0x7ffu : (uint32_t)((int)ef + 896 + shift);
+  return hilo2d(sign | (ed << 20) | ((u & 0x7fffffu) >> 3), (u & 7u) << 29);
 }
 
 // ff * 2^shift -> double: one rounding (one FP64 add).
-GVX_HD double to_double(ff x, int shift = 0) { return f2d_bits(x.hi, shift) + f2d_bits(x.lo, shift); }
+GVX_HD double to_double(ff x, int shift = 0) {
+  return f2d_bits(x.hi, shift) + f2d_bits(x.lo, shift);
+}
 
-// Signed integer D times 2^p as ff (|D| < 2^62), rounding only in lo.
-GVX_HD ff from_scaled_int(int64_t D, int p, bool *ok) {
+// Non-negative integer D times 2^p as ff (D < 2^63), rounding only in lo.
+GVX_HD ff from_scaled_int(uint64_t D, int p, bool *ok) {
   if (D == 0) return {0.0f, 0.0f};
-  uint32_t sign = D < 0 ? 0x80000000u : 0u;
-  uint64_t a = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
-  int lead = 63 - clz64(a);  // position of the leading 1
+  int lead = 63 - clz64(D);  // position of the leading 1
   int sh = lead > 23 ? lead - 23 : 0;
-  uint32_t m = (uint32_t)(a >> sh);  // 24 significant bits (fewer when lead < 23)
-  uint64_t rem = a - ((uint64_t)m << sh);
+  uint32_t m = (uint32_t)(D >> sh);  // 24 significant bits (fewer when lead < 23)
+  uint64_t rem = D - ((uint64_t)m << sh);
   int ehi = lead + p;  // exponent of hi
-  if (p < -126 || ehi > 126) {
+  if (p < -126 || p > 100 || ehi > 126) {
     *ok = false;
-    p = 0;
-    ehi = lead;
+    return {0.0f, 0.0f};
   }
-  float hi;
-  if (lead >= 23) {
-    hi = u2f(sign | ((uint32_t)((ehi + 127) & 0xff) << 23) | (m & 0x7fffffu));
-  } else {
-    hi = fmul(i2f((int32_t)m), pow2f(p > 127 ? 127 : p));
-    if (sign) hi = -hi;
-  }
-  // rem < 2^sh <= 2^39: split so the int -> float conversion sees at most 31 bits
+  float hi = lead >= 23 ? u2f(((uint32_t)(ehi + 127) << 23) | (m & 0x7fffffu))
+                        : fmul(i2f((int32_t)m), pow2f(p));
   float lo = 0.0f;
   if (rem) {
-    int rs = sh > 31 ? sh - 31 : 0;
+    int rs = sh > 31 ? sh - 31 : 0;  // at most 31 bits into the int -> float conversion
     lo = fmul(i2f((int32_t)(rem >> rs)), pow2f(p + rs));
-    if (sign) lo = -lo;
   }
   return {hi, lo};
 }
 
-// Exact a - b for doubles whose exponents differ by at most one (the range where the
-// difference can cancel): integer subtraction of the aligned significands.  Otherwise the
-// ff difference of the converted operands, which keeps relative accuracy there.
-GVX_HD ff diff(double a, double b, bool *ok) {
-  uint64_t ua = d2u(a), ub = d2u(b);
-  int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
-  bool same_sign = ((ua ^ ub) >> 63) == 0;
-  int de = ea - eb;
-  if (same_sign && ea != 0 && eb != 0 && de >= -1 && de <= 1 && ea != 0x7ff && eb != 0x7ff) {
-    int emin = ea < eb ? ea : eb;
-    int64_t ma = (int64_t)((ua & 0xfffffffffffffull) | (1ull << 52)) << (ea - emin);
-    int64_t mb = (int64_t)((ub & 0xfffffffffffffull) | (1ull << 52)) << (eb - emin);
-    int64_t D = ma - mb;
-    if (ua >> 63) D = -D;
-    return from_scaled_int(D, emin - 1075, ok);
-  }
-  ff fa = from_double(a, ok), fb = from_double(b, ok);
-  return add(fa, neg(fb));
-}
-
-// ---- tables for the elementary functions ------------------------------------------------------
-
-// exp family: c = ln2/64, n = 64 k + j;  tm1[j] = 2^(j/64) - 1,  um1[j] = 1 - 2^(-j/64).
-// trig: d = pi/256;  sn[j] = sin(j d), cs[j] = cos(j d), j = 0..128.
-// Reduction constants (Cody & Waite): c = hc[0] + hc[1] + hc[2] with hc[0] carrying 11
-// significant bits (so n hc[0] is exact for |n| < 2^13); d = tc[0] + tc[1] + tc[2] with tc[0]
-// carrying 16 bits.  pi = pi_ff + (remainder below 2^-48).
-struct Tables {
-  ff tm1[64];
-  ff um1[64];
-  ff sn[129];
-  ff cs[129];
-  float hc[3];
-  float tc[3];
-  float inv_c;  // 1/c
-  float inv_d;  // 1/d
-  ff third6;    // 1/6
-  ff pi;
-};
-
-// Host construction of the tables in long double (64- or 113-bit significand).
-#if defined(__CUDACC__)
-#define GVX_HOST __host__
+GVX_HD uint64_t umulhi64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umul64hi(a, b);
 #else
-#define GVX_HOST
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
 #endif
-GVX_HOST static inline ff ff_of_ld(long double x) {
-  float hi = (float)x;
-  float lo = (float)(x - (long double)hi);
-  return {hi, lo};
-}
-GVX_HOST static inline float trunc_bits(long double x, int bits) {
-  int e;
-  long double m = frexpl(x, &e);  // x = m 2^e, 0.5 <= |m| < 1
-  long double t = truncl(ldexpl(m, bits));
-  return (float)ldexpl(t, e - bits);
-}
-GVX_HOST static inline void build_tables(Tables *T) {
-  const long double ln2 = logl(2.0L);
-  const long double pi = acosl(-1.0L);
-  const long double c = ln2 / 64;
-  const long double d = pi / 256;
-  for (int j = 0; j < 64; j++) {
-    T->tm1[j] = ff_of_ld(expm1l((long double)j * c));
-    T->um1[j] = ff_of_ld(-expm1l(-(long double)j * c));
-  }
-  for (int j = 0; j <= 128; j++) {
-    T->sn[j] = ff_of_ld(sinl((long double)j * d));
-    T->cs[j] = ff_of_ld(cosl((long double)j * d));
-  }
-  T->hc[0] = trunc_bits(c, 11);
-  T->hc[1] = (float)(c - T->hc[0]);
-  T->hc[2] = (float)(c - T->hc[0] - (long double)T->hc[1]);
-  T->tc[0] = trunc_bits(d, 16);
-  T->tc[1] = (float)(d - T->tc[0]);
-  T->tc[2] = (float)(d - T->tc[0] - (long double)T->tc[1]);
-  T->inv_c = (float)(1.0L / c);
-  T->inv_d = (float)(1.0L / d);
-  T->third6 = ff_of_ld(1.0L / 6);
-  T->pi = ff_of_ld(pi);
 }
 
-// ---- elementary functions -------------------------------------------------------------------
+// 1 - (bx^2 + by^2 + bz^2) for doubles with |b| < 1, in 64-bit fixed point (unit 2^-62): each
+// square is the top 64 bits of the 106-bit square of the significand, truncated, so the result
+// is exact to 3 * 2^-62.  *ok is cleared when the result is below 2^-16 (|beta| > 0.99998) or
+// any component is not finite / not below 1 in magnitude.
+GVX_HD ff one_minus_sq3(double bx, double by, double bz, bool *ok) {
+  const double c[3] = {bx, by, bz};
+  uint64_t sum = 0;
+  for (int k = 0; k < 3; k++) {
+    uint32_t wh = dhi(c[k]), wl = dlo(c[k]);
+    int eb = (int)((wh >> 20) & 0x7ffu);
+    if (eb == 0) continue;  // zero (denormals count as zero: < 2^-1022)
+    int e = eb - 1023;      // |b| in [2^e, 2^(e+1))
+    if (e >= 0) {
+      *ok = false;
+      return make(0.0f);
+    }
+    uint64_t m = ((((uint64_t)(wh & 0xfffffu) | 0x100000u) << 32) | wl) << 11;
+    uint64_t hi = umulhi64(m, m);  // floor(M^2 2^22 / 2^64); the square is hi 2^(2e - 62)
+    int sh = -2 * e;               // >= 2
+    sum += sh < 64 ? hi >> sh : 0;
+  }
+  const uint64_t one = 1ull << 62;
+  if (sum >= one - (one >> 16)) {  // 1 - b2 < 2^-16
+    *ok = false;
+    return make(0.0f);
+  }
+  return from_scaled_int(one - sum, -62, ok);
+}
+
+// ---- elementary functions (tables in ff_tables.cuh) ------------------------------------------
+
+#if defined(__CUDACC__)
+typedef float4 gvx_f4;
+#else
+struct alignas(16) gvx_f4 {
+  float x, y, z, w;
+};
+#endif
 
 // Round-to-nearest integer of x (|x| < 2^22) with two FP32 adds (the 1.5 * 2^23 shift).
 GVX_HD float round_shift(float x, int *n) {
@@ -377,90 +367,37 @@ GVX_HD float round_shift(float x, int *n) {
 }
 
 // r = x - nf (c0 + c1 + c2) as ff, with nf c0 exact and x.hi - nf c0 exact.
-GVX_HD ff reduce(ff x, float nf, const float *c) {
-  float r1 = ffma(-nf, c[0], x.hi);
-  ff p = two_prod(nf, c[1]);
+GVX_HD ff reduce(ff x, float nf, float c0, float c1, float c2) {
+  float r1 = ffma(-nf, c0, x.hi);
+  ff p = two_prod(nf, c1);
   ff s = two_sum(r1, -p.hi);
-  float lo = fadd(fsub(s.lo, p.lo), fsub(x.lo, fmul(nf, c[2])));
-  return two_sum(s.hi, lo);
+  return two_sum(s.hi, fadd(fsub(s.lo, p.lo), fsub(x.lo, fmul(nf, c2))));
 }
 
-// Even and odd Taylor parts of exp(r) for |r| <= ln2/128:
-//   E = 1 + r^2/2 + r^4/24 (r^6/720 < 4e-17 dropped),  O = r + r^3/6 + r^5/120.
-GVX_HD void exp_parts(ff r, const Tables &T, ff *E, ff *O) {
-  ff r2 = sqr(r);
-  float r4 = fmul(r2.hi, r2.hi);
-  ff e = fast_two_sum(1.0f, fmul(r2.hi, 0.5f));
-  *E = fast_two_sum(e.hi, fadd(e.lo, ffma(r2.lo, 0.5f, fmul(r4, 0.041666668f))));
-  ff r3 = mul(r, r2);
-  ff r3_6 = mul(r3, T.third6);
-  float r5_120 = fmul(fmul(r3.hi, r2.hi), 0.008333334f);
-  *O = add_same(r, add_same_f(r3_6, r5_120));
-}
-
-// cosh(x) for ff x with |x| <= 40:  (2^(n/64) (E + O) + 2^(-n/64) (E - O)) / 2, n = 64 k + j,
-//   2^(j/64) = 1 + tm1[j],  2^(-j/64) = 1 - um1[j].
-GVX_HD ff cosh(ff x, const Tables &T) {
-  if (x.hi < 0.0f) x = neg(x);
-  int n;
-  float nf = round_shift(fmul(x.hi, T.inv_c), &n);
-  ff r = reduce(x, nf, T.hc);
+// Hyperbolic reduction for x >= 0 with x < 16: x = n c + r, |r| <= c/2 = ln2/2048, and the even
+// and odd Taylor parts of exp(r): E = 1 + r^2/2 (r^4/24 < 6e-16 dropped), O = r + r^3/6.
+struct HypParts {
   ff E, O;
-  exp_parts(r, T, &E, &O);
-  int j = n & 63, k = n >> 6;
-  ff tp = fast_two_sum(1.0f, T.tm1[j].hi);
-  tp.lo = fadd(tp.lo, T.tm1[j].lo);
-  ff tn = fast_two_sum(1.0f, -T.um1[j].hi);
-  tn.lo = fsub(tn.lo, T.um1[j].lo);
-  ff ep = scale(mul(tp, add_same(E, O)), pow2f(k - 1));
-  ff en = scale(mul(tn, add(E, neg(O))), pow2f(-k - 1));
-  return add_same(ep, en);
-}
-
-// sinh(x) for ff x with |x| <= 40, accurate to ~2^-46 relative also for tiny |x|:
-//   sinh(n c + r) = S_n E(r) + C_n O(r),
-//   S_n = ((2^k - 2^-k) + 2^k tm1[j] + 2^-k um1[j]) / 2        (all terms >= 0)
-//   C_n = ((2^k + 2^-k) + 2^k tm1[j] - 2^-k um1[j]) / 2        (>= 1)
-GVX_HD ff sinh(ff x, const Tables &T) {
-  bool negx = x.hi < 0.0f;
-  if (negx) x = neg(x);
+  int j, k;  // n = 1024 k + j
+};
+GVX_HD HypParts hyp_parts(ff x, float inv_c, float c0, float c1, float c2) {
+  HypParts h;
   int n;
-  float nf = round_shift(fmul(x.hi, T.inv_c), &n);
-  ff r = reduce(x, nf, T.hc);
-  ff E, O;
-  exp_parts(r, T, &E, &O);
-  int j = n & 63, k = n >> 6;
-  float pk = pow2f(k), mk = pow2f(-k);
-  ff a = scale(T.tm1[j], pk), b = scale(T.um1[j], mk);
-  ff S = scale(add_same(add_same(fast_two_sum(pk, -mk), a), b), 0.5f);
-  ff C = scale(add(add_same(fast_two_sum(pk, mk), a), neg(b)), 0.5f);
-  ff s = add(mul(S, E), mul(C, O));
-  return negx ? neg(s) : s;
+  float nf = round_shift(fmul(x.hi, inv_c), &n);
+  ff r = reduce(x, nf, c0, c1, c2);
+  float t = ffma(r.hi, r.hi, fmul(fadd(r.hi, r.hi), r.lo));  // r^2
+  h.E = fast_two_sum(1.0f, fmul(t, 0.5f));
+  ff o = two_sum(r.hi, fmul(fmul(r.hi, t), 0.16666667f));
+  h.O = {o.hi, fadd(o.lo, r.lo)};
+  h.j = n & 1023;
+  h.k = n >> 10;
+  return h;
 }
 
-// sin(h) for ff h with 0 <= h <= pi/2 (+ a few ulps):  sin(j d + r) = sn[j] cos r + cs[j] sin r,
-//   cos r = 1 - r^2/2 + r^4/24,  sin r = r - r^3/6 + r^5/120,  |r| <= pi/512.
-GVX_HD ff sin_q1(ff h, const Tables &T) {
-  int j;
-  float jf = round_shift(fmul(h.hi, T.inv_d), &j);
-  if (j > 128) {
-    j = 128;
-    jf = 128.0f;
-  }
-  if (j < 0) {
-    j = 0;
-    jf = 0.0f;
-  }
-  ff r = reduce(h, jf, T.tc);
-  ff r2 = sqr(r);
-  float r4 = fmul(r2.hi, r2.hi);
-  ff cr = fast_two_sum(1.0f, -fmul(r2.hi, 0.5f));
-  cr = fast_two_sum(cr.hi, fadd(cr.lo, ffma(-r2.lo, 0.5f, fmul(r4, 0.041666668f))));
-  ff r3 = mul(r, r2);
-  ff r3_6 = mul(r3, T.third6);
-  float r5_120 = fmul(fmul(r3.hi, r2.hi), 0.008333334f);
-  ff sr = add(r, neg(add_same_f(r3_6, -r5_120)));
-  return add(mul(T.sn[j], cr), mul(T.cs[j], sr));
+// E +- O as ff (|O| <= 4e-4, E ~ 1: no cancellation)
+GVX_HD ff add_eo(ff E, ff O) {
+  ff s = fast_two_sum(E.hi, O.hi);
+  return {s.hi, fadd(s.lo, fadd(E.lo, O.lo))};
 }
 
 }  // namespace ffm

@@ -13,8 +13,6 @@
 // rare lanes outside the float-float domain (huge |eta|, extreme scale ratios).
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "common.cuh"
 #include "mass_ff.cuh"
 #include "pair_math.cuh"
@@ -32,20 +30,11 @@ __global__ void __launch_bounds__(256) mass_kernel(Lv a, Lv b, T *__restrict__ m
   }
 }
 
-// Shared-memory copy of the elementary-function tables (3 KB), taken once per CTA from the
-// kernel parameter.
-__device__ __forceinline__ void stage_tables(const ffm::Tables &src, ffm::Tables *dst) {
-  const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
-  uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-  for (int k = threadIdx.x; k < (int)(sizeof(ffm::Tables) / 4); k += blockDim.x) d[k] = s[k];
-  __syncthreads();
-}
-
 template <int LA, int LB>
-__global__ void __launch_bounds__(256) mass_f64_kernel(Lv a, Lv b, double *__restrict__ m, int64_t n,
-                                                       const __grid_constant__ ffm::Tables tab) {
-  __shared__ ffm::Tables T;
-  stage_tables(tab, &T);
+__global__ void __launch_bounds__(256) mass_f64_kernel(Lv a, Lv b, double *__restrict__ m, int64_t n) {
+  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
+  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
+  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     V4<double> x = ld4<double, LA>(a, i);
@@ -55,13 +44,6 @@ __global__ void __launch_bounds__(256) mass_f64_kernel(Lv a, Lv b, double *__res
       out = sqrt(pair_terms(make_leg(x), make_leg(y)).m2);
     st_s(m + i, out);
   }
-}
-
-const ffm::Tables &host_tables() {
-  static ffm::Tables t;
-  static std::once_flag once;
-  std::call_once(once, [] { ffm::build_tables(&t); });
-  return t;
 }
 
 // Adjoint.  With S = sinh^2(d_eta/2) + sin^2(d_phi/2) and
@@ -128,7 +110,7 @@ void launch_mass_f64_l(const Lv &a, const Lv &b, double *m, int64_t n, cudaStrea
   int dev = 0;
   cudaGetDevice(&dev);
   unsigned grid = resident_grid(mass_f64_kernel<LA, LB>, threads, 0, n, &occ[dev & 63]);
-  mass_f64_kernel<LA, LB><<<grid, threads, 0, s>>>(a, b, m, n, host_tables());
+  mass_f64_kernel<LA, LB><<<grid, threads, 0, s>>>(a, b, m, n);
 }
 
 cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaStream_t s) {

@@ -8,15 +8,7 @@
 
 using namespace gvx::ffm;
 
-static const Tables &tables() {
-  static Tables t;
-  static bool init = false;
-  if (!init) {
-    build_tables(&t);
-    init = true;
-  }
-  return t;
-}
+static TabRef tables() { return TabRef{kExpTab, kTrigTab}; }
 
 extern "C" {
 
@@ -40,14 +32,28 @@ void ffh_unary(int op, const double *x, int64_t n, double *out, uint8_t *ok) {
     ff v = from_double(x[i], &f);
     ff r;
     switch (op) {
-      case 0: r = cosh(v, tables()); break;
-      case 1: r = sinh(v, tables()); break;
-      case 2: r = sin_q1(v, tables()); break;
+      case 0: r = cosh_t(v, tables()); break;
+      case 1: r = sinh_t(v, tables()); break;
+      case 2: r = sin_t(v, tables()); break;
       case 3: r = v; break;
       case 4: r = sqrt(v); break;
       default: r = sqr(v); break;
     }
     out[i] = to_double(r);
+    ok[i] = f;
+  }
+}
+
+// gamma = 1/sqrt(1 - b2) and k = gamma^2/(1 + gamma) as the FP64 boost computes them.
+void ffh_boost_coef(const double *beta, int64_t n, double *g, double *k, uint8_t *ok) {
+  for (int64_t i = 0; i < n; i++) {
+    bool f = true;
+    ff omb = one_minus_sq3(beta[3 * i], beta[3 * i + 1], beta[3 * i + 2], &f);
+    ff s = sqrt(omb);
+    ff gg = recip(s);
+    ff kk = mul(gg, recip(add_same(make(1.0f), s)));
+    g[i] = to_double(gg);
+    k[i] = to_double(kk);
     ok[i] = f;
   }
 }
@@ -58,7 +64,7 @@ void ffh_binary(int op, const double *x, const double *y, int64_t n, double *out
     bool f = true;
     ff r;
     if (op == 0) {
-      r = diff(x[i], y[i], &f);
+      r = from_double(x[i] - y[i], &f);
     } else {
       ff a = from_double(x[i], &f), b = from_double(y[i], &f);
       r = op == 1 ? mul(a, b) : op == 2 ? div(a, b) : add(a, b);
