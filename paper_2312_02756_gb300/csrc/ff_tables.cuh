@@ -78,6 +78,55 @@ GVX_HD ff sin_t(ff h, const TabRef &T) {
   return add(mul(ff{t.x, t.y}, cr), mul(ff{t.z, t.w}, sr));
 }
 
+// sinh(x) and cosh(x) together (one reduction), |x| < 16.
+GVX_HD void sinhcosh_t(ff x, const TabRef &T, ff *sh, ff *ch) {
+  bool negx = x.hi < 0.0f;
+  if (negx) x = neg(x);
+  HypParts h = hyp_parts(x, kExpInvC, kExpC0, kExpC1, kExpC2);
+  gvx_f4 t = T.exp[h.j];
+  float pk = pow2f(h.k), mk = pow2f(-h.k);
+  ff a = {fmul(t.x, pk), fmul(t.y, pk)};
+  ff b = {fmul(t.z, mk), fmul(t.w, mk)};
+  ff S = scale(add_same(add_same(fast_two_sum(pk, -mk), a), b), 0.5f);
+  ff tn = fast_two_sum(1.0f, -t.z);
+  tn.lo = fsub(tn.lo, t.w);
+  ff C = add_same(S, scale(tn, mk));
+  ff s = add(mul(S, h.E), mul(C, h.O));
+  *sh = negx ? neg(s) : s;
+  *ch = add(mul(C, h.E), mul(S, h.O));
+}
+
+// sin(phi) and cos(phi) for |phi| <= pi (+ a few ulps), absolute error ~2^-47: the first
+// quadrant through the table, the second through pi - |phi|.
+GVX_HD void sincos_t(double phi, const TabRef &T, ff *sn, ff *cs, bool *ok) {
+  ff a = from_double(fabs(phi), ok);
+  bool q2 = a.hi > 1.57079637f;
+  if (q2) a = add(ff{kPiHi, kPiLo}, neg(a));
+  int j;
+  float jf = round_shift(fmul(a.hi, kTrigInvD), &j);
+  if (j > GVX_TRIG_N) {
+    j = GVX_TRIG_N;
+    jf = (float)GVX_TRIG_N;
+  }
+  if (j < 0) {
+    j = 0;
+    jf = 0.0f;
+  }
+  ff r = reduce(a, jf, kTrigD0, kTrigD1, kTrigD2);
+  ff r2 = two_prod(r.hi, r.hi);
+  r2.lo = ffma(fadd(r.hi, r.hi), r.lo, r2.lo);
+  ff cr = fast_two_sum(1.0f, fmul(r2.hi, -0.5f));
+  cr.lo = fadd(cr.lo, ffma(r2.lo, -0.5f, fmul(fmul(r2.hi, r2.hi), 0.041666668f)));
+  ff sr = two_sum(r.hi, fmul(fmul(r.hi, r2.hi), -0.16666667f));
+  sr.lo = fadd(sr.lo, r.lo);
+  gvx_f4 t = T.trig[j];
+  ff sj = {t.x, t.y}, cj = {t.z, t.w};
+  ff s = add(mul(sj, cr), mul(cj, sr));
+  ff c = add(mul(cj, cr), neg(mul(sj, sr)));
+  *sn = (dhi(phi) >> 31) ? neg(s) : s;
+  *cs = q2 ? neg(c) : c;
+}
+
 #if defined(__CUDACC__)
 // Copy both tables (32 KB) into shared memory; every thread of the CTA takes part.
 __device__ __forceinline__ TabRef stage_tables(gvx_f4 *s_exp, gvx_f4 *s_trig) {

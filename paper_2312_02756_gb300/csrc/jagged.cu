@@ -9,24 +9,31 @@
 //      (bounded wait: a predecessor that never publishes makes the CTA record GVX_ERR_TIMEOUT
 //      and go on);  write pair_offsets;
 //   3. stage the tile's particles in shared memory in sub-batches of at most kCP particles:
-//      per-particle terms (cosh, sinh, sincos, sqrt) once per particle, then the event sums
-//      (one thread per event) and the pair masses (one thread per pair over the flattened pair
-//      range of the sub-batch, coalesced stores);
+//      per-particle terms once per particle -- the float-float leg (pt, P = pt cosh(eta), m^2,
+//      E^2, scaled by the event's power of two) and the Cartesian components for the sums --
+//      then the event sums (one thread per event, FP64) and the pair masses (one thread per pair
+//      over the flattened pair range of the sub-batch, coalesced stores) with the same
+//      float-float pair arithmetic as the elementwise FP64 kernel (mass_ff.cuh), falling back
+//      to FP64 for pairs outside its domain;
 //   4. an event with more than kCP particles is handled alone, straight from global memory.
 // Tile descriptors are 64-bit words: 2 flag bits (aggregate / inclusive prefix) + 62-bit value.
 #include <cuda_runtime.h>
 
 #include <type_traits>
 
+#include <limits.h>
+
 #include "common.cuh"
+#include "mass_ff.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
 namespace {
 
-constexpr int kCP = 1024;  // particles staged in shared memory per sub-batch
-constexpr int kSmemArrays = 9;
-constexpr size_t kDynSmem = (size_t)kSmemArrays * kCP * sizeof(double);
+constexpr int kCP = 384;  // particles staged in shared memory per sub-batch
+// per particle: eta, phi, px, py, pz, E (doubles), pt, P, q, E2 (float pairs), scale (int)
+constexpr size_t kDynSmem = (size_t)kCP * (6 * sizeof(double) + 4 * sizeof(float2) + sizeof(int));
+constexpr int kNoFast = INT_MIN;  // scale marker of a particle outside the float-float domain
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -155,15 +162,20 @@ template <int TE, int NT, int LP, int LS>
 __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
   static_assert(TE <= NT && NT % 32 == 0, "one event per thread in the tile scan");
   extern __shared__ double s_dyn[];
-  double *s_pt = s_dyn, *s_eta = s_pt + kCP, *s_phi = s_eta + kCP, *s_q = s_phi + kCP;
-  double *s_P = s_q + kCP, *s_E = s_P + kCP, *s_px = s_E + kCP, *s_py = s_px + kCP;
-  double *s_pz = s_py + kCP;
+  double *s_eta = s_dyn, *s_phi = s_eta + kCP, *s_px = s_phi + kCP, *s_py = s_px + kCP;
+  double *s_pz = s_py + kCP, *s_E = s_pz + kCP;
+  ffm::ff *s_pt = reinterpret_cast<ffm::ff *>(s_E + kCP), *s_P = s_pt + kCP, *s_q = s_P + kCP;
+  ffm::ff *s_E2 = s_q + kCP;
+  int *s_sc = reinterpret_cast<int *>(s_E2 + kCP);
+  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
+  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
   __shared__ int64_t s_off[TE + 1];
   __shared__ int64_t s_pp[TE + 1];
   __shared__ int64_t s_warp[NT / 32];
   __shared__ double s_red[4 * (NT / 32)];
   __shared__ int64_t s_base;
   __shared__ int64_t s_tile;
+  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(A.counter, 1u);
@@ -247,20 +259,60 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
         continue;
       }
       const int np = (int)(s_off[sbe] - pb);
+      // (a) raw particles; pt and m parked in the px/py slots until the event scale is known
       for (int k = threadIdx.x; k < np; k += NT) {
         V4<double> v = ld4<double, LP>(A.p, pb + k);
-        Leg<double> l = make_leg(v);
-        double s, c;
-        sincos(v.z, &s, &c);
-        s_pt[k] = l.pt;
-        s_eta[k] = l.eta;
-        s_phi[k] = l.phi;
-        s_q[k] = l.q;
-        s_P[k] = l.P;
-        s_E[k] = l.E;
-        s_px[k] = v.x * c;
-        s_py[k] = v.x * s;
-        s_pz[k] = v.x * sinh(v.y);
+        s_eta[k] = v.y;
+        s_phi[k] = v.z;
+        s_px[k] = v.x;
+        s_py[k] = v.w;
+        s_sc[k] = ffm::leg_exponent(v.x, v.w);
+      }
+      __syncthreads();
+      // (b) one thread per event: the event's scale, and which particles the fast path takes
+      for (int e = sb + threadIdx.x; e < sbe; e += NT) {
+        const int k0 = (int)(s_off[e] - pb), k1 = (int)(s_off[e + 1] - pb);
+        int emax = 0;
+        for (int k = k0; k < k1; k++) emax = s_sc[k] > emax ? s_sc[k] : emax;
+        for (int k = k0; k < k1; k++) {
+          bool fast = emax > 0 && emax < 0x7ff &&
+                      ffm::leg_in_domain(s_px[k], s_eta[k], s_phi[k], s_py[k], emax);
+          s_sc[k] = fast ? emax - 1023 : kNoFast;
+        }
+      }
+      __syncthreads();
+      // (c) per-particle terms
+      for (int k = threadIdx.x; k < np; k += NT) {
+        const double pt = s_px[k], m = s_py[k], eta = s_eta[k], phi = s_phi[k];
+        const int sc = s_sc[k];
+        bool ok = true;
+        if (sc != kNoFast) {
+          ffm::LegFF l;
+          l.pt = ffm::from_double(pt, &ok, sc);
+          l.q = ffm::sqr(ffm::from_double(m, &ok, sc));
+          ffm::ff sh, ch, sn, cs;
+          ffm::sinhcosh_t(ffm::from_double(eta, &ok), T, &sh, &ch);
+          ffm::sincos_t(phi, T, &sn, &cs, &ok);
+          l.P = ffm::mul(l.pt, ch);
+          l.E2 = ffm::add_same(ffm::sqr(l.P), l.q);
+          s_pt[k] = l.pt;
+          s_P[k] = l.P;
+          s_q[k] = l.q;
+          s_E2[k] = l.E2;
+          s_px[k] = ffm::to_double(ffm::renorm(ffm::mul(l.pt, cs)), sc);
+          s_py[k] = ffm::to_double(ffm::renorm(ffm::mul(l.pt, sn)), sc);
+          s_pz[k] = ffm::to_double(ffm::renorm(ffm::mul(l.pt, sh)), sc);
+          s_E[k] = ffm::to_double(ffm::sqrt(l.E2), sc);
+        }
+        if (sc == kNoFast || !ok) {  // FP64 evaluation
+          s_sc[k] = kNoFast;
+          double sphi, cphi;
+          sincos(phi, &sphi, &cphi);
+          s_px[k] = pt * cphi;
+          s_py[k] = pt * sphi;
+          s_pz[k] = pt * sinh(eta);
+          s_E[k] = make_leg(V4<double>{pt, eta, phi, m}).E;
+        }
       }
       __syncthreads();
       for (int e = sb + threadIdx.x; e < sbe; e += NT) {
@@ -287,11 +339,24 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
         int64_t i, j;
         decode_pair(q - s_pp[lo], n, i, j);
         const int ia = (int)(s_off[lo] - pb + i), ib = (int)(s_off[lo] - pb + j);
-        Leg<double> a = {s_pt[ia], s_eta[ia], s_phi[ia], 0.0, s_q[ia], s_P[ia], s_E[ia]};
-        Leg<double> b = {s_pt[ib], s_eta[ib], s_phi[ib], 0.0, s_q[ib], s_P[ib], s_E[ib]};
+        double mass;
+        bool done = false;
+        const int sc = s_sc[ia];
+        if (sc != kNoFast && s_sc[ib] != kNoFast) {
+          bool ok = true;
+          ffm::LegFF a{s_pt[ia], s_P[ia], s_q[ia], s_E2[ia]};
+          ffm::LegFF b{s_pt[ib], s_P[ib], s_q[ib], s_E2[ib]};
+          ffm::ff m2 = ffm::pair_m2_ff(a, b, s_eta[ia], s_eta[ib], s_phi[ia], s_phi[ib], T, &ok);
+          done = ffm::finish_mass(m2, sc, ok, &mass);
+        }
+        if (!done) {
+          Leg<double> a = make_leg(ld4<double, LP>(A.p, pb + ia));
+          Leg<double> b = make_leg(ld4<double, LP>(A.p, pb + ib));
+          mass = sqrt(pair_terms(a, b).m2);
+        }
         const int64_t dst = base + q;
         if (dst < A.cap)
-          st_s(A.pair_m + dst, sqrt(pair_terms(a, b).m2));
+          st_s(A.pair_m + dst, mass);
         else
           over = true;
       }

@@ -31,21 +31,30 @@ GVX_HD bool within_pi(double d) {
   return h < kPiHiWord || (h == kPiHiWord && dlo(d) <= kPiLoWord);
 }
 
+// Exponent used to scale a leg: the larger biased exponent of pt and m (0 when both are 0).
+GVX_HD int leg_exponent(double pt, double m) {
+  int e1 = dexp(pt), e3 = dexp(m);
+  return e1 > e3 ? e1 : e3;
+}
+
+// Whether one leg is inside the fast-path domain for the scale exponent emax (biased).
+GVX_HD bool leg_in_domain(double pt, double eta, double phi, double m, int emax) {
+  if (dhi(pt) >> 31) return false;                              // pt < 0 (or -0)
+  if (((dhi(eta) >> 20) & 0x7ffu) > 1026u) return false;        // |eta| >= 16, NaN, Inf
+  if (!within_pi(phi)) return false;                            // |phi| > pi, NaN
+  int ep = dexp(pt), em = dexp(m);
+  if (ep >= 0x7ff || em >= 0x7ff) return false;                 // Inf/NaN
+  if ((ep && emax - ep > 30) || (em && emax - em > 30)) return false;
+  return true;
+}
+
 // Fast-path domain test on the raw bits; s receives the scaling exponent.
 GVX_HD bool mass_ff_domain(double pt1, double eta1, double phi1, double m1, double pt2, double eta2,
                            double phi2, double m2, int *s) {
-  if ((dhi(pt1) | dhi(pt2)) >> 31) return false;  // pt < 0 (or -0: handled by the FP64 path)
-  // |eta| < 16: biased exponent <= 1026
-  if (((dhi(eta1) >> 20) & 0x7ffu) > 1026u || ((dhi(eta2) >> 20) & 0x7ffu) > 1026u) return false;
-  if (!within_pi(phi1) || !within_pi(phi2)) return false;
-  int e1 = dexp(pt1), e2 = dexp(pt2), e3 = dexp(m1), e4 = dexp(m2);
-  int emax = e1 > e2 ? e1 : e2;
-  emax = emax > e3 ? emax : e3;
-  emax = emax > e4 ? emax : e4;
+  int ea = leg_exponent(pt1, m1), eb = leg_exponent(pt2, m2);
+  int emax = ea > eb ? ea : eb;
   if (emax == 0 || emax >= 0x7ff) return false;  // all zero, or Inf/NaN
-  // every nonzero scaled magnitude >= 2^-30
-  if ((e1 && emax - e1 > 30) || (e2 && emax - e2 > 30) || (e3 && emax - e3 > 30) ||
-      (e4 && emax - e4 > 30))
+  if (!leg_in_domain(pt1, eta1, phi1, m1, emax) || !leg_in_domain(pt2, eta2, phi2, m2, emax))
     return false;
   *s = emax - 1023;
   return true;
@@ -64,30 +73,51 @@ GVX_HD ff half_dphi_ff(double phi1, double phi2, bool *ok) {
   return scale(y, 0.5f);
 }
 
+// One leg in ff, pt and m scaled by 2^-s: pt, P = pt cosh(eta), q = m^2, E2 = P^2 + q.
+struct LegFF {
+  ff pt, P, q, E2;
+};
+
+GVX_HD LegFF make_leg_ff(double pt, double eta, double m, int s, const TabRef &T, bool *ok) {
+  LegFF l;
+  l.pt = from_double(pt, ok, s);
+  l.q = sqr(from_double(m, ok, s));
+  l.P = mul(l.pt, cosh_t(from_double(eta, ok), T));
+  l.E2 = add_same(sqr(l.P), l.q);
+  return l;
+}
+
+// Scaled m^2 of a pair of legs (renormalized).  eta and phi are the legs' unscaled angles.
+GVX_HD ff pair_m2_ff(const LegFF &a, const LegFF &b, double eta1, double eta2, double phi1,
+                     double phi2, const TabRef &T, bool *ok) {
+  // 2 (E1 E2 - P1 P2) = 2 (m1^2 E2^2 + m2^2 P1^2) / (E1 E2 + P1 P2)
+  ff den = add_same(sqrt(mul(a.E2, b.E2)), mul(a.P, b.P));
+  ff num = add_same(mul(a.q, b.E2), mul(b.q, sqr(a.P)));
+  ff tm = den.hi > 0.0f ? scale(div(num, den), 2.0f) : make(0.0f);
+  // 4 pt1 pt2 (sinh^2(d_eta/2) + sin^2(d_phi/2)); d_eta in FP64 is exact where it cancels
+  ff se = sinh_t(scale(from_double(eta1 - eta2, ok), 0.5f), T);
+  ff sp = sin_t(half_dphi_ff(phi1, phi2, ok), T);
+  ff ta = scale(mul(mul(a.pt, b.pt), add_same(sqr(se), sqr(sp))), 4.0f);
+  return renorm(add_same(add_same(add_same(a.q, b.q), tm), ta));
+}
+
+// sqrt of a scaled m^2 as a double; false when m^2 fell below 2^-80 (where flushed terms could
+// matter) or an operand left the float range.
+GVX_HD bool finish_mass(ff m2s, int s, bool ok, double *out) {
+  if (!ok || (m2s.hi < 8.27180613e-25f && m2s.hi != 0.0f)) return false;  // 2^-80
+  *out = to_double(sqrt(m2s), s);
+  return true;
+}
+
 // Returns false (and leaves *out untouched) outside the fast-path domain.
 GVX_HD bool pair_mass_ff(double pt1, double eta1, double phi1, double m1, double pt2, double eta2,
                          double phi2, double m2, const TabRef &T, double *out) {
   int s;
   if (!mass_ff_domain(pt1, eta1, phi1, m1, pt2, eta2, phi2, m2, &s)) return false;
   bool ok = true;
-  ff pa = from_double(pt1, &ok, s), pb = from_double(pt2, &ok, s);
-  ff qa = sqr(from_double(m1, &ok, s)), qb = sqr(from_double(m2, &ok, s));
-  ff Pa = mul(pa, cosh_t(from_double(eta1, &ok), T));
-  ff Pb = mul(pb, cosh_t(from_double(eta2, &ok), T));
-  ff P2a = sqr(Pa), P2b = sqr(Pb);
-  ff E2a = add_same(P2a, qa), E2b = add_same(P2b, qb);
-  // 2 (E1 E2 - P1 P2) = 2 (m1^2 E2^2 + m2^2 P1^2) / (E1 E2 + P1 P2)
-  ff den = add_same(sqrt(mul(E2a, E2b)), mul(Pa, Pb));
-  ff num = add_same(mul(qa, E2b), mul(qb, P2a));
-  ff tm = den.hi > 0.0f ? scale(div(num, den), 2.0f) : make(0.0f);
-  // 4 pt1 pt2 (sinh^2(d_eta/2) + sin^2(d_phi/2)); d_eta in FP64 is exact where it cancels
-  ff se = sinh_t(scale(from_double(eta1 - eta2, &ok), 0.5f), T);
-  ff sp = sin_t(half_dphi_ff(phi1, phi2, &ok), T);
-  ff ta = scale(mul(mul(pa, pb), add_same(sqr(se), sqr(sp))), 4.0f);
-  ff m2s = renorm(add_same(add_same(add_same(qa, qb), tm), ta));
-  if (!ok || (m2s.hi < 8.27180613e-25f && m2s.hi != 0.0f)) return false;  // 2^-80
-  *out = to_double(sqrt(m2s), s);
-  return true;
+  LegFF a = make_leg_ff(pt1, eta1, m1, s, T, &ok);
+  LegFF b = make_leg_ff(pt2, eta2, m2, s, T, &ok);
+  return finish_mass(pair_m2_ff(a, b, eta1, eta2, phi1, phi2, T, &ok), s, ok, out);
 }
 
 }  // namespace ffm
