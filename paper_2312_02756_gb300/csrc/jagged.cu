@@ -100,8 +100,22 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *s_warp, i
 }
 
 // Row-major index k of pair (i, j), i < j, among n particles: k = i n - i(i+1)/2 + (j - i - 1).
-// Inverse: the largest i with start(i) = i (2n - i - 1)/2 <= k.
+// Inverse: the largest i with start(i) = i (2n - i - 1)/2 <= k.  The estimate from the
+// quadratic formula (in float: within one of the answer for the sizes staged in shared memory)
+// is corrected by integer steps, so the result is exact for any n.
 __device__ __forceinline__ void decode_pair(int64_t k, int64_t n, int64_t &i, int64_t &j) {
+  float b = (float)(2 * n - 1);
+  int64_t r = (int64_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)k, 0.0f))) * 0.5f);
+  if (r < 0) r = 0;
+  if (r > n - 2) r = n - 2;
+  while (r > 0 && r * (2 * n - r - 1) / 2 > k) r--;
+  while ((r + 1) * (2 * n - r - 2) / 2 <= k) r++;
+  i = r;
+  j = k - r * (2 * n - r - 1) / 2 + r + 1;
+}
+
+// The same decoding with a double-precision estimate, for events of any size.
+__device__ __forceinline__ void decode_pair_wide(int64_t k, int64_t n, int64_t &i, int64_t &j) {
   double b = (double)(2 * n - 1);
   int64_t r = (int64_t)((b - sqrt(fmax(b * b - 8.0 * (double)k, 0.0))) * 0.5);
   if (r < 0) r = 0;
@@ -146,7 +160,7 @@ __device__ void big_event(const JArgs &A, int64_t e, int64_t pbeg, int64_t n, in
   bool over = false;
   for (int64_t k = threadIdx.x; k < npairs; k += NT) {
     int64_t i, j;
-    decode_pair(k, n, i, j);
+    decode_pair_wide(k, n, i, j);
     Leg<double> a = make_leg(ld4<double, LP>(A.p, pbeg + i));
     Leg<double> b = make_leg(ld4<double, LP>(A.p, pbeg + j));
     int64_t dst = out0 + k;
@@ -290,10 +304,11 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
           ffm::LegFF l;
           l.pt = ffm::from_double(pt, &ok, sc);
           l.q = ffm::sqr(ffm::from_double(m, &ok, sc));
-          ffm::ff sh, ch, sn, cs;
-          ffm::sinhcosh_t(ffm::from_double(eta, &ok), T, &sh, &ch);
+          ffm::ff sn, cs;
+          const ffm::ff eta_f = ffm::from_double(eta, &ok);
+          const ffm::ff sh = ffm::sinh_t(eta_f, T);
           ffm::sincos_t(phi, T, &sn, &cs, &ok);
-          l.P = ffm::mul(l.pt, ch);
+          l.P = ffm::mul(l.pt, ffm::cosh_t(eta_f, T));  // as make_leg_ff: bitwise the same leg
           l.E2 = ffm::add_same(ffm::sqr(l.P), l.q);
           s_pt[k] = l.pt;
           s_P[k] = l.P;
