@@ -3,7 +3,7 @@
 
 One step = the FP64 workload at N = 2^26: invariant mass of 2^26 PtEtaPhiM pairs in SoA, the
 same in AoS (32-byte structs), and the boost of 2^26 PxPyPzE vectors, each by its own velocity
-(GenVectorX Sec. 4: "invariant masses from two arrays of particles" and "boosting of one
+(GenVectorX Sec. 5.1: "invariant masses from two arrays of particles" and "boosting of one
 array").  Inputs are resident in HBM and larger than L2, so no flush is needed between steps.
 
 Printed on rank 0 as one JSON line: whole-job outputs/s (pair masses + boosted vectors), the

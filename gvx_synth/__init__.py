@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
 
 This module only draws random numbers with the shapes and distributions of the paper's
-workloads (two arrays of particles for the invariant mass, one array for the boost, Sec. 4.1);
+workloads (two arrays of particles for the invariant mass, one array for the boost, Sec. 5.1);
 it holds none of the arithmetic under test.  Every generator takes a numpy Generator so that the
 CUDA path and the oracle can be fed the identical bytes.
 

@@ -2,12 +2,12 @@
  * gvx -- Lorentz-vector kernels for one GB300 (sm_103a): C ABI.
  *
  * The operations follow GenVectorX (arXiv 2312.02756):
- *   - InvariantMasses (Sec. 3.1, Fig. 1): two arrays of Lorentz vectors in PtEtaPhiM
+ *   - InvariantMasses (Sec. 4.1, Fig. 1): two arrays of Lorentz vectors in PtEtaPhiM
  *     coordinates; for each index i the vectors are added and the mass of the sum is stored.
- *   - ApplyBoost (Sec. 3.1): a Lorentz boost, held in the paper as a 4x4 matrix, applied to
+ *   - ApplyBoost (Sec. 4.1): a Lorentz boost, held in the paper as a 4x4 matrix, applied to
  *     every vector of a PxPyPzE array.
  *   - The jagged per-event form (all pair masses and the summed 4-vector of each event) serves
- *     the RDataFrame-style analyses named as the next target in Sec. 5.
+ *     the RDataFrame-style analyses named as the next target in Sec. 6.
  *   - The *_bwd entry points are the adjoints (vector-Jacobian products) of the above.
  *
  * Conventions shared by every entry point
@@ -79,7 +79,7 @@ const char *gvx_status_string(int32_t status);
 int32_t gvx_last_cuda_error(void);
 
 /*
- * Invariant mass of pairs (Sec. 3.1, Fig. 1: m[i] = (v1[i] + v2[i]).mass()).
+ * Invariant mass of pairs (Sec. 4.1, Fig. 1: m[i] = (v1[i] + v2[i]).mass()).
  *   a, b:   n PtEtaPhiM vectors each (layouts may differ), scalars of `dtype`.
  *   m:      n outputs of `dtype`.  m[i] = sqrt(E^2 - |P|^2) of the summed vector, computed from
  *           non-negative terms only, so m[i] >= 0 and the result keeps its relative accuracy for
@@ -101,7 +101,7 @@ gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *
                                   void *stream);
 
 /*
- * Lorentz boost (Sec. 3.1 ApplyBoost): out[i] = L(beta_i) v[i] for PxPyPzE vectors, with
+ * Lorentz boost (Sec. 4.1 ApplyBoost): out[i] = L(beta_i) v[i] for PxPyPzE vectors, with
  *   gamma = 1/sqrt(1 - beta^2), E' = gamma (E + beta.p),
  *   p' = p + (gamma^2/(1 + gamma) (beta.p) + gamma E) beta
  * (the symmetric 4x4 matrix of the paper applied without being stored; "boost by +beta": a

@@ -17,12 +17,12 @@
  *      baseline.  O1 and O2 use different formulas, so their agreement pins both.
  *
  * Paper references (GenVectorX, arXiv 2312.02756):
- *   Sec. 3.1 and Fig. 1: InvariantMasses -- two arrays of Lorentz vectors given in any 4-D
+ *   Sec. 4.1 and Fig. 1: InvariantMasses -- two arrays of Lorentz vectors given in any 4-D
  *     coordinate system; per index the two vectors are added and mass() of the sum is stored.
- *   Sec. 3.1: ApplyBoost -- a 4-D Lorentz transformation held as a 4x4 matrix and applied to every
+ *   Sec. 4.1: ApplyBoost -- a 4-D Lorentz transformation held as a 4x4 matrix and applied to every
  *     vector of an array.
- *   Sec. 2.1: vectors are templated on the coordinate system (here PtEtaPhiM in, PxPyPzE out).
- *   Sec. 5 (future work, RDataFrame analyses): per-event combinatorics -- the jagged form.
+ *   Sec. 3.1: vectors are templated on the coordinate system (here PtEtaPhiM in, PxPyPzE out).
+ *   Sec. 6 (future work, RDataFrame analyses): per-event combinatorics -- the jagged form.
  * The paper prints no formula for the coordinate conversion or the boost matrix; the standard
  * relations used here (and their readings) are listed beside each function.
  *
@@ -104,7 +104,7 @@ static void run_ranges(range_fn fn, void *ctx, int64_t n, int nthreads) {
 /* ------------------------------------------------------------------------------------------ */
 /* O1: definitions in binary128                                                               */
 
-/* PtEtaPhiM -> PxPyPzE (Sec. 2.1 coordinate systems; the conversion that v1[id] + v2[id] in
+/* PtEtaPhiM -> PxPyPzE (Sec. 3.1 coordinate systems; the conversion that v1[id] + v2[id] in
  * Fig. 1 performs before adding):
  *   px = pt cos(phi), py = pt sin(phi), pz = pt sinh(eta), E = sqrt(px^2 + py^2 + pz^2 + m^2).
  * Reading: the stored m enters only through m^2 (its sign is ignored). */
@@ -144,7 +144,7 @@ static void mass_def_range(void *p, int64_t lo, int64_t hi) {
   for (int64_t i = lo; i < hi; i++) c->m[i] = pair_mass_def(c->a + 4 * i, c->b + 4 * i);
 }
 
-/* Invariant mass of each pair (Sec. 3.1, Fig. 1): m[i] = mass(v1[i] + v2[i]). */
+/* Invariant mass of each pair (Sec. 4.1, Fig. 1): m[i] = mass(v1[i] + v2[i]). */
 void orc_mass_def(const double *a, const double *b, int64_t n, double *m, int nthreads) {
   mass_ctx c = {a, b, m};
   run_ranges(mass_def_range, &c, n, nthreads);
@@ -241,7 +241,7 @@ void orc_mass_grad_def(const double *a, const double *b, const double *gm, int64
   run_ranges(mass_grad_def_range, &c, n, nthreads);
 }
 
-/* The boost matrix (Sec. 3.1: ApplyBoost applies a 4x4 Lorentz matrix).  Index order is
+/* The boost matrix (Sec. 4.1: ApplyBoost applies a 4x4 Lorentz matrix).  Index order is
  * (x, y, z, t) to match PxPyPzE.  For a velocity beta with b2 = |beta|^2 < 1:
  *   gamma = 1 / sqrt(1 - b2)
  *   L[t][t] = gamma,  L[i][t] = L[t][i] = gamma beta_i,
@@ -300,7 +300,7 @@ static void boost_def_range(void *p, int64_t lo, int64_t hi) {
 }
 
 /* out[i] = L(beta[i * stride]) v[i]; stride 1 gives each vector its own velocity, stride 0
- * applies beta[0] to all (Sec. 3.1 ApplyBoost, one array of vectors). */
+ * applies beta[0] to all (Sec. 4.1 ApplyBoost, one array of vectors). */
 void orc_boost_def(const double *v, const double *beta, int64_t beta_stride, int64_t n,
                    double *out, int nthreads) {
   boost_ctx c = {v, beta, beta_stride, out};
@@ -377,7 +377,7 @@ void orc_boost_grad_def(const double *v, const double *beta, int64_t beta_stride
 }
 
 /* Jagged events (the per-event combinatorics of the RDataFrame analyses named as future work in
- * Sec. 5).  Event e owns particles [off[e], off[e+1]) (PtEtaPhiM rows).  Outputs:
+ * Sec. 6).  Event e owns particles [off[e], off[e+1]) (PtEtaPhiM rows).  Outputs:
  *   pair_off[e] = sum over earlier events of n(n-1)/2, pair_off[0] = 0 (n_events + 1 entries);
  *   pair_m[pair_off[e] + k(i,j)] = mass(p_i + p_j) for i < j, packed row-major:
  *     k(i,j) = i n - i(i+1)/2 + (j - i - 1);

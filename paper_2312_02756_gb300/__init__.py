@@ -126,7 +126,7 @@ class _InvariantMass(torch.autograd.Function):
 
 
 def invariant_mass(a: torch.Tensor, b: torch.Tensor, layout_a=None, layout_b=None):
-    """Mass of each pair of PtEtaPhiM vectors (GenVectorX Sec. 3.1, Fig. 1).
+    """Mass of each pair of PtEtaPhiM vectors (GenVectorX Sec. 4.1, Fig. 1).
 
     Differentiable with respect to both legs (hand-written adjoint kernel)."""
     _require_cuda(a, b)
@@ -189,7 +189,7 @@ class _Boost(torch.autograd.Function):
 
 
 def boost(v: torch.Tensor, beta: torch.Tensor, layout=None, beta_layout=None):
-    """Boost PxPyPzE vectors by velocities beta (GenVectorX Sec. 3.1, ApplyBoost).
+    """Boost PxPyPzE vectors by velocities beta (GenVectorX Sec. 4.1, ApplyBoost).
 
     ``beta`` is one velocity per vector ((n, 3) or (3, n)) or one shared (3,) velocity.
     Differentiable with respect to v and beta (hand-written adjoint kernel)."""

@@ -1,4 +1,4 @@
-// Lorentz boost of PxPyPzE vectors and its adjoint (GenVectorX, Sec. 3.1: ApplyBoost applies a
+// Lorentz boost of PxPyPzE vectors and its adjoint (GenVectorX, Sec. 4.1: ApplyBoost applies a
 // 4x4 Lorentz matrix to every vector of an array).
 //
 // The symmetric matrix L(beta) is applied without being formed:

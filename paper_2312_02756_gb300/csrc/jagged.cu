@@ -1,6 +1,6 @@
 // Jagged events: every in-event pair mass and every per-event summed 4-vector, in one
 // persistent launch (the per-event combinatorics of the RDataFrame analyses that GenVectorX
-// names as its next target, Sec. 5; the pair mass itself is that of Sec. 3.1, Fig. 1).
+// names as its next target, Sec. 6; the pair mass itself is that of Sec. 4.1, Fig. 1).
 //
 // Work unit: a tile of TE consecutive events.  CTAs take tiles in increasing order from an
 // atomic counter and stay resident until the tiles run out.  Per tile:

@@ -1,4 +1,4 @@
-// Invariant mass of pairs of PtEtaPhiM vectors and its adjoint (GenVectorX, Sec. 3.1, Fig. 1:
+// Invariant mass of pairs of PtEtaPhiM vectors and its adjoint (GenVectorX, Sec. 4.1, Fig. 1:
 // per index, the two vectors are added and the mass of the sum is stored).
 //
 // The plain form sqrt(E^2 - |P|^2) cancels catastrophically for light, collinear pairs.  Both

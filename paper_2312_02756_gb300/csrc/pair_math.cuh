@@ -1,7 +1,7 @@
 // Pair-mass arithmetic shared by the elementwise kernel (mass.cu) and the jagged-event kernel
 // (jagged.cu), so that both give the same bits for the same two particles.
 //
-// GenVectorX (Sec. 3.1, Fig. 1) forms mass((pt1,eta1,phi1,m1) + (pt2,eta2,phi2,m2)).  The plain
+// GenVectorX (Sec. 4.1, Fig. 1) forms mass((pt1,eta1,phi1,m1) + (pt2,eta2,phi2,m2)).  The plain
 // form sqrt(E^2 - |P|^2) cancels catastrophically for light, collinear pairs; this uses
 //   m^2 = m1^2 + m2^2 + 2 (m1^2 P2^2 + m2^2 P1^2 + m1^2 m2^2) / (E1 E2 + P1 P2)
 //             + 4 pt1 pt2 (sinh^2(d_eta/2) + sin^2(d_phi/2)),
