@@ -152,6 +152,28 @@ gvx_status gvx_event_pair_masses(const gvx_lv *particles, const int64_t *offsets
                                  size_t workspace_bytes, void *stream);
 
 /*
+ * gvx_event_pair_masses without a workspace argument, for callers that cannot allocate device
+ * memory: code that runs where cudaMalloc is not allowed or not wanted -- inside a host callback
+ * or a framework plugin that does not own the allocator, in a pipeline with a fixed memory budget
+ * decided up front, or on a hot path where cudaMalloc's implicit device synchronisation would
+ * stall other streams.  (The paper has no counterpart: its host functions allocate freely.)
+ *
+ * The scratch memory is a fixed array inside the library module, GVX_NOALLOC_MAX_EVENTS events
+ * large (262,400 bytes); every GPU that loads the library keeps it until the process exits.
+ * Arguments and results are those of gvx_event_pair_masses.  More than GVX_NOALLOC_MAX_EVENTS
+ * events returns GVX_ERR_SIZE and launches nothing.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array (each clears what it uses before its kernel): two calls that can
+ * run at the same time on the GPU (unordered streams) race and give wrong results -- order them.
+ * Nothing here calls cudaMalloc, cudaFree or an allocating library routine.
+ */
+#define GVX_NOALLOC_MAX_EVENTS (1 << 21)
+gvx_status gvx_event_pair_masses_noalloc(const gvx_lv *particles, const int64_t *offsets,
+                                         int64_t n_events, int64_t n_particles,
+                                         int64_t *pair_offsets, double *pair_m,
+                                         int64_t pair_capacity, gvx_lv *event_sum, void *stream);
+
+/*
  * Tile shapes of the jagged kernel.  The kernel is compiled for gvx_event_pair_masses_num_shapes()
  * (events per tile, threads per CTA) shapes; which one a call uses is looked up per device and
  * per power-of-two bucket of n_events (a default shape until a bucket is tuned or set).
