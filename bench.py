@@ -307,34 +307,39 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms):
 
 # ------------------------------------------------------------------------------------------ e2e
 
-def e2e(torch, step, a, b, v, beta, steps=3, warmup=1):
-    """Same step through the C ABI with pinned HOST buffers: every step copies its inputs
-    host -> device, runs the three kernels and copies the outputs device -> host."""
+def e2e(torch, gvx, a, b, v, beta, steps=3, warmup=1):
+    """The step through the C ABI with HOST buffers: the same three calls, given pinned host
+    pointers for every input and output, so each kernel streams its inputs over the host link
+    and writes its outputs back over it (both directions at once) inside the timed region.
+    (Explicit cudaMemcpyAsync copies in and out on one stream measured ~2x slower: they do not
+    overlap the two directions.)"""
     stream = torch.cuda.current_stream()
     pin = lambda x: torch.as_tensor(x).pin_memory()
-    ha_soa, hb_soa = pin(a.T.copy()), pin(b.T.copy())
-    ha_aos, hb_aos = pin(a), pin(b)
-    hv, hbeta = pin(v.T.copy()), pin(beta.T.copy())
-    hm1 = torch.empty(step.n, dtype=torch.float64).pin_memory()
-    hm2 = torch.empty(step.n, dtype=torch.float64).pin_memory()
-    hout = torch.empty((4, step.n), dtype=torch.float64).pin_memory()
-    pairs = [(step.a_soa, ha_soa), (step.b_soa, hb_soa), (step.a_aos, ha_aos),
-             (step.b_aos, hb_aos), (step.v, hv), (step.beta, hbeta)]
-    outs = [(hm1, step.m1), (hm2, step.m2), (hout, step.out)]
-    h2d = sum(h.numel() * h.element_size() for _, h in pairs)
-    d2h = sum(h.numel() * h.element_size() for h, _ in outs)
-
-    def one():
-        for d, h in pairs:
-            d.copy_(h, non_blocking=True)
-        step(stream)
-        for h, d in outs:
-            h.copy_(d, non_blocking=True)
-
-    ms = time_loop(torch, one, stream, steps, warmup)
-    return {"value": 3 * step.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "how": "pinned host buffers, cudaMemcpyAsync in and out every step, same stream"}
+    n = a.shape[0]
+    host = {
+        "a_soa": pin(a.T.copy()), "b_soa": pin(b.T.copy()), "a_aos": pin(a), "b_aos": pin(b),
+        "v": pin(v.T.copy()), "beta": pin(beta.T.copy()),
+        "m1": torch.empty(n, dtype=torch.float64).pin_memory(),
+        "m2": torch.empty(n, dtype=torch.float64).pin_memory(),
+        "out": torch.empty((4, n), dtype=torch.float64).pin_memory(),
+    }
+    h2d = sum(host[k].numel() * 8 for k in ("a_soa", "b_soa", "a_aos", "b_aos", "v", "beta"))
+    d2h = sum(host[k].numel() * 8 for k in ("m1", "m2", "out"))
+    step = Step.__new__(Step)  # the timed step, pointed at the host buffers
+    from paper_2312_02756_gb300 import _lib
+    step.torch, step.lib, step._lib, step.n = torch, gvx.load_library(), _lib, n
+    for k, t in host.items():
+        setattr(step, k, t)
+    step.lv = [Step._lv(host["a_soa"], 0, 4), Step._lv(host["b_soa"], 0, 4),
+               Step._lv(host["a_aos"], 1, 4), Step._lv(host["b_aos"], 1, 4),
+               Step._lv(host["v"], 0, 4), Step._lv(host["beta"], 0, 3), Step._lv(host["out"], 0, 4)]
+    step.names = ["mass_f64_soa", "mass_f64_aos", "boost_f64_soa"]
+    ms = time_loop(torch, lambda: step(stream), stream, steps, warmup)
+    res = {"value": 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "how": "the C-ABI calls given pinned host pointers: inputs read and outputs written by "
+                  "the kernels across the host link inside the timed region"}
+    return res
 
 
 # ----------------------------------------------------------------------------------------- arms
@@ -447,7 +452,7 @@ def run_gvx(args):
         "kernels": kern, "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clk,
     }
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e(torch, step, a, b, v, beta)
+        line["e2e"] = e2e(torch, gvx, a, b, v, beta)
     if rank == 0 and not args.no_cpu:
         rate, cores, tm, tb = cpu_oracle_rate(a, b, v, beta)
         line["cpu_baseline"] = {

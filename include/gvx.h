@@ -11,12 +11,15 @@
  *   - The *_bwd entry points are the adjoints (vector-Jacobian products) of the above.
  *
  * Conventions shared by every entry point
- *   Memory:  every pointer is caller-owned DEVICE memory (cudaMalloc, torch, ...) unless the
- *            name ends in _host.  The library allocates no device memory; the few calls that
- *            need scratch take a caller-provided workspace and have a *_workspace size query.
+ *   Memory:  every pointer is caller-owned memory that the GPU can address: device memory
+ *            (cudaMalloc, torch, ...), or host memory the device maps (pinned / registered
+ *            memory, and on systems with pageable-memory access any host memory) -- the kernels
+ *            then stream it over the host link, which is how host buffers are processed without
+ *            staging copies.  The library allocates no device memory; the few calls that need
+ *            scratch take a caller-provided workspace and have a *_workspace size query.
  *   Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.
  *            Every call only enqueues work on `stream` and returns without synchronising
- *            (the _host variants and gvx_device_status synchronise, as documented).
+ *            (the autotuner, graph creation and gvx_device_status synchronise, as documented).
  *   Sizes:   element counts are int64_t; n = 0 is valid and launches nothing.
  *   Errors:  arguments are validated on the host before anything is enqueued; a failed check
  *            returns its gvx_status and enqueues nothing.  GVX_ERR_CUDA means a launch or a copy

@@ -105,9 +105,45 @@ __global__ void __launch_bounds__(256) boost_kernel(Lv v, Lv beta, LvOut out, in
 // Adjoint.  grad_v = L grad_out (L symmetric: the same boost applied to grad_out).  With
 // gb = beta . grad_p, k' = dk/dgamma = gamma (gamma + 2)/(gamma + 1)^2, f = k bp + gamma E:
 //   grad_beta = gamma^3 [gb (k' bp + E) + gE (E + bp)] beta + (k gb + gamma gE) p + f grad_p.
+// In FP64, gamma, k, k' = (1 + 2 s)/(1 + s)^2 and gamma^3 (s = 1/gamma = sqrt(1 - b2)) come
+// from float-float arithmetic; the multiply-adds with v, beta and grad_out stay in FP64.
 template <typename T>
-__device__ __forceinline__ void boost_grads(V3<T> b, BoostCoef<T> c, V4<T> v, V4<T> g,
+struct BoostCoefBwd {
+  BoostCoef<T> c;
+  T kp, g3;
+};
+
+template <typename T>
+__device__ __forceinline__ BoostCoefBwd<T> boost_coef_bwd(V3<T> b) {
+  if constexpr (sizeof(T) == 8) {
+    bool ok = true;
+    ffm::ff omb = ffm::one_minus_sq3(b.x, b.y, b.z, &ok);
+    if (ok) {
+      ffm::ff s = ffm::sqrt(omb);
+      ffm::ff g = ffm::recip(s);
+      ffm::ff w = ffm::recip(ffm::add_same(ffm::make(1.0f), s));
+      ffm::ff k = ffm::mul(g, w);
+      ffm::ff kp = ffm::mul(ffm::add_same(ffm::make(1.0f), ffm::scale(s, 2.0f)), ffm::sqr(w));
+      ffm::ff g3 = ffm::mul(ffm::sqr(g), g);
+      BoostCoefBwd<T> r;
+      r.c = {ffm::to_double(ffm::renorm(g)), ffm::to_double(ffm::renorm(k)), true};
+      r.kp = ffm::to_double(ffm::renorm(kp));
+      r.g3 = ffm::to_double(ffm::renorm(g3));
+      return r;
+    }
+  }
+  BoostCoefBwd<T> r;
+  r.c = boost_coef(b);
+  T gp1 = r.c.g + (T)1;
+  r.kp = r.c.g * (r.c.g + (T)2) / (gp1 * gp1);
+  r.g3 = r.c.g * r.c.g * r.c.g;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void boost_grads(V3<T> b, BoostCoefBwd<T> cb, V4<T> v, V4<T> g,
                                             V4<T> &gv, V3<T> &gbeta) {
+  const BoostCoef<T> &c = cb.c;
   if (!c.ok) {
     const T nan = (T)NAN;
     gv = {nan, nan, nan, nan};
@@ -118,9 +154,8 @@ __device__ __forceinline__ void boost_grads(V3<T> b, BoostCoef<T> c, V4<T> v, V4
   T bp = fma(b.x, v.x, fma(b.y, v.y, b.z * v.z));
   T gb = fma(b.x, g.x, fma(b.y, g.y, b.z * g.z));
   T f = fma(c.k, bp, c.g * v.w);
-  T gp1 = c.g + (T)1;
-  T kp = c.g * (c.g + (T)2) / (gp1 * gp1);
-  T g3 = c.g * c.g * c.g;
+  T kp = cb.kp;
+  T g3 = cb.g3;
   T A = g3 * fma(gb, fma(kp, bp, v.w), g.w * (v.w + bp));
   T B = fma(c.k, gb, c.g * g.w);
   gbeta.x = fma(A, b.x, fma(B, v.x, f * g.x));
@@ -138,7 +173,7 @@ __global__ void __launch_bounds__(256) boost_bwd_kernel(Lv v, Lv beta, Lv gout, 
     V4<T> g = ld4<T, LG>(gout, i);
     V4<T> ogv;
     V3<T> ogb;
-    boost_grads(b, boost_coef(b), x, g, ogv, ogb);
+    boost_grads(b, boost_coef_bwd(b), x, g, ogv, ogb);
     st4<T, LGV>(gv, i, ogv);
     st3<T, LGB>(gbeta, i, ogb);
   }
@@ -155,7 +190,7 @@ __global__ void __launch_bounds__(kBwdThreads) boost_bwd_shared_kernel(Lv v, Lv 
                                                                        int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   V3<T> b = ld3<T, LBETA>(beta, 0);
-  BoostCoef<T> c = boost_coef(b);
+  BoostCoefBwd<T> c = boost_coef_bwd(b);
   double acc[3] = {0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     V4<T> x = ld4<T, LV>(v, i);

@@ -96,6 +96,31 @@ GVX_HD void sinhcosh_t(ff x, const TabRef &T, ff *sh, ff *ch) {
   *ch = add(mul(C, h.E), mul(S, h.O));
 }
 
+// sin(h) and cos(h) for 0 <= h <= pi/2 (+ a few ulps), relative accuracy ~2^-46 for both.
+GVX_HD void sincos_q1_t(ff h, const TabRef &T, ff *sn, ff *cs) {
+  int j;
+  float jf = round_shift(fmul(h.hi, kTrigInvD), &j);
+  if (j > GVX_TRIG_N) {
+    j = GVX_TRIG_N;
+    jf = (float)GVX_TRIG_N;
+  }
+  if (j < 0) {
+    j = 0;
+    jf = 0.0f;
+  }
+  ff r = reduce(h, jf, kTrigD0, kTrigD1, kTrigD2);
+  ff r2 = two_prod(r.hi, r.hi);
+  r2.lo = ffma(fadd(r.hi, r.hi), r.lo, r2.lo);
+  ff cr = fast_two_sum(1.0f, fmul(r2.hi, -0.5f));
+  cr.lo = fadd(cr.lo, ffma(r2.lo, -0.5f, fmul(fmul(r2.hi, r2.hi), 0.041666668f)));
+  ff sr = two_sum(r.hi, fmul(fmul(r.hi, r2.hi), -0.16666667f));
+  sr.lo = fadd(sr.lo, r.lo);
+  gvx_f4 t = T.trig[j];
+  ff sj = {t.x, t.y}, cj = {t.z, t.w};
+  *sn = add(mul(sj, cr), mul(cj, sr));
+  *cs = add(mul(cj, cr), neg(mul(sj, sr)));
+}
+
 // sin(phi) and cos(phi) for |phi| <= pi (+ a few ulps), absolute error ~2^-47: the first
 // quadrant through the table, the second through pi - |phi|.
 GVX_HD void sincos_t(double phi, const TabRef &T, ff *sn, ff *cs, bool *ok) {

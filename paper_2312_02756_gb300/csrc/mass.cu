@@ -126,6 +126,45 @@ cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaSt
   return cudaGetLastError();
 }
 
+// FP64 adjoint: float-float evaluation (mass_ff.cuh, pair_mass_grad_ff) with the FP64 formulas
+// kept for lanes outside its domain.
+template <int LA, int LB, int LGA, int LGB>
+__global__ void __launch_bounds__(256) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ gm,
+                                                           LvOut ga, LvOut gb, int64_t n) {
+  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
+  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
+  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    V4<double> x = ld4<double, LA>(a, i);
+    V4<double> y = ld4<double, LB>(b, i);
+    double g = ld_s(gm + i);
+    double o[8];
+    V4<double> g1, g2;
+    if (ffm::pair_mass_grad_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
+      g1 = {o[0], o[1], o[2], o[3]};
+      g2 = {o[4], o[5], o[6], o[7]};
+    } else {
+      Leg<double> la = make_leg(x), lb = make_leg(y);
+      PairTerms<double> t = pair_terms(la, lb);
+      double m = sqrt(t.m2);
+      g1 = {0, 0, 0, 0};
+      g2 = {0, 0, 0, 0};
+      if (m > 0.0) {
+        double scale = g / (2.0 * m);
+        double ce = sqrt(1.0 + t.se * t.se);
+        double sgn;
+        double cp = cos(half_dphi(la.phi, lb.phi, &sgn));
+        double sdeta = 2.0 * t.se * ce, sdphi = sgn * 2.0 * t.sp * cp;
+        g1 = leg_grad(la, lb, t.S, sdeta, sdphi, scale);
+        g2 = leg_grad(lb, la, t.S, -sdeta, -sdphi, scale);
+      }
+    }
+    st4<double, LGA>(ga, i, g1);
+    st4<double, LGB>(gb, i, g2);
+  }
+}
+
 template <typename T>
 cudaError_t launch_mass_t(const Lv &a, const Lv &b, void *m, int64_t n, cudaStream_t s) {
   const int threads = 256;
@@ -142,17 +181,31 @@ cudaError_t launch_mass_t(const Lv &a, const Lv &b, void *m, int64_t n, cudaStre
   return cudaGetLastError();
 }
 
+template <typename T, int LA, int LB, int LGA, int LGB>
+void launch_bwd_one(unsigned grid, int threads, const Lv &a, const Lv &b, const T *gm,
+                    const LvOut &ga, const LvOut &gb, int64_t n, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    static int occ[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    unsigned g = resident_grid(mass_bwd_f64_kernel<LA, LB, LGA, LGB>, threads, 0, n, &occ[dev & 63]);
+    mass_bwd_f64_kernel<LA, LB, LGA, LGB><<<g, threads, 0, s>>>(a, b, gm, ga, gb, n);
+  } else {
+    mass_bwd_kernel<T, LA, LB, LGA, LGB><<<grid, threads, 0, s>>>(a, b, gm, ga, gb, n);
+  }
+}
+
 template <typename T, int LA, int LB>
 void launch_bwd_out(unsigned grid, int threads, const Lv &a, const Lv &b, const T *gm,
                     const LvOut &ga, const LvOut &gb, int64_t n, cudaStream_t s) {
   if (ga.layout == GVX_SOA && gb.layout == GVX_SOA)
-    mass_bwd_kernel<T, LA, LB, GVX_SOA, GVX_SOA><<<grid, threads, 0, s>>>(a, b, gm, ga, gb, n);
+    launch_bwd_one<T, LA, LB, GVX_SOA, GVX_SOA>(grid, threads, a, b, gm, ga, gb, n, s);
   else if (ga.layout == GVX_SOA)
-    mass_bwd_kernel<T, LA, LB, GVX_SOA, GVX_AOS><<<grid, threads, 0, s>>>(a, b, gm, ga, gb, n);
+    launch_bwd_one<T, LA, LB, GVX_SOA, GVX_AOS>(grid, threads, a, b, gm, ga, gb, n, s);
   else if (gb.layout == GVX_SOA)
-    mass_bwd_kernel<T, LA, LB, GVX_AOS, GVX_SOA><<<grid, threads, 0, s>>>(a, b, gm, ga, gb, n);
+    launch_bwd_one<T, LA, LB, GVX_AOS, GVX_SOA>(grid, threads, a, b, gm, ga, gb, n, s);
   else
-    mass_bwd_kernel<T, LA, LB, GVX_AOS, GVX_AOS><<<grid, threads, 0, s>>>(a, b, gm, ga, gb, n);
+    launch_bwd_one<T, LA, LB, GVX_AOS, GVX_AOS>(grid, threads, a, b, gm, ga, gb, n, s);
 }
 
 template <typename T>

@@ -63,14 +63,17 @@ GVX_HD bool mass_ff_domain(double pt1, double eta1, double phi1, double m1, doub
 // Half of the azimuthal difference reduced to [0, pi/2], for sin^2 of it.  d = phi1 - phi2 in
 // FP64 is exact where it can cancel (Sterbenz); for |d| > pi the half-angle comes from
 // y = (pi_d - |phi1|) + (pi_d - |phi2|) + 2 (pi - pi_d), whose brackets are exact FP64
-// differences (|phi| >= pi/2 there) or sums without cancellation.
-GVX_HD ff half_dphi_ff(double phi1, double phi2, bool *ok) {
-  double d = phi1 - phi2;
-  if (within_pi(d)) return scale(from_double(fabs(d), ok), 0.5f);
+// differences (|phi| >= pi/2 there) and whose sum has no cancellation.  Both candidates are
+// formed and one is selected (no divergent branch); *wrapped tells which.
+GVX_HD ff half_dphi_ff(double phi1, double phi2, bool *ok, bool *wrapped = nullptr) {
+  const double d = fabs(phi1 - phi2);
   const double pid = hilo2d(kPiHiWord, kPiLoWord);
-  ff y = add_same(from_double(pid - fabs(phi1), ok), from_double(pid - fabs(phi2), ok));
-  y = add_small(y, make(kTwoPiLo));
-  return scale(y, 0.5f);
+  const double y = (pid - fabs(phi1)) + (pid - fabs(phi2));
+  const bool w = !within_pi(d);
+  if (wrapped) *wrapped = w;
+  ff h = from_double(w ? y : d, ok);
+  h = add_small(h, make(w ? kTwoPiLo : 0.0f));
+  return scale(h, 0.5f);
 }
 
 // One leg in ff, pt and m scaled by 2^-s: pt, P = pt cosh(eta), q = m^2, E2 = P^2 + q.
@@ -118,6 +121,91 @@ GVX_HD bool pair_mass_ff(double pt1, double eta1, double phi1, double m1, double
   LegFF a = make_leg_ff(pt1, eta1, m1, s, T, &ok);
   LegFF b = make_leg_ff(pt2, eta2, m2, s, T, &ok);
   return finish_mass(pair_m2_ff(a, b, eta1, eta2, phi1, phi2, T, &ok), s, ok, out);
+}
+
+// Gradient of the pair mass, gm * dm/d(pt, eta, phi, m) of both legs, in ff.  With the scaled
+// legs, S = sinh^2(d_eta/2) + sin^2(d_phi/2) and
+//   X_s = (P_s^2 m_o^2 - P_o^2 m_s^2) / ((P_s E_o + P_o E_s) E_s)       (= P_s E_o/E_s - P_o)
+// the derivatives of m^2 for leg s (o = the other leg) are
+//   d/dpt_s = 4 pt_o S + 2 cosh(eta_s) X_s,      d/deta_s = 2 pt_s (pt_o sinh(d_eta_so) + sinh(eta_s) X_s),
+//   d/dphi_s = 2 pt_s pt_o sin(d_phi_so),         d/dm_s = 2 m_s (E_s + E_o) / E_s,
+// and dm = d(m^2) / (2 m).  Readings as in the FP64 kernel: zero where m = 0; for a leg with
+// E_s = 0 the one-sided limit X_s = m_o^2 / (E_o + P_o); X_s = 0 where its denominator vanishes.
+// Returns false outside the fast-path domain (the caller then uses the FP64 evaluation).
+struct LegGradFF {
+  ff pt, q, m, P, E2, E, sh, ch;
+};
+
+GVX_HD LegGradFF leg_grad_prep(double pt, double eta, double m, int s, const TabRef &T, bool *ok) {
+  LegGradFF l;
+  l.pt = from_double(pt, ok, s);
+  l.m = from_double(m, ok, s);
+  l.q = sqr(l.m);
+  sinhcosh_t(from_double(eta, ok), T, &l.sh, &l.ch);
+  l.P = mul(l.pt, l.ch);
+  l.E2 = add_same(sqr(l.P), l.q);
+  l.E = sqrt(l.E2);
+  return l;
+}
+
+GVX_HD ff leg_x(const LegGradFF &s, const LegGradFF &o) {
+  if (s.E.hi > 0.0f) {
+    ff den = mul(add_same(mul(s.P, o.E), mul(o.P, s.E)), s.E);
+    if (!(den.hi > 0.0f)) return make(0.0f);
+    return div(add(mul(sqr(s.P), o.q), neg(mul(sqr(o.P), s.q))), den);
+  }
+  ff eo = add_same(o.E, o.P);
+  return eo.hi > 0.0f ? div(o.q, eo) : make(0.0f);
+}
+
+// out[0..3] leg a (pt, eta, phi, m), out[4..7] leg b.
+GVX_HD bool pair_mass_grad_ff(double pt1, double eta1, double phi1, double m1, double pt2,
+                              double eta2, double phi2, double m2, double gm, const TabRef &T,
+                              double *out) {
+  int s;
+  if (!mass_ff_domain(pt1, eta1, phi1, m1, pt2, eta2, phi2, m2, &s)) return false;
+  bool ok = true;
+  LegGradFF a = leg_grad_prep(pt1, eta1, m1, s, T, &ok);
+  LegGradFF b = leg_grad_prep(pt2, eta2, m2, s, T, &ok);
+  ff den = add_same(mul(a.E, b.E), mul(a.P, b.P));
+  ff num = add_same(mul(a.q, b.E2), mul(b.q, sqr(a.P)));
+  ff tm = den.hi > 0.0f ? scale(div(num, den), 2.0f) : make(0.0f);
+  ff se, ce;
+  sinhcosh_t(scale(from_double(eta1 - eta2, &ok), 0.5f), T, &se, &ce);
+  bool wrapped;
+  ff sp, cp;
+  sincos_q1_t(half_dphi_ff(phi1, phi2, &ok, &wrapped), T, &sp, &cp);
+  ff S = add_same(sqr(se), sqr(sp));
+  ff m2s = renorm(add_same(add_same(add_same(a.q, b.q), tm), scale(mul(mul(a.pt, b.pt), S), 4.0f)));
+  if (!ok || (m2s.hi < 8.27180613e-25f && m2s.hi != 0.0f)) return false;  // 2^-80
+  if (!(m2s.hi > 0.0f)) {
+    for (int k = 0; k < 8; k++) out[k] = 0.0;
+    return true;
+  }
+  ff g = from_double(gm, &ok);
+  if (!ok) return false;
+  ff c = div(g, scale(sqrt(m2s), 2.0f));  // gm / (2 m), scaled by 2^s
+  // sinh(d_eta) = 2 sinh(d_eta/2) cosh(d_eta/2);  sin(d_phi) = +-2 sin(h) cos(h), with the sign
+  // of phi1 - phi2 and reversed for the wrapped half-angle
+  ff sdeta = scale(mul(se, ce), 2.0f);
+  ff sdphi = scale(mul(sp, cp), 2.0f);
+  const bool dneg = (phi1 - phi2) < 0.0;
+  if (dneg != wrapped) sdphi = neg(sdphi);
+  const LegGradFF *L[2] = {&a, &b};
+  for (int l = 0; l < 2; l++) {
+    const LegGradFF &x = *L[l], &o = *L[1 - l];
+    ff sde = l == 0 ? sdeta : neg(sdeta), sdp = l == 0 ? sdphi : neg(sdphi);
+    ff X = leg_x(x, o);
+    ff d_pt = add(scale(mul(o.pt, S), 4.0f), scale(mul(x.ch, X), 2.0f));
+    ff d_eta = scale(mul(x.pt, add(mul(o.pt, sde), mul(x.sh, X))), 2.0f);
+    ff d_phi = scale(mul(mul(x.pt, o.pt), sdp), 2.0f);
+    ff d_m = x.E.hi > 0.0f ? scale(div(mul(x.m, add_same(x.E, o.E)), x.E), 2.0f) : make(0.0f);
+    out[4 * l + 0] = to_double(renorm(mul(c, d_pt)));
+    out[4 * l + 1] = to_double(renorm(mul(c, d_eta)), s);
+    out[4 * l + 2] = to_double(renorm(mul(c, d_phi)), s);
+    out[4 * l + 3] = to_double(renorm(mul(c, d_m)));
+  }
+  return true;
 }
 
 }  // namespace ffm

@@ -25,6 +25,24 @@ int64_t ffh_mass(const double *a, const double *b, int64_t n, double *m, uint8_t
   return c;
 }
 
+int64_t ffh_mass_grad(const double *a, const double *b, const double *gm, int64_t n, double *ga,
+                      double *gb, uint8_t *ok) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = a + 4 * i, *y = b + 4 * i;
+    double out[8];
+    bool f = pair_mass_grad_ff(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], gm[i], tables(),
+                               out);
+    ok[i] = f;
+    for (int k = 0; k < 4; k++) {
+      ga[4 * i + k] = f ? out[k] : NAN;
+      gb[4 * i + k] = f ? out[4 + k] : NAN;
+    }
+    c += f;
+  }
+  return c;
+}
+
 // op: 0 cosh, 1 sinh, 2 sin_q1, 3 round trip double -> ff -> double, 4 sqrt, 5 sqr
 void ffh_unary(int op, const double *x, int64_t n, double *out, uint8_t *ok) {
   for (int64_t i = 0; i < n; i++) {
