@@ -472,13 +472,25 @@ def run_gvx(args):
     return 0
 
 
+def _csrc_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2312_02756_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _profile_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one exists for the
-    current kernel build (profiles/traffic.json, written by hand from an ncu capture)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.json),
+    only while the kernel sources are the ones the counters were taken from."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
+        return None
+    if data.get("csrc_hash") != _csrc_hash():
         return None
     entry = data.get(kernel)
     return entry.get("bytes_per_launch") if isinstance(entry, dict) else None
