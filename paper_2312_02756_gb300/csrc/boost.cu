@@ -2,17 +2,19 @@
 // 4x4 Lorentz matrix to every vector of an array).
 //
 // The symmetric matrix L(beta) is applied without being formed:
-//   gamma = 1/sqrt(1 - b2),  k = (gamma - 1)/b2 = gamma^2/(1 + gamma),  bp = beta.p,
-//   E' = gamma (E + bp),      p' = p + (k bp + gamma E) beta.
-// 1 - b2 is formed from exact squares (fma) and error-free sums, so gamma keeps the working
-// precision as |beta| -> 1 instead of losing log10(1/(1 - b2)) digits.
+//   gamma = 1/sqrt(1 - b2),  bp = beta.p,  E' = gamma (E + bp),
+//   p' = p + f beta,  f = k bp + gamma E = E' - w bp,   k = gamma^2/(1 + gamma),  w = gamma/(1 + gamma).
+// The form f = E' - w bp keeps gamma out of the part of f that cancels when a vector is boosted
+// towards its rest frame (p' -> 0): an error in gamma then scales E' only, and only w's error is
+// amplified.  1 - b2 is formed from exact squares and error-free sums, so gamma keeps the
+// working precision as |beta| -> 1 instead of losing log10(1/(1 - b2)) digits.
 //
-// FP64: gamma and k come from float-float arithmetic on the FP32 pipe (1 - b2 exactly in 64-bit
-// fixed point, then sqrt and two reciprocals), and only the ten multiply-adds that combine
-// them with the vector run on the FP64 pipe: those sums cancel when a vector is boosted towards
-// its rest frame, and keep FP64 rounding there.
+// FP64: the fast path (boost_ff.cuh) forms gamma and f = k (E + bp) + w E in float-float on the
+// FP32 pipe and keeps seven FP64 operations per vector; vectors outside its domain take the FP64
+// evaluation below, with the compensated 1 - b2.
 #include <cuda_runtime.h>
 
+#include "boost_ff.cuh"
 #include "common.cuh"
 #include "ff.cuh"
 
@@ -43,7 +45,7 @@ __device__ __forceinline__ float rsqrt_(float x) { return 1.0f / sqrtf(x); }
 
 template <typename T>
 struct BoostCoef {
-  T g, k;
+  T g, w;
   bool ok;
 };
 
@@ -53,7 +55,7 @@ __device__ __forceinline__ BoostCoef<T> boost_coef(V3<T> b) {
   T omb = one_minus_b2(b);
   c.ok = omb > (T)0;
   c.g = rsqrt_(omb);
-  c.k = c.g * c.g / ((T)1 + c.g);
+  c.w = c.g / ((T)1 + c.g);
   return c;
 }
 
@@ -64,41 +66,55 @@ __device__ __forceinline__ V4<T> apply_boost(V3<T> b, BoostCoef<T> c, V4<T> v) {
     return {nan, nan, nan, nan};
   }
   T bp = fma(b.x, v.x, fma(b.y, v.y, b.z * v.z));
-  T f = fma(c.k, bp, c.g * v.w);
-  return {fma(f, b.x, v.x), fma(f, b.y, v.y), fma(f, b.z, v.z), c.g * (v.w + bp)};
-}
-
-// gamma = 1/s and k = gamma^2/(1 + gamma) = gamma/(1 + s), s = sqrt(1 - b2), in ff; the FP64
-// compensated evaluation outside the fast-path range |beta| <= 0.99998.
-template <typename T>
-__device__ __forceinline__ BoostCoef<T> boost_coef_fast(V3<T> b) {
-  if constexpr (sizeof(T) == 8) {
-    bool ok = true;
-    ffm::ff omb = ffm::one_minus_sq3(b.x, b.y, b.z, &ok);
-    if (ok) {
-      ffm::ff s = ffm::sqrt(omb);
-      ffm::ff g = ffm::recip(s);
-      ffm::ff k = ffm::mul(g, ffm::recip(ffm::add_same(ffm::make(1.0f), s)));
-      return {ffm::to_double(g), ffm::to_double(k), true};
-    }
-  }
-  return boost_coef(b);
+  T ep = c.g * (v.w + bp);
+  T f = fma(-c.w, bp, ep);
+  return {fma(f, b.x, v.x), fma(f, b.y, v.y), fma(f, b.z, v.z), ep};
 }
 
 template <typename T, int LV, int LBETA, int LOUT, bool SHARED>
 __global__ void __launch_bounds__(256) boost_kernel(Lv v, Lv beta, LvOut out, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   V3<T> b0;
-  BoostCoef<T> c0;
-  if (SHARED) {
-    b0 = ld3<T, LBETA>(beta, 0);
-    c0 = boost_coef_fast(b0);
-  }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    V4<T> x = ld4<T, LV>(v, i);
-    V3<T> b = SHARED ? b0 : ld3<T, LBETA>(beta, i);
-    BoostCoef<T> c = SHARED ? c0 : boost_coef_fast(b);
-    st4<T, LOUT>(out, i, apply_boost(b, c, x));
+  if (SHARED) b0 = ld3<T, LBETA>(beta, 0);
+  if constexpr (sizeof(T) == 8) {
+    ffm::BetaFF B0;
+    if (SHARED) B0 = ffm::beta_ff(b0.x, b0.y, b0.z);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      V4<T> x = ld4<T, LV>(v, i);
+      V3<T> b = SHARED ? b0 : ld3<T, LBETA>(beta, i);
+      const ffm::BetaFF B = SHARED ? B0 : ffm::beta_ff(b.x, b.y, b.z);
+      double o[4];
+      V4<T> r;
+      if (ffm::boost_ff(B, b.x, b.y, b.z, x.x, x.y, x.z, x.w, o))
+        r = {o[0], o[1], o[2], o[3]};
+      else
+        r = apply_boost(b, boost_coef(b), x);
+      st4<T, LOUT>(out, i, r);
+    }
+  } else {
+    // FP32: memory-bound, so each thread loads kUnroll vectors (strided by the grid) before it
+    // computes any of them, to keep more loads in flight per SM.
+    constexpr int kUnroll = 4;
+    BoostCoef<T> c0;
+    if (SHARED) c0 = boost_coef(b0);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kUnroll - 1) * stride < n; i += kUnroll * stride) {
+      V4<T> x[kUnroll];
+      V3<T> b[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; u++) {
+        x[u] = ld4<T, LV>(v, i + u * stride);
+        b[u] = SHARED ? b0 : ld3<T, LBETA>(beta, i + u * stride);
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; u++)
+        st4<T, LOUT>(out, i + u * stride, apply_boost(b[u], SHARED ? c0 : boost_coef(b[u]), x[u]));
+    }
+    for (; i < n; i += stride) {
+      V4<T> x = ld4<T, LV>(v, i);
+      V3<T> b = SHARED ? b0 : ld3<T, LBETA>(beta, i);
+      st4<T, LOUT>(out, i, apply_boost(b, SHARED ? c0 : boost_coef(b), x));
+    }
   }
 }
 
@@ -110,7 +126,7 @@ __global__ void __launch_bounds__(256) boost_kernel(Lv v, Lv beta, LvOut out, in
 template <typename T>
 struct BoostCoefBwd {
   BoostCoef<T> c;
-  T kp, g3;
+  T k, kp, g3;
 };
 
 template <typename T>
@@ -126,7 +142,8 @@ __device__ __forceinline__ BoostCoefBwd<T> boost_coef_bwd(V3<T> b) {
       ffm::ff kp = ffm::mul(ffm::add_same(ffm::make(1.0f), ffm::scale(s, 2.0f)), ffm::sqr(w));
       ffm::ff g3 = ffm::mul(ffm::sqr(g), g);
       BoostCoefBwd<T> r;
-      r.c = {ffm::to_double(ffm::renorm(g)), ffm::to_double(ffm::renorm(k)), true};
+      r.c = {ffm::to_double(ffm::renorm(g)), ffm::to_double(ffm::renorm(w)), true};
+      r.k = ffm::to_double(ffm::renorm(k));
       r.kp = ffm::to_double(ffm::renorm(kp));
       r.g3 = ffm::to_double(ffm::renorm(g3));
       return r;
@@ -134,6 +151,7 @@ __device__ __forceinline__ BoostCoefBwd<T> boost_coef_bwd(V3<T> b) {
   }
   BoostCoefBwd<T> r;
   r.c = boost_coef(b);
+  r.k = r.c.g * r.c.w;
   T gp1 = r.c.g + (T)1;
   r.kp = r.c.g * (r.c.g + (T)2) / (gp1 * gp1);
   r.g3 = r.c.g * r.c.g * r.c.g;
@@ -153,11 +171,11 @@ __device__ __forceinline__ void boost_grads(V3<T> b, BoostCoefBwd<T> cb, V4<T> v
   gv = apply_boost(b, c, g);
   T bp = fma(b.x, v.x, fma(b.y, v.y, b.z * v.z));
   T gb = fma(b.x, g.x, fma(b.y, g.y, b.z * g.z));
-  T f = fma(c.k, bp, c.g * v.w);
+  T f = fma(-c.w, bp, c.g * (v.w + bp));
   T kp = cb.kp;
   T g3 = cb.g3;
   T A = g3 * fma(gb, fma(kp, bp, v.w), g.w * (v.w + bp));
-  T B = fma(c.k, gb, c.g * g.w);
+  T B = fma(cb.k, gb, c.g * g.w);
   gbeta.x = fma(A, b.x, fma(B, v.x, f * g.x));
   gbeta.y = fma(A, b.y, fma(B, v.y, f * g.y));
   gbeta.z = fma(A, b.z, fma(B, v.z, f * g.z));

@@ -271,6 +271,23 @@ GVX_HD ff from_double(double d, bool *ok, int shift = 0) {
   return {u2f(hib), sign ? -lo : lo};
 }
 
+// from_double without the range checks, for a d whose scaled magnitude is known to be below
+// 2^126: zeros, denormals and values that scale below 2^-74 give a signed zero.  Bitwise the same
+// result as from_double wherever that leaves *ok set.
+GVX_HD ff from_double_ranged(double d, int shift) {
+  uint32_t wh = dhi(d), wl = dlo(d);
+  uint32_t sign = wh & 0x80000000u;
+  int e = (int)((wh >> 20) & 0x7ffu);
+  int ef = e - 896 - shift;
+  uint32_t top = ((wh & 0xfffffu) << 3) | (wl >> 29);
+  uint32_t rbit = (wl >> 28) & 1u;
+  uint32_t hib = (sign | ((uint32_t)ef << 23) | top) + rbit;
+  int32_t rem = (int32_t)(wl & 0x1fffffffu) - (int32_t)(rbit << 29);
+  float lo = fmul(i2f(rem), pow2f(ef - 179));
+  ff r = {u2f(hib), sign ? -lo : lo};
+  return (e != 0 && ef >= 53) ? r : ff{u2f(sign), 0.0f};
+}
+
 // Biased exponent field of a double (0 for zero and denormals).
 GVX_HD int dexp(double d) { return (int)((dhi(d) >> 20) & 0x7ffu); }
 
@@ -287,6 +304,33 @@ GVX_HD double f2d_bits(float f, int shift = 0) {
 // ff * 2^shift -> double: one rounding (one FP64 add).
 GVX_HD double to_double(ff x, int shift = 0) {
   return f2d_bits(x.hi, shift) + f2d_bits(x.lo, shift);
+}
+
+// ff * 2^shift -> double with integer operations only (no FP64 instruction): the exact sum
+// hi + lo truncated to 53 bits, an error below 2 ulps of the result.  Requires hi normal or 0,
+// |lo| <= 2^-21 |hi| (true of every normalized ff: add, renorm, recip, sqrt), and a result
+// inside the normal range of double.  A denormal lo counts as 0.
+GVX_HD double to_double_int(ff x, int shift) {
+  const uint32_t uh = f2u(x.hi), ul = f2u(x.lo);
+  const int eh = (int)((uh >> 23) & 0xffu), el = (int)((ul >> 23) & 0xffu);
+  const uint32_t mh = (uh & 0x7fffffu) | 0x800000u;
+  const uint32_t ml = el ? ((ul & 0x7fffffu) | 0x800000u) : 0u;
+  // lo in units of ulp(hi as a double) = 2^-29 ulp(hi as a float); |L| < 2^32
+  const int sft = el - eh + 29;
+  const uint32_t L = sft >= 0 ? ml << sft : (sft > -24 ? ml >> -sft : 0u);
+  const uint64_t M = (uint64_t)mh << 29;
+  uint64_t S = ((uh ^ ul) >> 31) ? M - L : M + L;  // in (2^52 - 2^32, 2^53 + 2^32)
+  int ed = eh + 896 + shift;
+  if (S >> 53) {
+    S >>= 1;
+    ed += 1;
+  } else if (!(S >> 52)) {
+    S <<= 1;
+    ed -= 1;
+  }
+  const uint64_t bits = ((uint64_t)(uh >> 31) << 63) | ((uint64_t)ed << 52) |
+                        (S & 0xfffffffffffffull);
+  return eh ? u2d(bits) : f2d_bits(x.lo, shift);
 }
 
 // Non-negative integer D times 2^p as ff (D < 2^63), rounding only in lo.
@@ -321,7 +365,7 @@ GVX_HD uint64_t umulhi64(uint64_t a, uint64_t b) {
 
 // 1 - (bx^2 + by^2 + bz^2) for doubles with |b| < 1, in 64-bit fixed point (unit 2^-62): each
 // square is the top 64 bits of the 106-bit square of the significand, truncated, so the result
-// is exact to 3 * 2^-62.  *ok is cleared when the result is below 2^-16 (|beta| > 0.99998) or
+// is exact to 3 * 2^-62.  *ok is cleared when the result is below 2^-16 (|beta| > 0.9999924) or
 // any component is not finite / not below 1 in magnitude.
 GVX_HD ff one_minus_sq3(double bx, double by, double bz, bool *ok) {
   const double c[3] = {bx, by, bz};

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
         int emax = 0;
         for (int k = k0; k < k1; k++) emax = s_sc[k] > emax ? s_sc[k] : emax;
         for (int k = k0; k < k1; k++) {
-          bool fast = emax > 0 && emax < 0x7ff &&
+          bool fast = ffm::scale_exponent_ok(emax) &&
                       ffm::leg_in_domain(s_px[k], s_eta[k], s_phi[k], s_py[k], emax);
           s_sc[k] = fast ? emax - 1023 : kNoFast;
         }
@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
         bool ok = true;
         if (sc != kNoFast) {
           ffm::LegFF l;
-          l.pt = ffm::from_double(pt, &ok, sc);
-          l.q = ffm::sqr(ffm::from_double(m, &ok, sc));
+          l.pt = ffm::from_double_ranged(pt, sc);
+          l.q = ffm::sqr(ffm::from_double_ranged(m, sc));
           ffm::ff sn, cs;
           const ffm::ff eta_f = ffm::from_double(eta, &ok);
           const ffm::ff sh = ffm::sinh_t(eta_f, T);

@@ -20,10 +20,26 @@
 namespace gvx {
 namespace {
 
+// FP32: memory-bound, so each thread loads kUnroll pairs (strided by the grid) before it
+// computes any of them, to keep more loads in flight per SM.
+constexpr int kUnroll = 4;
+
 template <typename T, int LA, int LB>
 __global__ void __launch_bounds__(256) mass_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * stride < n; i += kUnroll * stride) {
+    V4<T> x[kUnroll], y[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      x[u] = ld4<T, LA>(a, i + u * stride);
+      y[u] = ld4<T, LB>(b, i + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++)
+      st_s(m + i + u * stride, sqrt_(pair_terms(make_leg(x[u]), make_leg(y[u])).m2));
+  }
+  for (; i < n; i += stride) {
     Leg<T> la = make_leg(ld4<T, LA>(a, i));
     Leg<T> lb = make_leg(ld4<T, LB>(b, i));
     st_s(m + i, sqrt_(pair_terms(la, lb).m2));

@@ -10,8 +10,9 @@
 //
 // Domain of the fast path (anything else returns false and the caller uses the FP64 path):
 // finite inputs, pt >= 0, |eta| < 16, |phi| <= pi (rounded to double), and pt and m, scaled by
-// the power of two 2^-s that brings the largest of them into [1, 2), either 0 or >= 2^-30; the
-// scaled m^2 must come out >= 2^-80 (or exactly 0).  Over that domain every intermediate that
+// the power of two 2^-s that brings the largest of them into [1, 2), either 0 or >= 2^-30 (the
+// largest above 2^-993, so no denormal passes); the scaled m^2 must come out >= 2^-80 (or
+// exactly 0).  Over that domain every intermediate that
 // matters stays inside the normal float range (E^2 <= 2^47, products >= 2^-120), and anything
 // flushed to zero is below 2^-46 of the result.
 #pragma once
@@ -37,14 +38,22 @@ GVX_HD int leg_exponent(double pt, double m) {
   return e1 > e3 ? e1 : e3;
 }
 
-// Whether one leg is inside the fast-path domain for the scale exponent emax (biased).
+// Whether a scale exponent (biased) admits the fast path: not all zero, finite, and large enough
+// (> 2^-993) that a nonzero denormal pt or m always fails the 2^-30 test below.
+GVX_HD bool scale_exponent_ok(int emax) { return emax > 30 && emax < 0x7ff; }
+
+// Whether one leg is inside the fast-path domain for the scale exponent emax (biased, passing
+// scale_exponent_ok).  pt and m are then 0 or scaled into [2^-30, 2), so they convert to ff with
+// from_double_ranged.
 GVX_HD bool leg_in_domain(double pt, double eta, double phi, double m, int emax) {
   if (dhi(pt) >> 31) return false;                              // pt < 0 (or -0)
   if (((dhi(eta) >> 20) & 0x7ffu) > 1026u) return false;        // |eta| >= 16, NaN, Inf
   if (!within_pi(phi)) return false;                            // |phi| > pi, NaN
   int ep = dexp(pt), em = dexp(m);
   if (ep >= 0x7ff || em >= 0x7ff) return false;                 // Inf/NaN
-  if ((ep && emax - ep > 30) || (em && emax - em > 30)) return false;
+  const bool pt_nz = (dhi(pt) | dlo(pt)) != 0u;
+  const bool m_nz = ((dhi(m) & 0x7fffffffu) | dlo(m)) != 0u;
+  if ((pt_nz && emax - ep > 30) || (m_nz && emax - em > 30)) return false;
   return true;
 }
 
@@ -53,7 +62,7 @@ GVX_HD bool mass_ff_domain(double pt1, double eta1, double phi1, double m1, doub
                            double phi2, double m2, int *s) {
   int ea = leg_exponent(pt1, m1), eb = leg_exponent(pt2, m2);
   int emax = ea > eb ? ea : eb;
-  if (emax == 0 || emax >= 0x7ff) return false;  // all zero, or Inf/NaN
+  if (!scale_exponent_ok(emax)) return false;  // all zero, tiny, or Inf/NaN
   if (!leg_in_domain(pt1, eta1, phi1, m1, emax) || !leg_in_domain(pt2, eta2, phi2, m2, emax))
     return false;
   *s = emax - 1023;
@@ -83,8 +92,8 @@ struct LegFF {
 
 GVX_HD LegFF make_leg_ff(double pt, double eta, double m, int s, const TabRef &T, bool *ok) {
   LegFF l;
-  l.pt = from_double(pt, ok, s);
-  l.q = sqr(from_double(m, ok, s));
+  l.pt = from_double_ranged(pt, s);
+  l.q = sqr(from_double_ranged(m, s));
   l.P = mul(l.pt, cosh_t(from_double(eta, ok), T));
   l.E2 = add_same(sqr(l.P), l.q);
   return l;
@@ -138,8 +147,8 @@ struct LegGradFF {
 
 GVX_HD LegGradFF leg_grad_prep(double pt, double eta, double m, int s, const TabRef &T, bool *ok) {
   LegGradFF l;
-  l.pt = from_double(pt, ok, s);
-  l.m = from_double(m, ok, s);
+  l.pt = from_double_ranged(pt, s);
+  l.m = from_double_ranged(m, s);
   l.q = sqr(l.m);
   sinhcosh_t(from_double(eta, ok), T, &l.sh, &l.ch);
   l.P = mul(l.pt, l.ch);

@@ -5,6 +5,7 @@
 
 #include "../paper_2312_02756_gb300/csrc/ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_ff.cuh"
+#include "../paper_2312_02756_gb300/csrc/boost_ff.cuh"
 
 using namespace gvx::ffm;
 
@@ -62,18 +63,57 @@ void ffh_unary(int op, const double *x, int64_t n, double *out, uint8_t *ok) {
   }
 }
 
-// gamma = 1/sqrt(1 - b2) and k = gamma^2/(1 + gamma) as the FP64 boost computes them.
-void ffh_boost_coef(const double *beta, int64_t n, double *g, double *k, uint8_t *ok) {
+// gamma = 1/sqrt(1 - b2) and w = gamma/(1 + gamma) as the FP64 boost computes them.
+void ffh_boost_coef(const double *beta, int64_t n, double *g, double *w, uint8_t *ok) {
   for (int64_t i = 0; i < n; i++) {
     bool f = true;
     ff omb = one_minus_sq3(beta[3 * i], beta[3 * i + 1], beta[3 * i + 2], &f);
     ff s = sqrt(omb);
     ff gg = recip(s);
-    ff kk = mul(gg, recip(add_same(make(1.0f), s)));
+    ff ww = recip(add_same(make(1.0f), s));
     g[i] = to_double(gg);
-    k[i] = to_double(kk);
+    w[i] = to_double(ww);
     ok[i] = f;
   }
+}
+
+// from_double_ranged(x, shift) as (hi, lo) doubles, with same[i] = 1 where it is bitwise
+// from_double(x, shift), 0 where it differs, 2 where from_double rejects x.
+void ffh_conv_ranged(const double *x, int64_t n, int shift, double *hi, double *lo,
+                     uint8_t *same) {
+  for (int64_t i = 0; i < n; i++) {
+    bool f = true;
+    ff a = from_double(x[i], &f, shift);
+    ff b = from_double_ranged(x[i], shift);
+    hi[i] = b.hi;
+    lo[i] = b.lo;
+    uint32_t ah = f2u(a.hi), al = f2u(a.lo), bh = f2u(b.hi), bl = f2u(b.lo);
+    same[i] = !f ? 2 : (ah == bh && al == bl) ? 1 : 0;
+  }
+}
+
+// to_double_int and the FP64-add conversion to_double of the ff values (hi[i], lo[i]) * 2^shift.
+void ffh_to_double(const float *hi, const float *lo, int64_t n, int shift, double *out_int,
+                   double *out_add) {
+  for (int64_t i = 0; i < n; i++) {
+    out_int[i] = to_double_int(ff{hi[i], lo[i]}, shift);
+    out_add[i] = to_double(ff{hi[i], lo[i]}, shift);
+  }
+}
+
+// The FP64 boost's fast path: v (n, 4) PxPyPzE, beta (n, 3) -> out (n, 4), ok[i] = in domain.
+int64_t ffh_boost(const double *v, const double *beta, int64_t n, double *out, uint8_t *ok) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = v + 4 * i, *b = beta + 3 * i;
+    const BetaFF B = beta_ff(b[0], b[1], b[2]);
+    bool f = boost_ff(B, b[0], b[1], b[2], x[0], x[1], x[2], x[3], out + 4 * i);
+    if (!f)
+      for (int k = 0; k < 4; k++) out[4 * i + k] = NAN;
+    ok[i] = f;
+    c += f;
+  }
+  return c;
 }
 
 // op: 0 exact difference, 1 mul, 2 div, 3 add

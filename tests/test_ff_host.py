@@ -25,6 +25,7 @@ def ffh(tmp_path_factory):
                    check=True)
     lib = ctypes.CDLL(out)
     lib.ffh_mass.restype = ctypes.c_int64
+    lib.ffh_boost.restype = ctypes.c_int64
     return lib
 
 
@@ -114,21 +115,129 @@ def test_ff_pair_mass_against_oracle(ffh, orc):
             assert ok.mean() > 0.998, k  # the fast path covers the collider-like workloads
 
 
+def test_ff_unchecked_conversion_and_tiny_legs(ffh):
+    """pt and m (and the boost's inputs) enter the ff paths through the unchecked conversion:
+    bitwise the checked one on every value that one accepts, a signed zero for zeros, denormals
+    and values that scale below 2^-74.  The mass domain keeps out nonzero denormals and scale
+    exponents at or below 2^-993; exact zeros stay in."""
+    g = syn.rng(11)
+    x = np.concatenate([np.ldexp(g.uniform(1, 2, 20000), g.integers(-80, 1, 20000)),
+                        [0.0, -0.0, 1.0, 2.0 - 2.0 ** -52, 2.0 ** -30, 2.0 ** -74,
+                         2.0 ** -75 * (2 - 2.0 ** -52), 1.0 - 2.0 ** -53, 1.0 + 2.0 ** -29]])
+    x[::2] *= -1
+    for shift in (-940, -3, 0, 7, 1000):
+        xs = np.ldexp(x, shift)
+        hi, lo, same = np.empty(len(xs)), np.empty(len(xs)), np.empty(len(xs), np.uint8)
+        ffh.ffh_conv_ranged(_p(xs), ctypes.c_int64(len(xs)), shift, _p(hi), _p(lo), _p(same))
+        small = np.abs(x) < 2.0 ** -74
+        assert np.all(same[~small | (x == 0)] == 1), shift
+        assert np.all(same[small & (x != 0)] == 2), shift
+        assert np.all((hi[small] == 0) & (lo[small] == 0)), shift
+        assert np.array_equal(np.signbit(hi[small]), np.signbit(xs[small])), shift
+    ffh.ffh_conv_ranged(_p(np.array([5e-324])), ctypes.c_int64(1), 0, _p(hi), _p(lo), _p(same))
+    assert hi[0] == 0.0 and lo[0] == 0.0 and same[0] == 2
+    den = 5e-324
+    a = np.array([[den, 0.1, 0.2, 1e-290], [1e-290, 0.1, 0.2, den], [0.0, 0.1, 0.2, 1e-290],
+                  [1e-289, 0.3, -0.2, 0.0], [2.0 ** -990, 0.0, 0.0, 0.0], [2.0 ** -994, 0, 0, 0],
+                  [3.0, 0.5, 1.0, 0.0], [den, 0.5, 1.0, 2.0]])
+    b = np.array([[0.0, 0.0, 0.0, 0.0]] * 6 + [[4.0, -0.5, -1.0, 0.0], [1.0, 0.0, 0.0, 0.0]])
+    m, ok = _mass(ffh, a, b)
+    assert ok.tolist() == [False, False, True, True, True, False, True, False]
+    assert m[2] == 1e-290 and m[3] == 0.0 and m[4] == 0.0  # a massless leg alone has m = 0
+
+
 def test_ff_boost_coefficients(ffh):
-    """gamma = 1/sqrt(1 - b2) and k = gamma^2/(1 + gamma) of the FP64 boost, from the exact
+    """gamma = 1/sqrt(1 - b2) and w = gamma/(1 + gamma) of the FP64 boost, from the exact
     fixed-point 1 - b2, against mpmath."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 50
     b = np.concatenate([syn.velocities(syn.rng(8), 1500, 0.99),
                         syn.velocities(syn.rng(9), 500, 0.99998),
                         [[0, 0, 0], [1e-9, -2e-9, 3e-9], [0.6, 0.8, 0.0]]])
-    g, k = np.empty(len(b)), np.empty(len(b))
+    g, w = np.empty(len(b)), np.empty(len(b))
     ok = np.empty(len(b), np.uint8)
-    ffh.ffh_boost_coef(_p(b), ctypes.c_int64(len(b)), _p(g), _p(k), _p(ok))
+    ffh.ffh_boost_coef(_p(b), ctypes.c_int64(len(b)), _p(g), _p(w), _p(ok))
     ok = ok.astype(bool)
     assert not ok[-1] and ok[:-1].all()  # |beta| = 1 leaves the fast path
     for i in np.flatnonzero(ok):
         b2 = sum(mp.mpf(x) ** 2 for x in b[i])
         G = 1 / mp.sqrt(1 - b2)
         assert abs(g[i] / float(G) - 1) <= 3e-14
-        assert abs(k[i] / float(G * G / (1 + G)) - 1) <= 3e-14
+        assert abs(w[i] / float(G / (1 + G)) - 1) <= 3e-14
+
+
+def test_ff_to_double_by_integers(ffh):
+    """The integer ff -> double conversion against the exact sum hi + lo (rounded once by an FP64
+    add): within 2 ulps, signs and carries across a power of two included."""
+    g = syn.rng(12)
+    n = 200_000
+    hi = (np.ldexp(g.uniform(1, 2, n), g.integers(-60, 60, n)) * g.choice([-1, 1], n)).astype(np.float32)
+    hi[:64] = np.float32(1.0)
+    hi[64:128] = np.float32(-2.0)
+    hi[128:192] = np.nextafter(np.float32(2.0), np.float32(0))
+    rel = np.ldexp(g.uniform(-1, 1, n), -g.integers(21, 60, n))
+    lo = (hi.astype(np.float64) * rel).astype(np.float32)
+    lo[::7] = 0
+    lo[1::97] = np.float32(1e-45)  # denormal lo: counts as 0
+    for shift in (-700, 0, 5, 700):
+        oi, oa = np.empty(n), np.empty(n)
+        ffh.ffh_to_double(hi.ctypes.data_as(ctypes.c_void_p), lo.ctypes.data_as(ctypes.c_void_p),
+                          ctypes.c_int64(n), shift, _p(oi), _p(oa))
+        exact = np.ldexp(hi.astype(np.float64), shift)
+        assert np.all(np.abs(oi - oa) <= 2 * np.spacing(np.abs(oa))), shift
+        assert np.all(np.sign(oi) == np.sign(exact)), shift
+
+
+def _boost(lib, v, beta):
+    v, beta = np.ascontiguousarray(v), np.ascontiguousarray(beta)
+    out, ok = np.empty_like(v), np.empty(len(v), np.uint8)
+    lib.ffh_boost(_p(v), _p(beta), ctypes.c_int64(len(v)), _p(out), _p(ok))
+    return out, ok.astype(bool)
+
+
+def test_ff_boost_fast_path_against_oracle(ffh, orc):
+    """The FP64 boost's fast path (beta.p and E + beta.p in FP64, gamma, w, E' and f in ff)
+    against the binary128 boost.  Its error model: a few ulps of FP64 amplified by the condition
+    C = (E + |beta| |p|) / (E + beta.p) of E + beta.p, plus a few 2^-47 from the ff steps, so the
+    normwise error vs E' stays below 4e-14 + 2e-15 C (C <= 199 for |beta| <= 0.99)."""
+    g = syn.rng(1)
+    v, b = syn.pxpypze(g, 1 << 18), syn.velocities(g, 1 << 18, 0.99)
+    cond = (v[:, 3] + np.linalg.norm(b, axis=1) * np.linalg.norm(v[:, :3], axis=1)) / (
+        v[:, 3] + np.sum(b * v[:, :3], axis=1))
+    idx = np.union1d(np.arange(0, len(v), 16), np.argpartition(cond, -2048)[-2048:])
+    out, ok = _boost(ffh, v[idx], b[idx])
+    assert ok.all()
+    ref = orc.boost_def(v[idx], b[idx], nthreads=8)
+    err = np.abs(out - ref).max(axis=1) / ref[:, 3]
+    assert np.all(err <= 4e-14 + 2e-15 * cond[idx])
+    assert cond[idx].max() > 50  # the sample reaches the ill-conditioned end
+    # beta orthogonal to p at gamma up to 158: beta.p cancels, E + beta.p does not
+    m = 2000
+    w = syn.pxpypze(syn.rng(5), m)
+    d = syn.velocities(syn.rng(6), m, 1.0)
+    d -= (np.sum(d * w[:, :3], axis=1) / np.sum(w[:, :3] ** 2, axis=1))[:, None] * w[:, :3]
+    d *= (syn.rng(7).uniform(0.9, 0.99998, m) / np.linalg.norm(d, axis=1))[:, None]
+    out, ok = _boost(ffh, w, d)
+    ref = orc.boost_def(w, d)
+    assert ok.all()
+    assert np.all(np.abs(out - ref).max(axis=1) <= 4e-14 * ref[:, 3])
+    # rest frame (beta = -p/E): absolute error within a few 2^-47 of gamma (E + |beta| |p|)
+    bw = -w[:, :3] / w[:, 3:4]
+    out, ok = _boost(ffh, w, bw)
+    ref = orc.boost_def(w, bw)
+    gam = 1 / np.sqrt(1 - np.sum(bw * bw, axis=1))
+    sc = gam * (w[:, 3] + np.linalg.norm(bw, axis=1) * np.linalg.norm(w[:, :3], axis=1))
+    assert ok.any() and np.all(np.abs(out - ref)[ok].max(axis=1) <= 3e-14 * sc[ok])
+    # domain: 1 - b2 below 2^-16, a zero vector, magnitudes outside [2^-823, 2^1013), non-finite
+    one = np.array([[0.0, 0.0, 0.3]])
+    cases = [([1.0, 2.0, 3.0, 4.0], [0.0, 0.0, 0.999995]), ([0.0, 0.0, 0.0, 0.0], [0.0, 0.0, 0.3]),
+             ([1.0, 2.0, 3.0, 2.0 ** 1013], [0.0, 0.0, 0.3]), ([2.0 ** -824, 0, 0, 0], [0, 0, 0.3]),
+             ([1.0, np.inf, 0.0, 4.0], [0.0, 0.0, 0.3]), ([1.0, 2.0, 3.0, 4.0], [np.nan, 0, 0]),
+             ([1.0, 2.0, 3.0, 2.0 ** 1012], [0.0, 0.0, 0.3]), ([2.0 ** -823, 0, 0, 0], [0, 0, 0.3])]
+    out, ok = _boost(ffh, np.array([c[0] for c in cases], float), np.array([c[1] for c in cases], float))
+    assert ok.tolist() == [False] * 6 + [True, True]
+    ref = orc.boost_def(np.array([c[0] for c in cases[6:]], float), np.repeat(one, 2, axis=0))
+    assert np.all(np.abs(out[6:] - ref).max(axis=1) <= 4e-14 * ref[:, 3])
+    # beta = 0 is the identity, bit for bit (gamma = 1 and p + f 0 are exact)
+    out, ok = _boost(ffh, w, np.zeros((m, 3)))
+    assert ok.all() and np.array_equal(out, w)

@@ -59,7 +59,7 @@ def test_boost_f64_shared_velocity_and_edges(orc):
     assert np.array_equal(np.isnan(out).all(axis=1), ~fin)
     assert normwise(out[fin], ref[fin], ref[fin, 3]).max() <= TOL_F64
     # rest frame: boosting by -p/E gives (0, 0, 0, m).  Here |beta| -> 1 (gamma = E/m up to
-    # ~1e4), so the gate is the forward error bound of the vector form: gamma and k carry a
+    # ~1e4), so the gate is the forward error bound of the vector form: gamma and w carry a
     # relative error below 3e-14 (float-float, pinned by the host tests) and the multiply-adds
     # round in FP64,  |x'_k - ref_k| <= (3e-14 + 16 u) gamma (E + |beta| |p|),  u = 2^-53
     w = v[:1000]
@@ -87,7 +87,13 @@ def test_boost_f64_full_size_sampled(orc):
     import paper_2312_02756_gb300 as gvx
     g = syn.rng(1)
     v, beta = syn.pxpypze(g, N_FULL), syn.velocities(g, N_FULL, 0.99)
-    idx = np.sort(syn.rng(102).choice(N_FULL, 1 << 16, replace=False))
+    # a uniform sample plus the 4096 worst-conditioned vectors: there p' nearly cancels (the
+    # boost lands close to the vector's rest frame) and (E + |beta| |p|) / (E + beta.p) is largest
+    cond = (v[:, 3] + np.linalg.norm(beta, axis=1) * np.linalg.norm(v[:, :3], axis=1)) / (
+        v[:, 3] + np.sum(beta * v[:, :3], axis=1))
+    worst = np.argpartition(cond, -4096)[-4096:]
+    del cond
+    idx = np.union1d(syn.rng(102).choice(N_FULL, 1 << 16, replace=False), worst)
     ref = orc.boost_def(v[idx], beta[idx], nthreads=8)
     dv, db = dev(v, "soa"), dev(beta, "soa")
     out = gvx.boost(dv, db)
