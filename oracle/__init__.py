@@ -61,6 +61,7 @@ def _load():
         "orc_boost_def": ([P, P, I64, I64, P, INT], None),
         "orc_boost_grad_def": ([P, P, I64, P, I64, P, P], None),
         "orc_event_pairs_def": ([P, P, I64, P, P, P], INT),
+        "orc_event_pairs_grad_def": ([P, P, I64, P, P, P], INT),
         "orc_to_cartesian_def": ([P, I64, P], None),
         "orc_lv_mass_def": ([P, I64, P], None),
         "orc_mass_fp64": ([P, P, I64, P, INT], None),
@@ -178,6 +179,33 @@ def event_pairs_def(p, offsets):
     if rc != 0:
         raise ValueError("malformed offsets")
     return pair_off, pair_m[:n_pairs], sums[:n_ev]
+
+
+def event_pairs_grad_def(p, offsets, grad_pair_m, grad_sums=None) -> np.ndarray:
+    """O1 adjoint of event_pairs_def: d/dp of sum(grad_pair_m * pair_m) + sum(grad_sums * sums),
+    as (n_particles, 4) PtEtaPhiM rows.  grad_sums None means zero."""
+    p = _rows(p, 4) if len(p) else np.zeros((0, 4))
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    n_ev = off.shape[0] - 1
+    if n_ev < 0 or off[-1] != p.shape[0]:
+        raise ValueError("offsets must have n_events+1 entries ending at the particle count")
+    counts = np.diff(off)
+    if np.any(counts < 0):
+        raise ValueError("offsets must be non-decreasing")
+    n_pairs = int(np.sum(counts * (counts - 1) // 2))
+    gpm = np.ascontiguousarray(np.asarray(grad_pair_m, dtype=np.float64)).reshape(-1)
+    if gpm.shape[0] != n_pairs:
+        raise ValueError("grad_pair_m must hold one value per pair")
+    gpm = gpm if n_pairs else np.zeros(1)
+    gs = None if grad_sums is None else _rows(grad_sums, 4)
+    if gs is not None and gs.shape[0] != n_ev:
+        raise ValueError("grad_sums must hold one row per event")
+    out = np.zeros((max(p.shape[0], 1), 4))
+    rc = _load().orc_event_pairs_grad_def(_ptr(p), _ptr(off), n_ev, _ptr(gpm),
+                                          None if gs is None else _ptr(gs), _ptr(out))
+    if rc != 0:
+        raise ValueError("malformed offsets")
+    return out[:p.shape[0]]
 
 
 def to_cartesian_def(p) -> np.ndarray:

@@ -169,57 +169,74 @@ void orc_mass_naive_fp64(const double *a, const double *b, int64_t n, double *m)
   }
 }
 
-/* Gradient of the pair mass by the chain rule through the definition:
- *   dm/d(Px,Py,Pz,E) of the summed vector = (-Px, -Py, -Pz, E) / m,
- *   times the Jacobian of each leg's (px,py,pz,E) with respect to (pt,eta,phi,m):
+/* Jacobian of one leg's PtEtaPhiM -> PxPyPzE conversion, J[r][c] = d v_r / d x_c with rows
+ * (px, py, pz, E) and columns (pt, eta, phi, m), v = leg_to_cartesian_q(leg):
  *     px: ( cos phi,      0,           -pt sin phi, 0    )
  *     py: ( sin phi,      0,            pt cos phi, 0    )
  *     pz: ( sinh eta,     pt cosh eta,  0,          0    )
- *     E : ((px cos phi + py sin phi + pz sinh eta)/E_i, pz pt cosh eta / E_i,
- *          (-px pt sin phi + py pt cos phi)/E_i,  m/E_i )
- * Readings: where m <= 0 the gradient is zero (m is not differentiable at 0).  A massless leg
- * (m_i = 0) has E_i = pt cosh(eta), whose derivatives are used as they stand, so that a leg at
- * pt = 0, m = 0 gets the one-sided (pt >= 0) derivative and dE/dm = 0. */
-static void pair_mass_grad_def(const double *a, const double *b, double gm, double *ga,
-                               double *gb) {
+ *     E : ((px cos phi + py sin phi + pz sinh eta)/E, pz pt cosh eta / E,
+ *          (-px pt sin phi + py pt cos phi)/E,  m/E )
+ * Reading: a massless leg (m = 0) has E = pt cosh(eta), whose derivatives are used as they
+ * stand, so that a leg at pt = 0, m = 0 gets the one-sided (pt >= 0) derivative and dE/dm = 0. */
+static void leg_jacobian_q(const double *leg, const qreal v[4], qreal J[4][4]) {
+  qreal pt = leg[0], eta = leg[1], phi = leg[2], mm = leg[3];
+  qreal c = Q_COS(phi), s = Q_SIN(phi), sh = Q_SINH(eta), ch = Q_COSH(eta);
+  qreal px = v[0], py = v[1], pz = v[2], e = v[3];
+  qreal rows[4][4] = {
+      {c, 0, -pt * s, 0},
+      {s, 0, pt * c, 0},
+      {sh, pt * ch, 0, 0},
+      {0, 0, 0, 0},
+  };
+  for (int r = 0; r < 4; r++)
+    for (int k = 0; k < 4; k++) J[r][k] = rows[r][k];
+  if (mm == 0) {
+    J[3][0] = ch;
+    J[3][1] = pt * sh;
+  } else {
+    J[3][0] = (px * c + py * s + pz * sh) / e;
+    J[3][1] = pz * pt * ch / e;
+    J[3][2] = (-px * pt * s + py * pt * c) / e;
+    J[3][3] = mm / e;
+  }
+}
+
+/* dm/d(pt, eta, phi, m) of both legs of the pair mass, by the chain rule through the definition:
+ * dm/d(Px,Py,Pz,E) of the summed vector = (-Px, -Py, -Pz, E) / m, times each leg's Jacobian.
+ * Reading: where m <= 0 the gradient is zero (m is not differentiable at 0). */
+static void pair_mass_dm_q(const double *a, const double *b, qreal ga[4], qreal gb[4]) {
   qreal v[2][4], w[4];
   leg_to_cartesian_q(a, v[0]);
   leg_to_cartesian_q(b, v[1]);
   for (int k = 0; k < 4; k++) w[k] = v[0][k] + v[1][k];
   qreal m = lv_mass_q(w);
   const double *legs[2] = {a, b};
-  double *outs[2] = {ga, gb};
+  qreal *outs[2] = {ga, gb};
   if (!(m > 0)) {
     for (int l = 0; l < 2; l++)
-      for (int k = 0; k < 4; k++) outs[l][k] = 0.0;
+      for (int k = 0; k < 4; k++) outs[l][k] = 0;
     return;
   }
   qreal dmdv[4] = {-w[0] / m, -w[1] / m, -w[2] / m, w[3] / m};
   for (int l = 0; l < 2; l++) {
-    qreal pt = legs[l][0], eta = legs[l][1], phi = legs[l][2], mm = legs[l][3];
-    qreal c = Q_COS(phi), s = Q_SIN(phi), sh = Q_SINH(eta), ch = Q_COSH(eta);
-    qreal px = v[l][0], py = v[l][1], pz = v[l][2], e = v[l][3];
-    qreal J[4][4] = {
-        {c, 0, -pt * s, 0},
-        {s, 0, pt * c, 0},
-        {sh, pt * ch, 0, 0},
-        {0, 0, 0, 0},
-    };
-    if (mm == 0) {
-      /* massless leg: E = pt cosh(eta), differentiable for pt >= 0 including pt = 0 */
-      J[3][0] = ch;
-      J[3][1] = pt * sh;
-    } else {
-      J[3][0] = (px * c + py * s + pz * sh) / e;
-      J[3][1] = pz * pt * ch / e;
-      J[3][2] = (-px * pt * s + py * pt * c) / e;
-      J[3][3] = mm / e;
-    }
+    qreal J[4][4];
+    leg_jacobian_q(legs[l], v[l], J);
     for (int k = 0; k < 4; k++) {
       qreal acc = 0;
       for (int r = 0; r < 4; r++) acc += dmdv[r] * J[r][k];
-      outs[l][k] = (double)(acc * (qreal)gm);
+      outs[l][k] = acc;
     }
+  }
+}
+
+/* Gradient of the pair mass times the upstream gradient gm, rounded once. */
+static void pair_mass_grad_def(const double *a, const double *b, double gm, double *ga,
+                               double *gb) {
+  qreal qa[4], qb[4];
+  pair_mass_dm_q(a, b, qa, qb);
+  for (int k = 0; k < 4; k++) {
+    ga[k] = (double)(qa[k] * (qreal)gm);
+    gb[k] = (double)(qb[k] * (qreal)gm);
   }
 }
 
@@ -405,6 +422,48 @@ int orc_event_pairs_def(const double *p, const int64_t *off, int64_t n_events, i
       for (int c = 0; c < 4; c++) s[c] += v[c];
     }
     for (int c = 0; c < 4; c++) sums[4 * e + c] = (double)s[c];
+  }
+  return 0;
+}
+
+/* Adjoint of orc_event_pairs_def (the per-event combinatorics, differentiated).  Inputs: the
+ * upstream gradients gpm of the pair masses, packed as orc_event_pairs_def packs pair_m, and gsum
+ * of the event sums (n_events rows of PxPyPzE; NULL means zero).  For particle i of event e:
+ *   grad_p[i] = sum over j != i in e of gpm[pair(i, j)] dm(p_i, p_j)/dp_i  +  J_i^T gsum[e],
+ * with pair(i, j) the packed index of the unordered pair and J_i the leg Jacobian above,
+ * accumulated in binary128 and rounded once.  Returns 0, or -1 for malformed offsets. */
+int orc_event_pairs_grad_def(const double *p, const int64_t *off, int64_t n_events,
+                             const double *gpm, const double *gsum, double *grad_p) {
+  if (n_events < 0 || off[0] != 0) return -1;
+  for (int64_t e = 0; e < n_events; e++)
+    if (off[e + 1] < off[e]) return -1;
+  int64_t pbase = 0;  /* packed index of the event's first pair */
+  for (int64_t e = 0; e < n_events; e++) {
+    int64_t base = off[e], n = off[e + 1] - off[e];
+    for (int64_t i = 0; i < n; i++) {
+      const double *pi = p + 4 * (base + i);
+      qreal acc[4] = {0, 0, 0, 0};
+      for (int64_t j = 0; j < n; j++) {
+        if (j == i) continue;
+        int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+        int64_t k = lo * n - lo * (lo + 1) / 2 + (hi - lo - 1);
+        qreal d[4], other[4];
+        if (i < j)
+          pair_mass_dm_q(pi, p + 4 * (base + j), d, other);
+        else
+          pair_mass_dm_q(p + 4 * (base + j), pi, other, d);
+        for (int c = 0; c < 4; c++) acc[c] += (qreal)gpm[pbase + k] * d[c];
+      }
+      if (gsum) {
+        qreal v[4], J[4][4];
+        leg_to_cartesian_q(pi, v);
+        leg_jacobian_q(pi, v, J);
+        for (int c = 0; c < 4; c++)
+          for (int r = 0; r < 4; r++) acc[c] += (qreal)gsum[4 * e + r] * J[r][c];
+      }
+      for (int c = 0; c < 4; c++) grad_p[4 * (base + i) + c] = (double)acc[c];
+    }
+    pbase += n * (n - 1) / 2;
   }
   return 0;
 }

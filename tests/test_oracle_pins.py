@@ -349,3 +349,118 @@ def test_event_pairs_rejects_bad_offsets(orc):
         orc.event_pairs_def(p, [0, 3, 2, 5])
     with pytest.raises(ValueError):
         orc.event_pairs_def(p, [0, 2, 4])
+
+
+def _event_losses(orc, p, off, gpm, gsum):
+    """Per-event L_e = sum of gpm * pair masses + gsum . event sum, from the forward oracle."""
+    pair_off, pair_m, sums = orc.event_pairs_def(p, off)
+    n_ev = len(off) - 1
+    pair_ev = np.repeat(np.arange(n_ev), np.diff(pair_off))
+    L = np.bincount(pair_ev, weights=gpm * pair_m, minlength=n_ev)
+    return L + np.sum(gsum * sums, axis=1)
+
+
+def test_event_pairs_grad_finite_differences(orc):
+    """Central differences of the forward oracle's per-event losses.  Events are independent, so
+    perturbing the r-th particle of every event at once gives each event's derivative in one
+    pair of forward calls."""
+    g = syn.rng(118)
+    off = syn.jagged_offsets(g, 80, lam=4.0, n_max=8)
+    off = np.concatenate([off, off[-1:] + [0, 1, 3, 6]])
+    p = syn.ptetaphim(g, int(off[-1]))
+    counts = np.diff(off)
+    n_pairs = int(np.sum(counts * (counts - 1) // 2))
+    gpm, gsum = syn.upstream(g, n_pairs), syn.upstream(g, (len(counts), 4))
+    grad = orc.event_pairs_grad_def(p, off, gpm, gsum)
+    for r in range(counts.max()):
+        ev = np.flatnonzero(counts > r)
+        idx = off[ev] + r
+        for k in range(4):
+            h = 1e-6 * np.maximum(np.abs(p[idx, k]), 1.0)
+            hi, lo = p.copy(), p.copy()
+            hi[idx, k] += h
+            lo[idx, k] -= h
+            fd = (_event_losses(orc, hi, off, gpm, gsum) - _event_losses(orc, lo, off, gpm, gsum))[ev]
+            fd /= hi[idx, k] - lo[idx, k]
+            scale = np.abs(grad[idx]).max(axis=1) + np.abs(gsum[ev]).sum(axis=1) * 10
+            assert np.all(np.abs(fd - grad[idx, k]) <= 2e-6 * scale), (r, k)
+
+
+def test_event_pairs_grad_sum_part_closed_form(orc):
+    """With only an event-sum gradient along one axis, each particle gets one row of the
+    PtEtaPhiM -> PxPyPzE Jacobian: d px = (cos phi, 0, -pt sin phi, 0), d pz = (sinh eta,
+    pt cosh eta, 0, 0), d E = (pt cosh^2 eta, pt^2 cosh eta sinh eta, 0, m) / E."""
+    g = syn.rng(119)
+    off = syn.jagged_offsets(g, 50, lam=5.0, n_max=10)
+    p = syn.ptetaphim(g, int(off[-1]))
+    counts = np.diff(off)
+    gpm = np.zeros(int(np.sum(counts * (counts - 1) // 2)))
+    pt, eta, phi, m = p.T
+    ch, sh = np.cosh(eta), np.sinh(eta)
+    E = np.sqrt((pt * ch) ** 2 + m ** 2)
+    zero = np.zeros_like(pt)
+    want = {0: np.stack([np.cos(phi), zero, -pt * np.sin(phi), zero], axis=1),
+            2: np.stack([sh, pt * ch, zero, zero], axis=1),
+            3: np.stack([pt * ch * ch / E, pt * pt * ch * sh / E, zero, m / E], axis=1)}
+    for axis, w in want.items():
+        gsum = np.zeros((len(counts), 4))
+        gsum[:, axis] = 1.0
+        got = orc.event_pairs_grad_def(p, off, gpm, gsum)
+        assert np.all(np.abs(got - w) <= 1e-14 * np.abs(w).max(axis=1, keepdims=True)), axis
+
+
+def test_event_pairs_grad_massless_pairs_closed_form(orc):
+    """Two-particle events of massless legs: m = sqrt(2 pt1 pt2 (cosh d - cos f)) gives
+    dm/dpt1 = m/(2 pt1), dm/deta1 = pt1 pt2 sinh(d)/m, dm/dphi1 = pt1 pt2 sin(f)/m, dm/dm1 = 0,
+    and the opposite signs of the angle terms for the second particle."""
+    a, b = _massless_pairs(200, 120)
+    p = np.empty((400, 4))
+    p[0::2], p[1::2] = a, b
+    off = np.arange(0, 401, 2)
+    gpm = syn.upstream(syn.rng(121), 200)
+    got = orc.event_pairs_grad_def(p, off, gpm)
+    m = orc.mass_def(a, b)
+    d, f = a[:, 1] - b[:, 1], a[:, 2] - b[:, 2]
+    pp = a[:, 0] * b[:, 0]
+    zero = np.zeros_like(m)
+    want_a = np.stack([m / (2 * a[:, 0]), pp * np.sinh(d) / m, pp * np.sin(f) / m, zero], axis=1)
+    want_b = np.stack([m / (2 * b[:, 0]), -pp * np.sinh(d) / m, -pp * np.sin(f) / m, zero], axis=1)
+    for got_l, w in ((got[0::2], want_a), (got[1::2], want_b)):
+        w = w * gpm[:, None]
+        assert np.all(np.abs(got_l - w) <= 1e-12 * np.abs(w).max(axis=1, keepdims=True))
+
+
+def test_event_pairs_grad_permutation(orc):
+    """Reordering the particles of every event (and the pair gradients with them) reorders the
+    particle gradients."""
+    g = syn.rng(122)
+    off = syn.jagged_offsets(g, 60, lam=6.0, n_max=12)
+    p = syn.ptetaphim(g, int(off[-1]))
+    counts = np.diff(off)
+    n_pairs = int(np.sum(counts * (counts - 1) // 2))
+    gpm, gsum = syn.upstream(g, n_pairs), syn.upstream(g, (len(counts), 4))
+    grad = orc.event_pairs_grad_def(p, off, gpm, gsum)
+    perm = np.arange(len(p))
+    gpm2 = np.empty_like(gpm)
+    pbase = 0
+    for e, n in enumerate(counts):
+        local = g.permutation(n)  # new position q holds old particle local[q]
+        perm[off[e]:off[e + 1]] = off[e] + local
+        ii, jj = np.triu_indices(n, 1)
+        old = {}
+        for k, (i, j) in enumerate(zip(ii, jj)):
+            old[(i, j)] = gpm[pbase + k]
+        for k, (i, j) in enumerate(zip(ii, jj)):
+            a, b = sorted((local[i], local[j]))
+            gpm2[pbase + k] = old[(a, b)]
+        pbase += n * (n - 1) // 2
+    grad2 = orc.event_pairs_grad_def(p[perm], off, gpm2, gsum)
+    assert np.all(np.abs(grad2 - grad[perm]) <= 1e-15 * np.abs(grad[perm]).max(axis=1, keepdims=True))
+
+
+def test_event_pairs_grad_rejects_bad_input(orc):
+    p = syn.ptetaphim(syn.rng(123), 5)
+    with pytest.raises(ValueError):
+        orc.event_pairs_grad_def(p, [0, 3, 2, 5], np.zeros(4))
+    with pytest.raises(ValueError):
+        orc.event_pairs_grad_def(p, [0, 2, 5], np.zeros(3))  # 1 + 3 pairs expected
