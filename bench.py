@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "inv-mass & boost vectors/s at N=2^26 FP64/FP32, % roofline; fwd+bwd vs fwd"
 UNIT = "vectors/s"
 N_FULL = 1 << 26
+FORMS = ("fp32", "jagged", "fwd_bwd")
 WORKLOAD = ("FP64 invariant mass of 2^26 PtEtaPhiM pairs in SoA and in AoS, plus FP64 boost of "
             "2^26 PxPyPzE vectors by per-vector beta (|beta| <= 0.99)")
 BYTES_MASS_F64 = 72    # 2 legs x 4 doubles in + 1 double out, per pair
@@ -208,7 +209,7 @@ def time_loop(torch, fn, stream, steps, warmup):
 
 # ---------------------------------------------------------------------------------------- forms
 
-def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms):
+def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS):
     """FP32, jagged and forward+backward forms, each timed alone on the same GPU."""
     import gvx_synth as syn
     from paper_2312_02756_gb300 import _lib
@@ -217,91 +218,111 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms):
     s = ctypes.c_void_p(stream.cuda_stream)
     r, P = ctypes.byref, ctypes.c_void_p
     res = {}
-    # FP32: half the particles light and hard; boost with |beta| <= 0.999999
-    g = syn.rng(2)
-    a = torch.as_tensor(syn.to_f32(syn.ptetaphim_light_mix(g, N_FULL)).T.copy()).cuda()
-    b = torch.as_tensor(syn.to_f32(syn.ptetaphim_light_mix(g, N_FULL)).T.copy()).cuda()
-    m = torch.empty(N_FULL, dtype=torch.float32, device="cuda")
-    la, lb = Step._lv(a, 0, 4), Step._lv(b, 0, 4)
-    t_m = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass(
-        r(la), r(lb), P(m.data_ptr()), N_FULL, 1, s)), stream, steps, warmup)
-    del a, b, m
-    v = torch.as_tensor(syn.to_f32(syn.pxpypze(g, N_FULL)).T.copy()).cuda()
-    be = torch.as_tensor(syn.to_f32(syn.velocities(g, N_FULL, 0.999999)).T.copy()).cuda()
-    o = torch.empty_like(v)
-    lv_, lbe, lo = Step._lv(v, 0, 4), Step._lv(be, 0, 3), Step._lv(o, 0, 4)
-    t_b = time_loop(torch, lambda: _lib.check(lib.gvx_boost(
-        r(lv_), r(lbe), 1, r(lo), N_FULL, 1, s)), stream, steps, warmup)
-    del v, be, o
-    torch.cuda.empty_cache()
-    res["fp32"] = {
-        "workload": "FP32 mass of 2^26 pairs (half light, pt up to 5 TeV) + FP32 boost of 2^26 "
-                    "vectors, |beta| <= 0.999999, SoA",
-        "mass_ms": t_m, "boost_ms": t_b,
-        "mass_pairs_per_s": N_FULL / (t_m * 1e-3), "boost_vectors_per_s": N_FULL / (t_b * 1e-3),
-        "mass_GBps": BYTES_MASS_F32 * N_FULL / (t_m * 1e-3) / 1e9,
-        "boost_GBps": BYTES_BOOST_F32 * N_FULL / (t_b * 1e-3) / 1e9,
-        "mass_speedup_vs_fp64": fp64_mass_ms / t_m,
-    }
-    # jagged: 2^20 events, Poisson(8) multiplicities, one persistent launch in a CUDA graph
-    g = syn.rng(3)
-    off = syn.jagged_offsets(g, 1 << 20)
-    p = torch.as_tensor(syn.ptetaphim(g, int(off[-1]))).cuda()
-    c = np.diff(off)
-    n_pairs = int(np.sum(c * (c - 1) // 2))
-    doff = torch.as_tensor(off).cuda()
-    shape, (te, nt), _ = gvx.autotune_event_pair_masses(p, doff, n_pairs, reps=3, cache=False)
-    graph = gvx.EventPairMassesGraph(p, doff, n_pairs)
-    t_j = time_loop(torch, lambda: graph.launch(stream), stream, steps, warmup)
-    status = gvx.device_status()
-    graph.close()
-    del p, doff, graph
-    torch.cuda.empty_cache()
-    jag_bytes = 32 * int(off[-1]) + 8 * n_pairs + 8 * (len(off)) * 2 + 32 * (len(off) - 1)
-    res["jagged"] = {
-        "workload": "2^20 events, multiplicity Poisson(8) clamped to [0,64]; all in-event pair "
-                    "masses + per-event sums; one persistent kernel replayed as a CUDA graph",
-        "ms": t_j, "pairs": n_pairs, "particles": int(off[-1]),
-        "pairs_per_s": n_pairs / (t_j * 1e-3), "events_per_s": (len(off) - 1) / (t_j * 1e-3),
-        "GBps": jag_bytes / (t_j * 1e-3) / 1e9, "shape": {"events_per_tile": te, "threads": nt},
-        "pairs_per_s_vs_fp64_mass": (n_pairs / (t_j * 1e-3)) / fp64_pairs_per_s,
-        "device_status": status,
-    }
-    # forward + backward, FP64 and FP32, N = 2^24
-    n = 1 << 24
-    out = {}
-    for dt, code, tdt in (("f64", 0, torch.float64), ("f32", 1, torch.float32)):
-        g = syn.rng(4)
-        a = torch.as_tensor(syn.ptetaphim(g, n).T.copy(), dtype=tdt).cuda()
-        b = torch.as_tensor(syn.ptetaphim(g, n).T.copy(), dtype=tdt).cuda()
-        gm = torch.as_tensor(syn.upstream(g, n), dtype=tdt).cuda()
-        m = torch.empty(n, dtype=tdt, device="cuda")
-        ga, gb = torch.empty_like(a), torch.empty_like(b)
-        la, lb, lga, lgb = (Step._lv(t, 0, 4) for t in (a, b, ga, gb))
-        fwd = lambda: _lib.check(lib.gvx_invariant_mass(r(la), r(lb), P(m.data_ptr()), n, code, s))
-        bwd = lambda: _lib.check(lib.gvx_invariant_mass_bwd(
-            r(la), r(lb), P(gm.data_ptr()), r(lga), r(lgb), n, code, s))
-        t_f = time_loop(torch, fwd, stream, steps, warmup)
-        t_fb = time_loop(torch, lambda: (fwd(), bwd()), stream, steps, warmup)
-        del a, b, gm, m, ga, gb
-        v = torch.as_tensor(syn.pxpypze(g, n).T.copy(), dtype=tdt).cuda()
-        be = torch.as_tensor(syn.velocities(g, n, 0.99).T.copy(), dtype=tdt).cuda()
-        go = torch.as_tensor(syn.upstream(g, (n, 4)).T.copy(), dtype=tdt).cuda()
-        o, gv, gbe = torch.empty_like(v), torch.empty_like(v), torch.empty_like(be)
-        lv_, lbe, lgo, lo, lgv, lgbe = (Step._lv(t, 0, k) for t, k in
-                                        ((v, 4), (be, 3), (go, 4), (o, 4), (gv, 4), (gbe, 3)))
-        bf = lambda: _lib.check(lib.gvx_boost(r(lv_), r(lbe), 1, r(lo), n, code, s))
-        bb = lambda: _lib.check(lib.gvx_boost_bwd(r(lv_), r(lbe), 1, r(lgo), r(lgv), r(lgbe), n,
-                                                  code, None, 0, s))
-        t_bf = time_loop(torch, bf, stream, steps, warmup)
-        t_bfb = time_loop(torch, lambda: (bf(), bb()), stream, steps, warmup)
-        del v, be, go, o, gv, gbe
+    if "fp32" in which:
+        # FP32: half the particles light and hard; boost with |beta| <= 0.999999
+        g = syn.rng(2)
+        a = torch.as_tensor(syn.to_f32(syn.ptetaphim_light_mix(g, N_FULL)).T.copy()).cuda()
+        b = torch.as_tensor(syn.to_f32(syn.ptetaphim_light_mix(g, N_FULL)).T.copy()).cuda()
+        m = torch.empty(N_FULL, dtype=torch.float32, device="cuda")
+        la, lb = Step._lv(a, 0, 4), Step._lv(b, 0, 4)
+        t_m = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass(
+            r(la), r(lb), P(m.data_ptr()), N_FULL, 1, s)), stream, steps, warmup)
+        del a, b, m
+        v = torch.as_tensor(syn.to_f32(syn.pxpypze(g, N_FULL)).T.copy()).cuda()
+        be = torch.as_tensor(syn.to_f32(syn.velocities(g, N_FULL, 0.999999)).T.copy()).cuda()
+        o = torch.empty_like(v)
+        lv_, lbe, lo = Step._lv(v, 0, 4), Step._lv(be, 0, 3), Step._lv(o, 0, 4)
+        t_b = time_loop(torch, lambda: _lib.check(lib.gvx_boost(
+            r(lv_), r(lbe), 1, r(lo), N_FULL, 1, s)), stream, steps, warmup)
+        del v, be, o
         torch.cuda.empty_cache()
-        out[dt] = {"mass_fwd_ms": t_f, "mass_fwd_bwd_ms": t_fb, "mass_ratio": t_fb / t_f,
-                   "mass_fwd_bwd_GBps": 208 * n / (t_fb * 1e-3) / 1e9 * (1 if code == 0 else 0.5),
-                   "boost_fwd_ms": t_bf, "boost_fwd_bwd_ms": t_bfb, "boost_ratio": t_bfb / t_bf}
-    out["workload"] = "N = 2^24 pairs / vectors, SoA, upstream gradients uniform in [-1, 1]"
-    res["fwd_bwd"] = out
+        res["fp32"] = {
+            "workload": "FP32 mass of 2^26 pairs (half light, pt up to 5 TeV) + FP32 boost of 2^26 "
+                        "vectors, |beta| <= 0.999999, SoA",
+            "mass_ms": t_m, "boost_ms": t_b,
+            "mass_pairs_per_s": N_FULL / (t_m * 1e-3), "boost_vectors_per_s": N_FULL / (t_b * 1e-3),
+            "mass_GBps": BYTES_MASS_F32 * N_FULL / (t_m * 1e-3) / 1e9,
+            "boost_GBps": BYTES_BOOST_F32 * N_FULL / (t_b * 1e-3) / 1e9,
+            "mass_speedup_vs_fp64": fp64_mass_ms / t_m,
+        }
+    if "jagged" in which:
+        # jagged: 2^20 events, Poisson(8) multiplicities, one persistent launch in a CUDA graph
+        g = syn.rng(3)
+        off = syn.jagged_offsets(g, 1 << 20)
+        p = torch.as_tensor(syn.ptetaphim(g, int(off[-1]))).cuda()
+        c = np.diff(off)
+        n_pairs = int(np.sum(c * (c - 1) // 2))
+        doff = torch.as_tensor(off).cuda()
+        shape, (te, nt), _ = gvx.autotune_event_pair_masses(p, doff, n_pairs, reps=3, cache=False)
+        graph = gvx.EventPairMassesGraph(p, doff, n_pairs)
+        t_j = time_loop(torch, lambda: graph.launch(stream), stream, steps, warmup)
+        status = gvx.device_status()
+        # the adjoint (gvx_event_pair_masses_bwd) on the same events, upstream gradients U[-1, 1]
+        n_ev = len(off) - 1
+        gpm = torch.as_tensor(syn.upstream(g, n_pairs)).cuda()
+        gsum = torch.as_tensor(syn.upstream(g, (n_ev, 4))).cuda()
+        gp = torch.empty_like(p)
+        lp, lgs, lgp = Step._lv(p, 1, 4), Step._lv(gsum, 1, 4), Step._lv(gp, 1, 4)
+        jbwd = lambda: _lib.check(lib.gvx_event_pair_masses_bwd(
+            r(lp), P(doff.data_ptr()), P(graph.pair_offsets.data_ptr()), n_ev, int(off[-1]),
+            P(gpm.data_ptr()), n_pairs, r(lgs), r(lgp), s))
+        t_jb = time_loop(torch, jbwd, stream, steps, warmup)
+        status_b = gvx.device_status()
+        graph.close()
+        del p, doff, graph, gpm, gsum, gp
+        torch.cuda.empty_cache()
+        jag_bytes = 32 * int(off[-1]) + 8 * n_pairs + 8 * (len(off)) * 2 + 32 * (len(off) - 1)
+        # adjoint: particles, pair gradients, event-sum gradients and offsets in, gradients out
+        jag_bwd_bytes = 64 * int(off[-1]) + 8 * n_pairs + 16 * (len(off)) + 32 * n_ev
+        res["jagged"] = {
+            "workload": "2^20 events, multiplicity Poisson(8) clamped to [0,64]; all in-event pair "
+                        "masses + per-event sums; one persistent kernel replayed as a CUDA graph",
+            "ms": t_j, "pairs": n_pairs, "particles": int(off[-1]),
+            "pairs_per_s": n_pairs / (t_j * 1e-3), "events_per_s": (len(off) - 1) / (t_j * 1e-3),
+            "GBps": jag_bytes / (t_j * 1e-3) / 1e9, "shape": {"events_per_tile": te, "threads": nt},
+            "pairs_per_s_vs_fp64_mass": (n_pairs / (t_j * 1e-3)) / fp64_pairs_per_s,
+            "device_status": status,
+            "bwd": {"ms": t_jb, "pairs_per_s": n_pairs / (t_jb * 1e-3),
+                    "GBps": jag_bwd_bytes / (t_jb * 1e-3) / 1e9, "bwd_over_fwd": t_jb / t_j,
+                    "device_status": status_b,
+                    "how": "gvx_event_pair_masses_bwd, pair-mass and event-sum gradients U[-1, 1]"},
+        }
+    if "fwd_bwd" in which:
+        # forward + backward, FP64 and FP32, N = 2^24
+        n = 1 << 24
+        out = {}
+        for dt, code, tdt in (("f64", 0, torch.float64), ("f32", 1, torch.float32)):
+            g = syn.rng(4)
+            a = torch.as_tensor(syn.ptetaphim(g, n).T.copy(), dtype=tdt).cuda()
+            b = torch.as_tensor(syn.ptetaphim(g, n).T.copy(), dtype=tdt).cuda()
+            gm = torch.as_tensor(syn.upstream(g, n), dtype=tdt).cuda()
+            m = torch.empty(n, dtype=tdt, device="cuda")
+            ga, gb = torch.empty_like(a), torch.empty_like(b)
+            la, lb, lga, lgb = (Step._lv(t, 0, 4) for t in (a, b, ga, gb))
+            fwd = lambda: _lib.check(lib.gvx_invariant_mass(r(la), r(lb), P(m.data_ptr()), n, code, s))
+            bwd = lambda: _lib.check(lib.gvx_invariant_mass_bwd(
+                r(la), r(lb), P(gm.data_ptr()), r(lga), r(lgb), n, code, s))
+            t_f = time_loop(torch, fwd, stream, steps, warmup)
+            t_fb = time_loop(torch, lambda: (fwd(), bwd()), stream, steps, warmup)
+            del a, b, gm, m, ga, gb
+            v = torch.as_tensor(syn.pxpypze(g, n).T.copy(), dtype=tdt).cuda()
+            be = torch.as_tensor(syn.velocities(g, n, 0.99).T.copy(), dtype=tdt).cuda()
+            go = torch.as_tensor(syn.upstream(g, (n, 4)).T.copy(), dtype=tdt).cuda()
+            o, gv, gbe = torch.empty_like(v), torch.empty_like(v), torch.empty_like(be)
+            lv_, lbe, lgo, lo, lgv, lgbe = (Step._lv(t, 0, k) for t, k in
+                                            ((v, 4), (be, 3), (go, 4), (o, 4), (gv, 4), (gbe, 3)))
+            bf = lambda: _lib.check(lib.gvx_boost(r(lv_), r(lbe), 1, r(lo), n, code, s))
+            bb = lambda: _lib.check(lib.gvx_boost_bwd(r(lv_), r(lbe), 1, r(lgo), r(lgv), r(lgbe), n,
+                                                      code, None, 0, s))
+            t_bf = time_loop(torch, bf, stream, steps, warmup)
+            t_bfb = time_loop(torch, lambda: (bf(), bb()), stream, steps, warmup)
+            del v, be, go, o, gv, gbe
+            torch.cuda.empty_cache()
+            out[dt] = {"mass_fwd_ms": t_f, "mass_fwd_bwd_ms": t_fb, "mass_ratio": t_fb / t_f,
+                       "mass_fwd_bwd_GBps": 208 * n / (t_fb * 1e-3) / 1e9 * (1 if code == 0 else 0.5),
+                       "boost_fwd_ms": t_bf, "boost_fwd_bwd_ms": t_bfb, "boost_ratio": t_bfb / t_bf}
+        out["workload"] = "N = 2^24 pairs / vectors, SoA, upstream gradients uniform in [-1, 1]"
+        res["fwd_bwd"] = out
     return res
 
 
@@ -462,8 +483,12 @@ def run_gvx(args):
     del step
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_forms:
+        which = tuple(f for f in args.forms.split(",") if f)
+        unknown = set(which) - set(FORMS)
+        if unknown:
+            raise SystemExit("unknown --forms entries: %s" % ",".join(sorted(unknown)))
         line["forms"] = forms(torch, gvx, max(3, args.steps // 2), 2,
-                              N_FULL / (per_kernel[0] * 1e-3), per_kernel[0])
+                              N_FULL / (per_kernel[0] * 1e-3), per_kernel[0], which)
     if rank == 0:
         print(json.dumps(line))
     if dist:
@@ -503,6 +528,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gvx", choices=["gvx", "reference"])
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--forms", default=",".join(FORMS),
+                    help="comma-separated subset of %s" % ",".join(FORMS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-log2", type=int, default=26,

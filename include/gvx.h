@@ -155,6 +155,33 @@ gvx_status gvx_event_pair_masses(const gvx_lv *particles, const int64_t *offsets
                                  size_t workspace_bytes, void *stream);
 
 /*
+ * Adjoint of gvx_event_pair_masses (FP64): the gradient with respect to the particles of
+ *   sum_k grad_pair_m[k] pair_m[k] + sum_e <grad_event_sum[e], event_sum[e]>,
+ * i.e. for particle i of event e
+ *   grad_particles[i] = sum over j != i of grad_pair_m[pair(i, j)] dm(p_i, p_j)/dp_i
+ *                       + J_i^T grad_event_sum[e],
+ * with J_i the Jacobian of the particle's (px, py, pz, E) with respect to (pt, eta, phi, m).
+ * (The paper defines the forward quantities only, Sec. 4.1 Fig. 1 and Sec. 6; this is their
+ * derivative, with the conventions of gvx_invariant_mass_bwd: zero where a pair mass is 0, the
+ * one-sided pt >= 0 derivative of a massless particle.)
+ *   particles:       n_particles PtEtaPhiM vectors (SoA or AoS), as given to the forward call.
+ *   offsets:         the forward call's n_events + 1 event offsets.
+ *   pair_offsets:    the n_events + 1 pair offsets the forward call wrote.
+ *   grad_pair_m:     n_pairs upstream gradients, packed like pair_m (n_pairs = pair_offsets[n_events]).
+ *   grad_event_sum:  n_events PxPyPzE upstream gradients (SoA or AoS), or NULL for zero.
+ *   grad_particles:  out, n_particles PtEtaPhiM-shaped gradients (SoA or AoS).
+ * Deterministic (no atomics; a fixed summation order per particle).  Offsets or pair offsets that
+ * do not match the event sizes or n_pairs are detected on the device: GVX_ERR_OFFSETS is recorded
+ * in the device status word and the gradients of the affected events are not written.  All
+ * pointers are device (or GPU-addressable host) memory; one launch; nothing is allocated.
+ */
+gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *offsets,
+                                     const int64_t *pair_offsets, int64_t n_events,
+                                     int64_t n_particles, const double *grad_pair_m,
+                                     int64_t n_pairs, const gvx_lv *grad_event_sum,
+                                     gvx_lv *grad_particles, void *stream);
+
+/*
  * gvx_event_pair_masses without a workspace argument, for callers that cannot allocate device
  * memory: code that runs where cudaMalloc is not allowed or not wanted -- inside a host callback
  * or a framework plugin that does not own the allocator, in a pipeline with a fixed memory budget

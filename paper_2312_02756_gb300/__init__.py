@@ -233,21 +233,77 @@ def _jagged_args(particles, lp, offsets, n_events, pair_off, pair_m, n_pairs, su
             ctypes.c_void_p(ws.data_ptr()), ws_bytes)
 
 
+class _EventPairMasses(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, particles, offsets, n_pairs, layout, sums_layout, stream):
+        lp, ls, n_events, pair_off, pair_m, sums, ws, ws_bytes = _jagged_buffers(
+            particles, offsets, n_pairs, layout, sums_layout)
+        lib = load_library()
+        st = lib.gvx_event_pair_masses(*_jagged_args(particles, lp, offsets, n_events, pair_off,
+                                                     pair_m, n_pairs, sums, ls, ws, ws_bytes),
+                                       _stream(stream))
+        _lib.check(st, "gvx_event_pair_masses")
+        ctx.save_for_backward(particles, offsets, pair_off)
+        ctx.codes = (lp, ls, int(n_pairs), stream)
+        ctx.mark_non_differentiable(pair_off)
+        return pair_off, pair_m[:int(n_pairs)], sums
+
+    @staticmethod
+    def backward(ctx, _g_off, g_pm, g_sums):
+        particles, offsets, pair_off = ctx.saved_tensors
+        lp, ls, n_pairs, stream = ctx.codes
+        n_events = offsets.numel() - 1
+        gp = torch.empty_like(particles)
+        if g_pm is None:
+            g_pm = torch.zeros(max(n_pairs, 1), dtype=torch.float64, device=particles.device)
+        g_pm = g_pm.to(torch.float64).contiguous()
+        gs_arg = None
+        if g_sums is not None:
+            g_sums = g_sums.to(torch.float64).contiguous()
+            gs_arg = ctypes.byref(_lv(g_sums, ls, 4))
+        st = load_library().gvx_event_pair_masses_bwd(
+            ctypes.byref(_lv(particles, lp, 4)), ctypes.c_void_p(offsets.data_ptr()),
+            ctypes.c_void_p(pair_off.data_ptr()), n_events, _count(particles, lp),
+            ctypes.c_void_p(g_pm.data_ptr()), n_pairs, gs_arg, ctypes.byref(_lv(gp, lp, 4)),
+            _stream(stream))
+        _lib.check(st, "gvx_event_pair_masses_bwd")
+        return gp, None, None, None, None, None
+
+
 def event_pair_masses(particles: torch.Tensor, offsets: torch.Tensor, n_pairs: int, layout=None,
                       sums_layout=None, stream=None):
     """All in-event pair masses and per-event summed 4-vectors of jagged events (FP64).
 
     ``offsets`` (int64, n_events + 1, on the GPU) delimits the events; ``n_pairs`` is the
     capacity of the pair output (the exact total sum n(n-1)/2 when known).  Returns
-    (pair_offsets, pair_m[:n_pairs], event_sums).  Device-detected problems (malformed offsets,
-    capacity) are reported by ``check_device_status``."""
-    lp, ls, n_events, pair_off, pair_m, sums, ws, ws_bytes = _jagged_buffers(
-        particles, offsets, n_pairs, layout, sums_layout)
-    lib = load_library()
-    st = lib.gvx_event_pair_masses(*_jagged_args(particles, lp, offsets, n_events, pair_off, pair_m,
-                                                 n_pairs, sums, ls, ws, ws_bytes), _stream(stream))
-    _lib.check(st, "gvx_event_pair_masses")
-    return pair_off, pair_m[:int(n_pairs)], sums
+    (pair_offsets, pair_m[:n_pairs], event_sums).  Differentiable with respect to the particles
+    (hand-written adjoint kernel, gvx_event_pair_masses_bwd).  Device-detected problems
+    (malformed offsets, capacity) are reported by ``check_device_status``."""
+    return _EventPairMasses.apply(particles, offsets, int(n_pairs), layout, sums_layout, stream)
+
+
+def event_pair_masses_bwd(particles, offsets, pair_offsets, grad_pair_m, grad_sums=None,
+                          layout=None, sums_layout=None, grad_layout=None, stream=None):
+    """gvx_event_pair_masses_bwd: d/dparticles of sum(grad_pair_m * pair_m) +
+    sum(grad_sums * event_sums); ``grad_sums`` None means zero.  Returns the gradient with the
+    particles' shape (or ``grad_layout``)."""
+    _require_cuda(particles, offsets, pair_offsets, grad_pair_m)
+    lp = _layout_of(particles, 4, layout)
+    lg = lp if grad_layout is None else (AOS if grad_layout in ("aos", AOS) else SOA)
+    n = _count(particles, lp)
+    gp = torch.empty((n, 4) if lg == AOS else (4, n), dtype=torch.float64,
+                     device=particles.device)
+    gs_arg = None
+    if grad_sums is not None:
+        ls = _layout_of(grad_sums, 4, sums_layout)
+        gs_arg = ctypes.byref(_lv(grad_sums, ls, 4))
+    st = load_library().gvx_event_pair_masses_bwd(
+        ctypes.byref(_lv(particles, lp, 4)), ctypes.c_void_p(offsets.data_ptr()),
+        ctypes.c_void_p(pair_offsets.data_ptr()), offsets.numel() - 1, n,
+        ctypes.c_void_p(grad_pair_m.data_ptr()), grad_pair_m.numel(), gs_arg,
+        ctypes.byref(_lv(gp, lg, 4)), _stream(stream))
+    _lib.check(st, "gvx_event_pair_masses_bwd")
+    return gp
 
 
 class EventPairMassesGraph:

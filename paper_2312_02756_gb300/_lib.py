@@ -30,6 +30,7 @@ EXPORTS = (
     "gvx_event_pair_masses_autotune", "gvx_event_pair_masses_graph_create",
     "gvx_graph_launch", "gvx_graph_destroy", "gvx_device_status",
     "gvx_testing_skip_first_tile", "gvx_event_pair_masses_noalloc",
+    "gvx_event_pair_masses_bwd",
 )
 
 
@@ -82,6 +83,7 @@ def _sigs(lib):
         "gvx_device_status": ([P, ctypes.POINTER(I32)], S),
         "gvx_testing_skip_first_tile": ([I32], None),
         "gvx_event_pair_masses_noalloc": ([LVP, P, I64, I64, P, P, I64, LVP, P], S),
+        "gvx_event_pair_masses_bwd": ([LVP, P, P, I64, I64, P, I64, LVP, LVP, P], S),
     }
     for name, (args, res) in table.items():
         fn = getattr(lib, name)

@@ -284,6 +284,29 @@ gvx_status gvx_event_pair_masses(const gvx_lv *particles, const int64_t *offsets
   return enqueue_jagged(c, shape_for(n_events), (cudaStream_t)stream);
 }
 
+gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *offsets,
+                                     const int64_t *pair_offsets, int64_t n_events,
+                                     int64_t n_particles, const double *grad_pair_m,
+                                     int64_t n_pairs, const gvx_lv *grad_event_sum,
+                                     gvx_lv *grad_particles, void *stream) {
+  if (n_events < 0 || n_particles < 0 || n_pairs < 0) return GVX_ERR_SIZE;
+  if (!offsets || !pair_offsets) return GVX_ERR_NULL;
+  if ((uintptr_t)offsets % 8 || (uintptr_t)pair_offsets % 8) return GVX_ERR_ALIGN;
+  if (n_events == 0 || n_particles == 0) return GVX_OK;  // no particle has a gradient
+  GVX_TRY(check_lv(particles, GVX_F64, 4));
+  GVX_TRY(check_lv(grad_particles, GVX_F64, 4));
+  if (grad_event_sum) GVX_TRY(check_lv(grad_event_sum, GVX_F64, 4));
+  if (n_pairs > 0 && !grad_pair_m) return GVX_ERR_NULL;
+  if ((uintptr_t)grad_pair_m % 8) return GVX_ERR_ALIGN;
+  gvx::Lv gs;
+  if (grad_event_sum) gs = gvx::as_in(*grad_event_sum);
+  return from_cuda(gvx::launch_event_pairs_bwd(gvx::as_in(*particles), offsets, pair_offsets,
+                                               n_events, n_particles, grad_pair_m, n_pairs,
+                                               grad_event_sum ? &gs : nullptr,
+                                               gvx::as_out(*grad_particles),
+                                               (cudaStream_t)stream));
+}
+
 int32_t gvx_event_pair_masses_num_shapes(void) { return gvx::event_pairs_num_shapes(); }
 
 gvx_status gvx_event_pair_masses_shape(int32_t shape, int32_t *events_per_tile,

@@ -271,13 +271,15 @@ template <typename T>
 cudaError_t launch_boost_t(const Lv &v, const Lv &beta, int64_t stride, const LvOut &out,
                            int64_t n, cudaStream_t s) {
   const int threads = 256;
-  unsigned grid = grid_for(n, threads, 8);
   dispatch2(v.layout, out.layout, [&](auto LV, auto LO) {
     dispatch2(beta.layout, kSoA, [&](auto LB, auto) {
-      if (stride == 0)
-        boost_kernel<T, LV, LB, LO, true><<<grid, threads, 0, s>>>(v, beta, out, n);
-      else
-        boost_kernel<T, LV, LB, LO, false><<<grid, threads, 0, s>>>(v, beta, out, n);
+      if (stride == 0) {
+        constexpr auto k = boost_kernel<T, LV, LB, LO, true>;
+        k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, beta, out, n);
+      } else {
+        constexpr auto k = boost_kernel<T, LV, LB, LO, false>;
+        k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, beta, out, n);
+      }
     });
   });
   return cudaGetLastError();
@@ -305,15 +307,15 @@ cudaError_t launch_boost_bwd_t(const Lv &v, const Lv &beta, int64_t stride, cons
     return cudaGetLastError();
   }
   const int threads = 256;
-  unsigned grid = grid_for(n, threads, 8);
   dispatch2(v.layout, gout.layout, [&](auto LV, auto LG) {
     dispatch2(beta.layout, gv.layout, [&](auto LB, auto LGV) {
-      if (gbeta.layout == kSoA)
-        boost_bwd_kernel<T, LV, LB, LG, LGV, kSoA><<<grid, threads, 0, s>>>(v, beta, gout, gv,
-                                                                            gbeta, n);
-      else
-        boost_bwd_kernel<T, LV, LB, LG, LGV, kAoS><<<grid, threads, 0, s>>>(v, beta, gout, gv,
-                                                                            gbeta, n);
+      if (gbeta.layout == kSoA) {
+        constexpr auto k = boost_bwd_kernel<T, LV, LB, LG, LGV, kSoA>;
+        k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, beta, gout, gv, gbeta, n);
+      } else {
+        constexpr auto k = boost_bwd_kernel<T, LV, LB, LG, LGV, kAoS>;
+        k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, beta, gout, gv, gbeta, n);
+      }
     });
   });
   return cudaGetLastError();

@@ -54,6 +54,20 @@ __device__ __forceinline__ void st4(const LvOut &v, int64_t i, V4<T> x) {
   }
 }
 
+// The same load through the read-only path with normal caching, for data that other threads
+// read again soon (partners of a particle in an event).
+template <int LAYOUT>
+__device__ __forceinline__ V4<double> ld4c(const Lv &v, int64_t i) {
+  if constexpr (LAYOUT == GVX_SOA) {
+    return {__ldg((const double *)v.c[0] + i), __ldg((const double *)v.c[1] + i),
+            __ldg((const double *)v.c[2] + i), __ldg((const double *)v.c[3] + i)};
+  } else {
+    const double2 *p = (const double2 *)v.c[0] + 2 * i;
+    double2 a = __ldg(p), b = __ldg(p + 1);
+    return {a.x, a.y, b.x, b.y};
+  }
+}
+
 // Velocities: SoA c[0..2] or packed triples at c[0].  `i` is already multiplied by the stride.
 template <typename T, int LAYOUT>
 __device__ __forceinline__ V3<T> ld3(const Lv &v, int64_t i) {
@@ -88,10 +102,18 @@ inline unsigned grid_for(int64_t n, int threads, int per_sm) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-// Grid for a grid-stride kernel that keeps every SM full: the CTAs that can be resident at
-// once (occupancy query, cached per kernel by the caller's static), never more than the work.
+// CTAs per resident slot for grid-stride kernels.  With several times more CTAs than fit at once,
+// the hardware block scheduler hands the work out in smaller pieces and evens out SMs that run
+// ahead or behind; on GB300 a grid of exactly one resident wave finished 9-10% later than eight
+// waves on the FP64 mass and boost kernels (and sixteen waves gained nothing more).
+constexpr int kWaves = 8;
+
+// Grid for a grid-stride kernel: kWaves times the CTAs that can be resident at once (occupancy
+// query, cached per kernel by the caller's static), never more than the work (n elements,
+// per_block per CTA and pass; 0 means one per thread).
 template <typename Kernel>
-inline unsigned resident_grid(Kernel k, int threads, size_t smem, int64_t n, int *cache) {
+inline unsigned balanced_grid(Kernel k, int threads, size_t smem, int64_t n, int *cache,
+                              int64_t per_block = 0) {
   if (*cache <= 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess ||
@@ -99,10 +121,20 @@ inline unsigned resident_grid(Kernel k, int threads, size_t smem, int64_t n, int
       per_sm = 1;
     *cache = per_sm;
   }
-  int64_t need = (n + threads - 1) / threads;
-  int64_t cap = (int64_t)num_sms() * *cache;
+  if (per_block <= 0) per_block = threads;
+  int64_t need = (n + per_block - 1) / per_block;
+  int64_t cap = (int64_t)num_sms() * *cache * kWaves;
   int64_t g = need < cap ? need : cap;
   return (unsigned)(g < 1 ? 1 : g);
+}
+
+// balanced_grid for one kernel instantiation, its occupancy cached per device.
+template <auto Kernel>
+inline unsigned balanced_grid_of(int threads, size_t smem, int64_t n, int64_t per_block = 0) {
+  static int occ[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return balanced_grid(Kernel, threads, smem, n, &occ[dev & 63], per_block);
 }
 
 // Record a device-detected error (the first one since the last read wins).

@@ -1,5 +1,6 @@
-// Pair-mass arithmetic shared by the elementwise kernel (mass.cu) and the jagged-event kernel
-// (jagged.cu), so that both give the same bits for the same two particles.
+// Pair-mass arithmetic (and its adjoint) shared by the elementwise kernels (mass.cu) and the
+// jagged-event kernels (jagged.cu, jagged_bwd.cu), so that both give the same bits for the same
+// two particles.
 //
 // GenVectorX (Sec. 4.1, Fig. 1) forms mass((pt1,eta1,phi1,m1) + (pt2,eta2,phi2,m2)).  The plain
 // form sqrt(E^2 - |P|^2) cancels catastrophically for light, collinear pairs; this uses
@@ -88,6 +89,57 @@ __device__ __forceinline__ PairTerms<T> pair_terms(const Leg<T> &a, const Leg<T>
   T ta = (T)4 * a.pt * b.pt * t.S;
   t.m2 = a.q + b.q + tm + ta;
   return t;
+}
+
+// Adjoint of the pair mass.  With S = sinh^2(d_eta/2) + sin^2(d_phi/2) and
+//   X = (P1^2 m2^2 - P2^2 m1^2) / ((P1 E2 + P2 E1) E1)      (= P1 E2/E1 - P2, without cancellation)
+// the derivatives of m^2 with respect to leg 1 are
+//   d/dpt1  = 4 pt2 S + 2 cosh(eta1) X
+//   d/deta1 = 2 pt1 (pt2 sinh(d_eta) + sinh(eta1) X)
+//   d/dphi1 = 2 pt1 pt2 sin(d_phi)
+//   d/dm1   = 2 m1 (E1 + E2) / E1
+// and leg 2 follows by exchanging the legs (d_eta, d_phi change sign).  dm = d(m^2) / (2 m);
+// where m = 0 the gradient is 0.  A massless leg has E = pt cosh(eta), and at pt = 0 its
+// one-sided (pt >= 0) derivatives are used: X -> m_o^2 / (E_o + P_o), d/dm = 0.
+template <typename T>
+__device__ __forceinline__ V4<T> leg_grad(const Leg<T> &s, const Leg<T> &o, T S, T sdeta, T sdphi,
+                                          T scale) {
+  // X = P_s E_o / E_s - P_o.  Its denominator vanishes (with E_s > 0) only when P_o = 0 and
+  // either E_o = 0 (the other leg is the zero vector) or P_s = 0 (both legs at rest); X = 0 there.
+  T X;
+  if (s.E > (T)0) {
+    T den = (s.P * o.E + o.P * s.E) * s.E;
+    X = den > (T)0 ? (s.P * s.P * o.q - o.P * o.P * s.q) / den : (T)0;
+  } else {
+    X = (o.E + o.P) > (T)0 ? o.q / (o.E + o.P) : (T)0;
+  }
+  T ch = cosh_(s.eta), sh = sinh_(s.eta);
+  V4<T> g;
+  g.x = scale * ((T)4 * o.pt * S + (T)2 * ch * X);
+  g.y = scale * ((T)2 * s.pt * (o.pt * sdeta + sh * X));
+  g.z = scale * ((T)2 * s.pt * o.pt * sdphi);
+  g.w = s.E > (T)0 ? scale * ((T)2 * s.m * (s.E + o.E) / s.E) : (T)0;
+  return g;
+}
+
+// g * dm/d(pt, eta, phi, m) of leg a (g1) and leg b (g2), in the working precision T.
+template <typename T>
+__device__ __forceinline__ void pair_mass_grad(V4<T> x, V4<T> y, T g, V4<T> &g1, V4<T> &g2) {
+  Leg<T> la = make_leg(x), lb = make_leg(y);
+  PairTerms<T> t = pair_terms(la, lb);
+  T m = sqrt_(t.m2);
+  g1 = {0, 0, 0, 0};
+  g2 = {0, 0, 0, 0};
+  if (m > (T)0) {
+    T scale = g / ((T)2 * m);
+    // sinh(d_eta) = 2 sinh(d_eta/2) cosh(d_eta/2); sin(d_phi) = 2 sin(d_phi/2) cos(d_phi/2)
+    T ce = sqrt_((T)1 + t.se * t.se);
+    T sgn;
+    T cp = cos_(half_dphi(la.phi, lb.phi, &sgn));
+    T sdeta = (T)2 * t.se * ce, sdphi = sgn * (T)2 * t.sp * cp;
+    g1 = leg_grad(la, lb, t.S, sdeta, sdphi, scale);
+    g2 = leg_grad(lb, la, t.S, -sdeta, -sdphi, scale);
+  }
 }
 
 }  // namespace gvx
