@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
           l.pt = ffm::from_double_ranged(pt, sc);
           l.q = ffm::sqr(ffm::from_double_ranged(m, sc));
           ffm::ff sn, cs;
-          const ffm::ff eta_f = ffm::from_double(eta, &ok);
+          const ffm::ff eta_f = ffm::from_double_ranged(eta, 0);
           const ffm::ff sh = ffm::sinh_t(eta_f, T);
           ffm::sincos_t(phi, T, &sn, &cs, &ok);
           l.P = ffm::mul(l.pt, ffm::cosh_t(eta_f, T));  // as make_leg_ff: bitwise the same leg

@@ -80,7 +80,7 @@ GVX_HD ff half_dphi_ff(double phi1, double phi2, bool *ok, bool *wrapped = nullp
   const double y = (pid - fabs(phi1)) + (pid - fabs(phi2));
   const bool w = !within_pi(d);
   if (wrapped) *wrapped = w;
-  ff h = from_double(w ? y : d, ok);
+  ff h = from_double_ranged(w ? y : d, 0);  // 0 <= d, y <= 2 pi; below 2^-74 counts as 0
   h = add_small(h, make(w ? kTwoPiLo : 0.0f));
   return scale(h, 0.5f);
 }
@@ -94,7 +94,7 @@ GVX_HD LegFF make_leg_ff(double pt, double eta, double m, int s, const TabRef &T
   LegFF l;
   l.pt = from_double_ranged(pt, s);
   l.q = sqr(from_double_ranged(m, s));
-  l.P = mul(l.pt, cosh_t(from_double(eta, ok), T));
+  l.P = mul(l.pt, cosh_t(from_double_ranged(eta, 0), T));  // |eta| < 16
   l.E2 = add_same(sqr(l.P), l.q);
   return l;
 }
@@ -107,7 +107,7 @@ GVX_HD ff pair_m2_ff(const LegFF &a, const LegFF &b, double eta1, double eta2, d
   ff num = add_same(mul(a.q, b.E2), mul(b.q, sqr(a.P)));
   ff tm = den.hi > 0.0f ? scale(div(num, den), 2.0f) : make(0.0f);
   // 4 pt1 pt2 (sinh^2(d_eta/2) + sin^2(d_phi/2)); d_eta in FP64 is exact where it cancels
-  ff se = sinh_t(scale(from_double(eta1 - eta2, ok), 0.5f), T);
+  ff se = sinh_t(scale(from_double_ranged(eta1 - eta2, 0), 0.5f), T);
   ff sp = sin_t(half_dphi_ff(phi1, phi2, ok), T);
   ff ta = scale(mul(mul(a.pt, b.pt), add_same(sqr(se), sqr(sp))), 4.0f);
   return renorm(add_same(add_same(add_same(a.q, b.q), tm), ta));

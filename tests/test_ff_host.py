@@ -146,6 +146,21 @@ def test_ff_unchecked_conversion_and_tiny_legs(ffh):
     assert m[2] == 1e-290 and m[3] == 0.0 and m[4] == 0.0  # a massless leg alone has m = 0
 
 
+def test_ff_pair_mass_tiny_angles(ffh, orc):
+    """Angles and angle differences below 2^-74 enter the ff path as exact zeros (their share of
+    m^2 is below 2^-148 of pt1 pt2): such pairs stay on the fast path and keep the gate."""
+    pi_d = float(np.pi)
+    a = np.array([[50.0, 1e-30, 0.3, 1.0], [50.0, 1e-300, 0.3, 0.0], [40.0, 2.0, pi_d, 0.5],
+                  [40.0, 2.0, 1e-300, 0.5], [10.0, -3.0, -pi_d, 2.0], [7.0, 1e-25, -1e-25, 0.0]])
+    b = np.array([[60.0, -1e-30, 1.3, 2.0], [50.0, -1e-300, 0.3, 0.0], [30.0, 2.0, -pi_d, 0.0],
+                  [30.0, 2.0 + 1e-20, -1e-300, 0.5], [12.0, -3.0, pi_d, 3.0], [9.0, -1e-25, 1e-25, 0.0]])
+    m, ok = _mass(ffh, a, b)
+    ref = orc.mass_def(a, b)
+    assert ok.all()
+    e = lambda x: np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
+    assert np.all(np.abs(m - ref) <= 1e-13 * np.abs(ref) + 1e-16 * (e(a) + e(b)))
+
+
 def test_ff_boost_coefficients(ffh):
     """gamma = 1/sqrt(1 - b2) and w = gamma/(1 + gamma) of the FP64 boost, from the exact
     fixed-point 1 - b2, against mpmath."""
