@@ -3,8 +3,9 @@
 
 One step = the FP64 workload at N = 2^26: invariant mass of 2^26 PtEtaPhiM pairs in SoA, the
 same in AoS (32-byte structs), and the boost of 2^26 PxPyPzE vectors, each by its own velocity
-(GenVectorX Sec. 5.1: "invariant masses from two arrays of particles" and "boosting of one
-array").  Inputs are resident in HBM and larger than L2, so no flush is needed between steps.
+(the two kernels GenVectorX benchmarks in Sec. 5.1: pair masses from two particle arrays, and the
+boost of a single array).  Inputs are resident in HBM and larger than L2, so no flush is needed
+between steps.
 
 Printed on rank 0 as one JSON line: whole-job outputs/s (pair masses + boosted vectors), the
 roofline of the dominant kernel (per-launch CUDA events on the launching stream), the CPU
@@ -42,6 +43,21 @@ BYTES_MASS_F64 = 72    # 2 legs x 4 doubles in + 1 double out, per pair
 BYTES_BOOST_F64 = 88   # 4 doubles in + 3 doubles beta + 4 doubles out, per vector
 BYTES_MASS_F32 = 36
 BYTES_BOOST_F32 = 44
+
+
+def max_over_ranks(torch, dist, value, device):
+    """The largest per-rank value (a step time) over the process group; the value itself when
+    there is no group.  Whole-job rates divide all ranks' units by this time."""
+    if dist is None:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
 
 
 def _peaks():
@@ -328,7 +344,7 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
 
 # ------------------------------------------------------------------------------------------ e2e
 
-def e2e(torch, gvx, a, b, v, beta, steps=3, warmup=1):
+def e2e(torch, gvx, a, b, v, beta, steps=3, warmup=1, dist=None, world=1):
     """The step through the C ABI with HOST buffers: the same three calls, given pinned host
     pointers for every input and output, so each kernel streams its inputs over the host link
     and writes its outputs back over it (both directions at once) inside the timed region.
@@ -355,8 +371,11 @@ def e2e(torch, gvx, a, b, v, beta, steps=3, warmup=1):
                Step._lv(host["a_aos"], 1, 4), Step._lv(host["b_aos"], 1, 4),
                Step._lv(host["v"], 0, 4), Step._lv(host["beta"], 0, 3), Step._lv(host["out"], 0, 4)]
     step.names = ["mass_f64_soa", "mass_f64_aos", "boost_f64_soa"]
-    ms = time_loop(torch, lambda: step(stream), stream, steps, warmup)
-    res = {"value": 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(torch, dist, time_loop(torch, lambda: step(stream), stream, steps, warmup),
+                        "cuda")
+    res = {"value": job_rate(3 * n, world, ms), "unit": UNIT, "ms_per_step": ms,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "how": "the C-ABI calls given pinned host pointers: inputs read and outputs written by "
                   "the kernels across the host link inside the timed region"}
@@ -433,15 +452,11 @@ def run_gvx(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, e0.elapsed_time(e1) / args.steps, "cuda")
     per_kernel = [statistics.mean(ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps))
                   for j in range(3)]
     units = 3 * N_FULL
-    value = units * world / (ms * 1e-3)
+    value = job_rate(units, world, ms)
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     kern = {}
@@ -472,8 +487,10 @@ def run_gvx(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "kernels": kern, "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clk,
     }
-    if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e(torch, gvx, a, b, v, beta)
+    if not args.no_e2e:  # every rank streams its own replica over its host link
+        res = e2e(torch, gvx, a, b, v, beta, dist=dist, world=world)
+        if rank == 0:
+            line["e2e"] = res
     if rank == 0 and not args.no_cpu:
         rate, cores, tm, tb = cpu_oracle_rate(a, b, v, beta)
         line["cpu_baseline"] = {

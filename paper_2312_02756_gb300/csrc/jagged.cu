@@ -9,12 +9,13 @@
 //      (bounded wait: a predecessor that never publishes makes the CTA record GVX_ERR_TIMEOUT
 //      and go on);  write pair_offsets;
 //   3. stage the tile's particles in shared memory in sub-batches of at most kCP particles:
-//      per-particle terms once per particle -- the float-float leg (pt, P = pt cosh(eta), m^2,
-//      E^2, scaled by the event's power of two) and the Cartesian components for the sums --
-//      then the event sums (one thread per event, FP64) and the pair masses (one thread per pair
-//      over the flattened pair range of the sub-batch, coalesced stores) with the same
-//      float-float pair arithmetic as the elementwise FP64 kernel (mass_ff.cuh), falling back
-//      to FP64 for pairs outside its domain;
+//      per-particle terms once per particle (one thread each, which also finds its event's
+//      scale) -- the float-float leg (pt, P = pt cosh(eta), m^2, E^2, scaled by the event's
+//      power of two) and the Cartesian components for the sums -- then, after one barrier, the
+//      event sums (one thread per event, FP64) and the pair masses (one thread per pair over the
+//      flattened pair range of the sub-batch, coalesced stores) with the same float-float pair
+//      arithmetic as the elementwise FP64 kernel (mass_ff.cuh), falling back to FP64 for pairs
+//      outside its domain;
 //   4. an event with more than kCP particles is handled alone, straight from global memory.
 // Tile descriptors are 64-bit words: 2 flag bits (aggregate / inclusive prefix) + 62-bit value.
 #include <cuda_runtime.h>
@@ -31,8 +32,9 @@ namespace gvx {
 namespace {
 
 constexpr int kCP = 384;  // particles staged in shared memory per sub-batch
-// per particle: eta, phi, px, py, pz, E (doubles), pt, P, q, E2 (float pairs), scale (int)
-constexpr size_t kDynSmem = (size_t)kCP * (6 * sizeof(double) + 4 * sizeof(float2) + sizeof(int));
+// per particle: eta, phi, px, py, pz, E (doubles), pt, P, q, E2 (float pairs), leg exponent and
+// scale (ints)
+constexpr size_t kDynSmem = (size_t)kCP * (6 * sizeof(double) + 4 * sizeof(float2) + 2 * sizeof(int));
 constexpr int kNoFast = INT_MIN;  // scale marker of a particle outside the float-float domain
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
   double *s_pz = s_py + kCP, *s_E = s_pz + kCP;
   ffm::ff *s_pt = reinterpret_cast<ffm::ff *>(s_E + kCP), *s_P = s_pt + kCP, *s_q = s_P + kCP;
   ffm::ff *s_E2 = s_q + kCP;
-  int *s_sc = reinterpret_cast<int *>(s_E2 + kCP);
+  int *s_sc = reinterpret_cast<int *>(s_E2 + kCP), *s_fs = s_sc + kCP;
   __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
   __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
   __shared__ int64_t s_off[TE + 1];
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
         continue;
       }
       const int np = (int)(s_off[sbe] - pb);
-      // (a) raw particles; pt and m parked in the px/py slots until the event scale is known
+      // (a) raw particles; pt and m parked in the px/py slots, the leg exponent in s_sc
       for (int k = threadIdx.x; k < np; k += NT) {
         V4<double> v = ld4<double, LP>(A.p, pb + k);
         s_eta[k] = v.y;
@@ -283,22 +285,23 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
         s_sc[k] = ffm::leg_exponent(v.x, v.w);
       }
       __syncthreads();
-      // (b) one thread per event: the event's scale, and which particles the fast path takes
-      for (int e = sb + threadIdx.x; e < sbe; e += NT) {
-        const int k0 = (int)(s_off[e] - pb), k1 = (int)(s_off[e + 1] - pb);
-        int emax = 0;
-        for (int k = k0; k < k1; k++) emax = s_sc[k] > emax ? s_sc[k] : emax;
-        for (int k = k0; k < k1; k++) {
-          bool fast = ffm::scale_exponent_ok(emax) &&
-                      ffm::leg_in_domain(s_px[k], s_eta[k], s_phi[k], s_py[k], emax);
-          s_sc[k] = fast ? emax - 1023 : kNoFast;
-        }
-      }
-      __syncthreads();
-      // (c) per-particle terms
+      // (b) one thread per particle: its event's scale (the largest leg exponent over the event,
+      // from s_sc), whether the fast path takes it (the final scale goes to s_fs, so s_sc stays
+      // intact for the other particles of the event), and its per-particle terms
       for (int k = threadIdx.x; k < np; k += NT) {
-        const double pt = s_px[k], m = s_py[k], eta = s_eta[k], phi = s_phi[k];
-        const int sc = s_sc[k];
+        int lo = sb, hi = sbe - 1;  // the particle's event: the last e with s_off[e] <= pb + k
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= pb + k) lo = mid;
+          else hi = mid - 1;
+        }
+        int emax = 0;
+        for (int t = (int)(s_off[lo] - pb); t < (int)(s_off[lo + 1] - pb); t++)
+          emax = s_sc[t] > emax ? s_sc[t] : emax;
+        const double pt = s_px[k], eta = s_eta[k], phi = s_phi[k], m = s_py[k];
+        int sc = ffm::scale_exponent_ok(emax) && ffm::leg_in_domain(pt, eta, phi, m, emax)
+                     ? emax - 1023
+                     : kNoFast;
         bool ok = true;
         if (sc != kNoFast) {
           ffm::LegFF l;
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
           s_E[k] = ffm::to_double(ffm::sqrt(l.E2), sc);
         }
         if (sc == kNoFast || !ok) {  // FP64 evaluation
-          s_sc[k] = kNoFast;
+          sc = kNoFast;
           double sphi, cphi;
           sincos(phi, &sphi, &cphi);
           s_px[k] = pt * cphi;
@@ -328,6 +331,7 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
           s_pz[k] = pt * sinh(eta);
           s_E[k] = make_leg(V4<double>{pt, eta, phi, m}).E;
         }
+        s_fs[k] = sc;
       }
       __syncthreads();
       for (int e = sb + threadIdx.x; e < sbe; e += NT) {
@@ -356,8 +360,8 @@ __global__ void __launch_bounds__(NT) event_pairs_kernel(JArgs A) {
         const int ia = (int)(s_off[lo] - pb + i), ib = (int)(s_off[lo] - pb + j);
         double mass;
         bool done = false;
-        const int sc = s_sc[ia];
-        if (sc != kNoFast && s_sc[ib] != kNoFast) {
+        const int sc = s_fs[ia];
+        if (sc != kNoFast && s_fs[ib] != kNoFast) {
           bool ok = true;
           ffm::LegFF a{s_pt[ia], s_P[ia], s_q[ia], s_E2[ia]};
           ffm::LegFF b{s_pt[ib], s_P[ib], s_q[ib], s_E2[ib]};
