@@ -8,14 +8,21 @@
 // J_i = d(px, py, pz, E)/d(pt, eta, phi, m) of the particle.
 //
 // One thread per particle accumulates its own gradient over its partners in a fixed order, so the
-// result does not depend on scheduling and no atomics are needed.  Each pair is therefore
-// evaluated twice (once from each side).  CTAs take tiles of kTE consecutive events (grid-stride
-// over tiles); the pair gradient is the float-float one of the elementwise FP64 adjoint
-// (mass_ff.cuh) with the FP64 formulas for pairs outside its domain; the Jacobian rows come from
-// the float-float sin/cos/sinh/cosh tables and are combined in FP64.  The pair offsets are those
-// the forward call wrote; each tile checks them (and the offsets) against the event sizes and the
-// pair count before it reads any pair gradient, and records GVX_ERR_OFFSETS for a tile that does
-// not match (its particles' gradients are then not written).
+// result does not depend on scheduling and no atomics are needed; each pair is therefore
+// evaluated from both sides, but each side computes only its own leg's gradient.  CTAs take tiles
+// of kTE consecutive events (grid-stride over tiles) and stage them in sub-batches of whole
+// events of at most kNT particles: per particle once, its raw values, the event's scale and the
+// float-float leg terms (mass_ff.cuh, leg_grad_prep) go to shared memory, and its event-sum part
+// (the Jacobian rows from the float-float tables) starts a float-float accumulator.  After one
+// barrier every particle walks its partners with the float-float pair gradient
+// (pair_grad_terms, leg_grad_terms), adding to that accumulator at the event's scale, and
+// converts it to double once at the end; pairs outside the float-float domain use the FP64
+// formulas and a separate FP64 accumulator.  (The FP64 pipe is the scarce one: per directed pair
+// this leaves the FP64 differences of the angles only.)
+// An event with more than kNT particles is handled alone, straight from global memory.  The
+// pair offsets are those the forward call wrote; each tile checks them (and the offsets) against
+// the event sizes and the pair count before it reads any pair gradient, and records
+// GVX_ERR_OFFSETS for a tile that does not match (its particles' gradients are then not written).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -25,8 +32,11 @@
 namespace gvx {
 namespace {
 
-constexpr int kTE = 32;    // events per tile
-constexpr int kNT = 256;   // threads per CTA
+constexpr int kTE = 28;    // events per tile (about 224 particles at the benchmark multiplicity)
+constexpr int kNT = 256;   // threads per CTA, and particles staged per sub-batch
+constexpr int kNoFast = -100000;  // scale marker of a particle outside the float-float domain
+// per staged particle: pt, eta, phi, m (doubles), the ff leg terms, leg exponent and scale (ints)
+constexpr size_t kDynSmem = (size_t)kNT * (4 * sizeof(double) + sizeof(ffm::LegGradFF) + 2 * sizeof(int));
 
 struct BArgs {
   Lv p;
@@ -81,18 +91,79 @@ __device__ __forceinline__ V4<double> sum_part(V4<double> x, V4<double> gs, cons
   return g;
 }
 
+// gm-weighted gradient of particle i's leg over its partners in one event, everything read from
+// global memory (the path of events too large to stage).
+// The same J^T gs for a particle on the float-float path, from its prepared leg (scaled by 2^-sc)
+// and returned in the accumulator convention of leg_grad_terms (components 1 and 2 times 2^-sc).
+// False when an upstream component is outside the ff range (the caller then uses sum_part).
+__device__ __forceinline__ bool sum_part_ff(const ffm::LegGradFF &L, double phi, V4<double> gs,
+                                            const ffm::TabRef &T, ffm::ff *out) {
+  using namespace ffm;
+  bool ok = true;
+  ff sn, cs;
+  sincos_t(phi, T, &sn, &cs, &ok);
+  const ff gx = from_double(gs.x, &ok), gy = from_double(gs.y, &ok);
+  const ff gz = from_double(gs.z, &ok), gE = from_double(gs.w, &ok);
+  if (!ok) return false;
+  ff e0, e1, e3;  // E row: d/dpt, d/deta (times 2^-sc), d/dm
+  if (L.m.hi == 0.0f) {
+    e0 = L.ch;
+    e1 = mul(L.pt, L.sh);
+    e3 = make(0.0f);
+  } else {
+    const ff rE = recip(L.E);
+    e0 = mul(mul(L.P, L.ch), rE);
+    e1 = mul(mul(L.P, mul(L.pt, L.sh)), rE);
+    e3 = mul(L.m, rE);
+  }
+  out[0] = add(add(mul(gx, cs), mul(gy, sn)), add(mul(gz, L.sh), mul(gE, e0)));
+  out[1] = add(mul(gz, L.P), mul(gE, e1));
+  out[2] = mul(L.pt, add(mul(gy, cs), neg(mul(gx, sn))));
+  out[3] = mul(gE, e3);
+  return true;
+}
+
+template <int LP>
+__device__ __forceinline__ void partners_from_global(const BArgs &A, const ffm::TabRef &T,
+                                                     int64_t i, int64_t base, int64_t n,
+                                                     int64_t pair0, double *acc) {
+  const V4<double> x = ld4c<LP>(A.p, i);
+  const int64_t li = i - base;
+  for (int64_t lj = 0; lj < n; lj++) {
+    if (lj == li) continue;
+    const int64_t r = li < lj ? li : lj, q = li < lj ? lj : li;
+    const double g = __ldg(A.gpm + pair0 + r * n - r * (r + 1) / 2 + (q - r - 1));
+    const V4<double> y = ld4c<LP>(A.p, base + lj);
+    double o[8];
+    if (!ffm::pair_mass_grad_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
+      V4<double> g1, g2;
+      pair_mass_grad(x, y, g, g1, g2);
+      o[0] = g1.x;
+      o[1] = g1.y;
+      o[2] = g1.z;
+      o[3] = g1.w;
+    }
+    for (int c = 0; c < 4; c++) acc[c] += o[c];
+  }
+}
+
 template <int LP, int LS, int LG>
-__global__ void __launch_bounds__(kNT) event_pairs_bwd_kernel(BArgs A) {
+__global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
+  extern __shared__ double s_dyn[];
+  double *s_pt = s_dyn, *s_eta = s_pt + kNT, *s_phi = s_eta + kNT, *s_m = s_phi + kNT;
+  ffm::LegGradFF *s_leg = reinterpret_cast<ffm::LegGradFF *>(s_m + kNT);
+  int *s_ex = reinterpret_cast<int *>(s_leg + kNT), *s_fs = s_ex + kNT;
   __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
   __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
   __shared__ int64_t s_off[kTE + 1], s_poff[kTE + 1];
   __shared__ int s_bad;
   const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
   const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
+  const int k = threadIdx.x;  // the particle this thread stages in every sub-batch
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t e0 = tile * kTE;
     const int ne = (int)(A.n_events - e0 < kTE ? A.n_events - e0 : kTE);
-    __syncthreads();  // the previous tile is done with s_off / s_poff
+    __syncthreads();  // the previous tile is done with the shared arrays
     if (threadIdx.x == 0) s_bad = 0;
     if (threadIdx.x <= ne) {
       s_off[threadIdx.x] = A.off[e0 + threadIdx.x];
@@ -112,46 +183,115 @@ __global__ void __launch_bounds__(kNT) event_pairs_bwd_kernel(BArgs A) {
       if (threadIdx.x == 0) raise_status(A.status, GVX_ERR_OFFSETS);
       continue;
     }
-    const int64_t pbeg = s_off[0], np = s_off[ne] - pbeg;
-    for (int64_t k = threadIdx.x; k < np; k += kNT) {
-      const int64_t i = pbeg + k;
-      int lo = 0, hi = ne - 1;  // the event: the last e with s_off[e] <= i
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= i) lo = mid; else hi = mid - 1;
-      }
-      const int e = lo;
-      const int64_t base = s_off[e], n = s_off[e + 1] - base, li = i - base;
-      const V4<double> x = ld4c<LP>(A.p, i);
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int64_t lj = 0; lj < n; lj++) {
-        if (lj == li) continue;
-        const int64_t r = li < lj ? li : lj, q = li < lj ? lj : li;
-        const double g = __ldg(A.gpm + s_poff[e] + r * n - r * (r + 1) / 2 + (q - r - 1));
-        const V4<double> y = ld4c<LP>(A.p, base + lj);
-        double o[8];
-        if (!ffm::pair_mass_grad_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
-          V4<double> g1, g2;
-          pair_mass_grad(x, y, g, g1, g2);
-          o[0] = g1.x;
-          o[1] = g1.y;
-          o[2] = g1.z;
-          o[3] = g1.w;
+    int sb = 0;
+    while (sb < ne) {
+      const int64_t pbeg = s_off[sb];
+      const bool fits =
+          threadIdx.x >= sb && threadIdx.x < ne && s_off[threadIdx.x + 1] - pbeg <= kNT;
+      const int sbe = sb + __syncthreads_count(fits);
+      if (sbe == sb) {  // one event larger than a sub-batch
+        const int64_t n = s_off[sb + 1] - pbeg;
+        for (int64_t t = threadIdx.x; t < n; t += kNT) {
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};
+          const V4<double> x = ld4c<LP>(A.p, pbeg + t);
+          if (A.has_gsum) {
+            const V4<double> sp = sum_part(x, ld4c<LS>(A.gsum, e0 + sb), T);
+            acc[0] = sp.x;
+            acc[1] = sp.y;
+            acc[2] = sp.z;
+            acc[3] = sp.w;
+          }
+          partners_from_global<LP>(A, T, pbeg + t, pbeg, n, s_poff[sb], acc);
+          st4<double, LG>(A.grad, pbeg + t, V4<double>{acc[0], acc[1], acc[2], acc[3]});
         }
-        acc[0] += o[0];
-        acc[1] += o[1];
-        acc[2] += o[2];
-        acc[3] += o[3];
+        sb++;
+        __syncthreads();
+        continue;
       }
-      if (A.has_gsum) {
-        const V4<double> gsv = ld4c<LS>(A.gsum, e0 + e);
-        const V4<double> sp = sum_part(x, gsv, T);
-        acc[0] += sp.x;
-        acc[1] += sp.y;
-        acc[2] += sp.z;
-        acc[3] += sp.w;
+      const int np = (int)(s_off[sbe] - pbeg);
+      // (a) raw particles and their leg exponents
+      V4<double> x = {0.0, 0.0, 0.0, 0.0};
+      if (k < np) {
+        x = ld4c<LP>(A.p, pbeg + k);
+        s_pt[k] = x.x;
+        s_eta[k] = x.y;
+        s_phi[k] = x.z;
+        s_m[k] = x.w;
+        s_ex[k] = ffm::leg_exponent(x.x, x.w);
       }
-      st4<double, LG>(A.grad, i, V4<double>{acc[0], acc[1], acc[2], acc[3]});
+      __syncthreads();
+      // (b) the particle's event and scale, its ff leg terms, and its event-sum part
+      ffm::ff acc_f[4] = {ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f)};
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};  // FP64 contributions (pairs off the fast path)
+      int e = sb, sc = kNoFast;
+      if (k < np) {
+        int hi = sbe - 1;  // the particle's event: the last e with s_off[e] <= pbeg + k
+        while (e < hi) {
+          const int mid = (e + hi + 1) >> 1;
+          if (s_off[mid] <= pbeg + k) e = mid;
+          else hi = mid - 1;
+        }
+        int emax = 0;
+        for (int t = (int)(s_off[e] - pbeg); t < (int)(s_off[e + 1] - pbeg); t++)
+          emax = s_ex[t] > emax ? s_ex[t] : emax;
+        ffm::LegGradFF L;
+        if (ffm::scale_exponent_ok(emax) && ffm::leg_in_domain(x.x, x.y, x.z, x.w, emax)) {
+          bool ok = true;
+          L = ffm::leg_grad_prep(x.x, x.y, x.w, emax - 1023, T, &ok);
+          if (ok) {
+            sc = emax - 1023;
+            s_leg[k] = L;
+          }
+        }
+        s_fs[k] = sc;
+        if (A.has_gsum) {
+          const V4<double> gsv = ld4c<LS>(A.gsum, e0 + e);
+          if (sc == kNoFast || !sum_part_ff(L, x.z, gsv, T, acc_f)) {
+            const V4<double> sp = sum_part(x, gsv, T);
+            acc[0] = sp.x;
+            acc[1] = sp.y;
+            acc[2] = sp.z;
+            acc[3] = sp.w;
+          }
+        }
+      }
+      __syncthreads();
+      // (c) the partners, in order; fast-path terms accumulate in ff at the event's scale
+      if (k < np) {
+        const int b0 = (int)(s_off[e] - pbeg);
+        const int64_t n = s_off[e + 1] - s_off[e], li = k - b0, pair0 = s_poff[e];
+        for (int64_t lj = 0; lj < n; lj++) {
+          if (lj == li) continue;
+          const int64_t r = li < lj ? li : lj, q = li < lj ? lj : li;
+          const double g = __ldg(A.gpm + pair0 + r * n - r * (r + 1) / 2 + (q - r - 1));
+          const int j = b0 + (int)lj;
+          int done = 0;
+          if (sc != kNoFast && s_fs[j] != kNoFast) {
+            const ffm::LegGradFF &a = s_leg[k], &b = s_leg[j];
+            ffm::PairGradFF pg;
+            done = ffm::pair_grad_terms(a, b, x.y, s_eta[j], x.z, s_phi[j], g, T, &pg);
+            if (done == 2) {
+              ffm::ff t[4];
+              ffm::leg_grad_terms(a, b, pg, pg.sdeta, pg.sdphi, t);
+              for (int c = 0; c < 4; c++) acc_f[c] = ffm::add(acc_f[c], t[c]);
+            }
+          }
+          if (!done) {
+            V4<double> g1, g2;
+            pair_mass_grad(x, V4<double>{s_pt[j], s_eta[j], s_phi[j], s_m[j]}, g, g1, g2);
+            acc[0] += g1.x;
+            acc[1] += g1.y;
+            acc[2] += g1.z;
+            acc[3] += g1.w;
+          }
+        }
+        double out[4] = {0.0, 0.0, 0.0, 0.0};
+        if (sc != kNoFast) ffm::leg_grad_out(acc_f, sc, out);
+        st4<double, LG>(A.grad, pbeg + k,
+                        V4<double>{out[0] + acc[0], out[1] + acc[1], out[2] + acc[2], out[3] + acc[3]});
+      }
+      __syncthreads();  // before the next sub-batch overwrites the staged particles
+      sb = sbe;
     }
   }
 }
@@ -159,9 +299,12 @@ __global__ void __launch_bounds__(kNT) event_pairs_bwd_kernel(BArgs A) {
 template <int LP, int LS, int LG>
 cudaError_t launch_l(const BArgs &A, cudaStream_t s) {
   constexpr auto k = event_pairs_bwd_kernel<LP, LS, LG>;
+  cudaError_t err =
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+  if (err != cudaSuccess) return err;
   const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
-  const unsigned grid = balanced_grid_of<k>(kNT, 0, n_tiles, 1);  // one tile per CTA and pass
-  k<<<grid, kNT, 0, s>>>(A);
+  const unsigned grid = balanced_grid_of<k>(kNT, kDynSmem, n_tiles, 1);  // one tile per CTA and pass
+  k<<<grid, kNT, kDynSmem, s>>>(A);
   return cudaGetLastError();
 }
 

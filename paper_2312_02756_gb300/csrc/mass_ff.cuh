@@ -167,6 +167,88 @@ GVX_HD ff leg_x(const LegGradFF &s, const LegGradFF &o) {
   return eo.hi > 0.0f ? div(o.q, eo) : make(0.0f);
 }
 
+// Pair-level terms of the gradient: c = gm / (2 m) (times 2^s), S, sinh(d_eta), sin(d_phi).
+struct PairGradFF {
+  ff c, S, sdeta, sdphi;
+};
+
+// The pair part of the gradient from two legs prepared at a common scale 2^-s (leg_grad_prep);
+// eta and phi are the legs' unscaled angles.  Returns 0 when the pair leaves the fast path (an
+// operand outside its range, or m^2 below 2^-80 of the scale), 1 when m = 0 (zero gradient),
+// 2 with the terms in *pg.
+GVX_HD int pair_grad_terms(const LegGradFF &a, const LegGradFF &b, double eta1, double eta2,
+                           double phi1, double phi2, double gm, const TabRef &T, PairGradFF *pg) {
+  bool ok = true;
+  ff den = add_same(mul(a.E, b.E), mul(a.P, b.P));
+  ff num = add_same(mul(a.q, b.E2), mul(b.q, sqr(a.P)));
+  ff tm = den.hi > 0.0f ? scale(div(num, den), 2.0f) : make(0.0f);
+  ff se, ce;
+  sinhcosh_t(scale(from_double(eta1 - eta2, &ok), 0.5f), T, &se, &ce);
+  bool wrapped;
+  ff sp, cp;
+  const double dphi = phi1 - phi2;
+  sincos_q1_t(half_dphi_ff(phi1, phi2, &ok, &wrapped), T, &sp, &cp);
+  ff S = add_same(sqr(se), sqr(sp));
+  ff m2s = renorm(add_same(add_same(add_same(a.q, b.q), tm), scale(mul(mul(a.pt, b.pt), S), 4.0f)));
+  if (!ok || (m2s.hi < 8.27180613e-25f && m2s.hi != 0.0f)) return 0;  // 2^-80
+  if (!(m2s.hi > 0.0f)) return 1;
+  ff g = from_double(gm, &ok);
+  if (!ok) return 0;
+  pg->c = div(g, scale(sqrt(m2s), 2.0f));  // gm / (2 m), scaled by 2^s
+  pg->S = S;
+  // sinh(d_eta) = 2 sinh(d_eta/2) cosh(d_eta/2);  sin(d_phi) = +-2 sin(h) cos(h), with the sign
+  // of phi1 - phi2 (its sign bit: no FP64 comparison) and reversed for the wrapped half-angle
+  pg->sdeta = scale(mul(se, ce), 2.0f);
+  pg->sdphi = scale(mul(sp, cp), 2.0f);
+  const bool dneg = (dhi(dphi) >> 31) != 0u;
+  if (dneg != wrapped) pg->sdphi = neg(pg->sdphi);
+  return 2;
+}
+
+// gm dm/d(pt, eta, phi, m) of leg x against leg o as ff, before the final scaling: components 0
+// and 3 are the values, components 1 and 2 the values times 2^-s.  sde, sdp: sinh(eta_x - eta_o)
+// and sin(phi_x - phi_o).
+GVX_HD void leg_grad_terms(const LegGradFF &x, const LegGradFF &o, const PairGradFF &pg, ff sde,
+                           ff sdp, ff *out) {
+  ff X = leg_x(x, o);
+  ff d_pt = add(scale(mul(o.pt, pg.S), 4.0f), scale(mul(x.ch, X), 2.0f));
+  ff d_eta = scale(mul(x.pt, add(mul(o.pt, sde), mul(x.sh, X))), 2.0f);
+  ff d_phi = scale(mul(mul(x.pt, o.pt), sdp), 2.0f);
+  ff d_m = x.E.hi > 0.0f ? scale(div(mul(x.m, add_same(x.E, o.E)), x.E), 2.0f) : make(0.0f);
+  out[0] = mul(pg.c, d_pt);
+  out[1] = mul(pg.c, d_eta);
+  out[2] = mul(pg.c, d_phi);
+  out[3] = mul(pg.c, d_m);
+}
+
+// leg_grad_terms to doubles.
+GVX_HD void leg_grad_out(const ff *t, int s, double *out) {
+  out[0] = to_double(renorm(t[0]));
+  out[1] = to_double(renorm(t[1]), s);
+  out[2] = to_double(renorm(t[2]), s);
+  out[3] = to_double(renorm(t[3]));
+}
+
+// The gradient of both legs from two legs prepared at a common scale 2^-s: leg a into out[0..3],
+// leg b into out[4..7].  False when the pair leaves the fast path.
+GVX_HD bool pair_grad_legs(const LegGradFF &a, const LegGradFF &b, double eta1, double eta2,
+                           double phi1, double phi2, double gm, int s, const TabRef &T,
+                           double *out) {
+  PairGradFF pg;
+  const int r = pair_grad_terms(a, b, eta1, eta2, phi1, phi2, gm, T, &pg);
+  if (r == 0) return false;
+  if (r == 1) {
+    for (int k = 0; k < 8; k++) out[k] = 0.0;
+    return true;
+  }
+  ff t[4];
+  leg_grad_terms(a, b, pg, pg.sdeta, pg.sdphi, t);
+  leg_grad_out(t, s, out);
+  leg_grad_terms(b, a, pg, neg(pg.sdeta), neg(pg.sdphi), t);
+  leg_grad_out(t, s, out + 4);
+  return true;
+}
+
 // out[0..3] leg a (pt, eta, phi, m), out[4..7] leg b.
 GVX_HD bool pair_mass_grad_ff(double pt1, double eta1, double phi1, double m1, double pt2,
                               double eta2, double phi2, double m2, double gm, const TabRef &T,
@@ -176,45 +258,7 @@ GVX_HD bool pair_mass_grad_ff(double pt1, double eta1, double phi1, double m1, d
   bool ok = true;
   LegGradFF a = leg_grad_prep(pt1, eta1, m1, s, T, &ok);
   LegGradFF b = leg_grad_prep(pt2, eta2, m2, s, T, &ok);
-  ff den = add_same(mul(a.E, b.E), mul(a.P, b.P));
-  ff num = add_same(mul(a.q, b.E2), mul(b.q, sqr(a.P)));
-  ff tm = den.hi > 0.0f ? scale(div(num, den), 2.0f) : make(0.0f);
-  ff se, ce;
-  sinhcosh_t(scale(from_double(eta1 - eta2, &ok), 0.5f), T, &se, &ce);
-  bool wrapped;
-  ff sp, cp;
-  sincos_q1_t(half_dphi_ff(phi1, phi2, &ok, &wrapped), T, &sp, &cp);
-  ff S = add_same(sqr(se), sqr(sp));
-  ff m2s = renorm(add_same(add_same(add_same(a.q, b.q), tm), scale(mul(mul(a.pt, b.pt), S), 4.0f)));
-  if (!ok || (m2s.hi < 8.27180613e-25f && m2s.hi != 0.0f)) return false;  // 2^-80
-  if (!(m2s.hi > 0.0f)) {
-    for (int k = 0; k < 8; k++) out[k] = 0.0;
-    return true;
-  }
-  ff g = from_double(gm, &ok);
-  if (!ok) return false;
-  ff c = div(g, scale(sqrt(m2s), 2.0f));  // gm / (2 m), scaled by 2^s
-  // sinh(d_eta) = 2 sinh(d_eta/2) cosh(d_eta/2);  sin(d_phi) = +-2 sin(h) cos(h), with the sign
-  // of phi1 - phi2 and reversed for the wrapped half-angle
-  ff sdeta = scale(mul(se, ce), 2.0f);
-  ff sdphi = scale(mul(sp, cp), 2.0f);
-  const bool dneg = (phi1 - phi2) < 0.0;
-  if (dneg != wrapped) sdphi = neg(sdphi);
-  const LegGradFF *L[2] = {&a, &b};
-  for (int l = 0; l < 2; l++) {
-    const LegGradFF &x = *L[l], &o = *L[1 - l];
-    ff sde = l == 0 ? sdeta : neg(sdeta), sdp = l == 0 ? sdphi : neg(sdphi);
-    ff X = leg_x(x, o);
-    ff d_pt = add(scale(mul(o.pt, S), 4.0f), scale(mul(x.ch, X), 2.0f));
-    ff d_eta = scale(mul(x.pt, add(mul(o.pt, sde), mul(x.sh, X))), 2.0f);
-    ff d_phi = scale(mul(mul(x.pt, o.pt), sdp), 2.0f);
-    ff d_m = x.E.hi > 0.0f ? scale(div(mul(x.m, add_same(x.E, o.E)), x.E), 2.0f) : make(0.0f);
-    out[4 * l + 0] = to_double(renorm(mul(c, d_pt)));
-    out[4 * l + 1] = to_double(renorm(mul(c, d_eta)), s);
-    out[4 * l + 2] = to_double(renorm(mul(c, d_phi)), s);
-    out[4 * l + 3] = to_double(renorm(mul(c, d_m)));
-  }
-  return true;
+  return ok && pair_grad_legs(a, b, eta1, eta2, phi1, phi2, gm, s, T, out);
 }
 
 }  // namespace ffm

@@ -25,6 +25,7 @@ def ffh(tmp_path_factory):
                    check=True)
     lib = ctypes.CDLL(out)
     lib.ffh_mass.restype = ctypes.c_int64
+    lib.ffh_mass_grad.restype = ctypes.c_int64
     lib.ffh_boost.restype = ctypes.c_int64
     return lib
 
@@ -159,6 +160,28 @@ def test_ff_pair_mass_tiny_angles(ffh, orc):
     assert ok.all()
     e = lambda x: np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
     assert np.all(np.abs(m - ref) <= 1e-13 * np.abs(ref) + 1e-16 * (e(a) + e(b)))
+
+
+def test_ff_pair_mass_gradient_against_oracle(ffh, orc):
+    """The FP64 adjoint's ff pair gradient (both legs) against the binary128 chain rule, on the
+    workload, the light/heavy mix and the adversarial near-collinear pairs: normwise (components
+    weighted by max(|x|, 1)) within 1e-12 of the weighted reference where the fast path runs."""
+    from test_oracle_pins import _adversarial_pairs
+    from helpers import scaled_grad_err
+    cases = [(syn.ptetaphim(syn.rng(50), 20000), syn.ptetaphim(syn.rng(51), 20000)),
+             (syn.ptetaphim_light_mix(syn.rng(52), 20000), syn.ptetaphim_light_mix(syn.rng(53), 20000)),
+             _adversarial_pairs(5000, 54)]
+    for k, (a, b) in enumerate(cases):
+        a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+        gm = syn.upstream(syn.rng(55 + k), len(a))
+        ga, gb = np.empty_like(a), np.empty_like(b)
+        ok = np.empty(len(a), np.uint8)
+        ffh.ffh_mass_grad(_p(a), _p(b), _p(gm), ctypes.c_int64(len(a)), _p(ga), _p(gb), _p(ok))
+        ok = ok.astype(bool)
+        ra, rb = orc.mass_grad_def(a, b, gm, nthreads=8)
+        assert ok.mean() > 0.99, k
+        assert scaled_grad_err(ga[ok], ra[ok], a[ok]).max() <= 1e-12, k
+        assert scaled_grad_err(gb[ok], rb[ok], b[ok]).max() <= 1e-12, k
 
 
 def test_ff_boost_coefficients(ffh):
