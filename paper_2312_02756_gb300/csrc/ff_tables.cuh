@@ -35,6 +35,10 @@ GVX_HD ff cosh_t(ff x, const TabRef &T) {
   return add_same(ep, en);
 }
 
+// The sums sin(jd) cos r + cos(jd) sin r and sinh(nc) cosh r + cosh(nc) sinh r below can have
+// terms of opposite sign, but the second term is at most about half the first (j, n >= 1) or the
+// first is 0 (j = n = 0), so they cancel at most threefold and add_same keeps ff precision.
+
 // sinh(x) for |x| < 16, with full relative accuracy also for tiny |x|:
 //   sinh(n c + r) = S E + C O,  S = sinh(n c) = ((2^k - 2^-k) + 2^k tm1[j] + 2^-k um1[j]) / 2
 //   (every term >= 0), C = cosh(n c) = S + 2^-k (1 - um1[j]).
@@ -50,7 +54,7 @@ GVX_HD ff sinh_t(ff x, const TabRef &T) {
   ff tn = fast_two_sum(1.0f, -t.z);
   tn.lo = fsub(tn.lo, t.w);
   ff C = add_same(S, scale(tn, mk));
-  ff s = add(mul(S, h.E), mul(C, h.O));
+  ff s = add_same(mul(S, h.E), mul(C, h.O));  // opposite signs cancel at most 3x
   return negx ? neg(s) : s;
 }
 
@@ -75,7 +79,7 @@ GVX_HD ff sin_t(ff h, const TabRef &T) {
   ff sr = two_sum(r.hi, fmul(fmul(r.hi, r2.hi), -0.16666667f));
   sr.lo = fadd(sr.lo, r.lo);
   gvx_f4 t = T.trig[j];
-  return add(mul(ff{t.x, t.y}, cr), mul(ff{t.z, t.w}, sr));
+  return add_same(mul(ff{t.x, t.y}, cr), mul(ff{t.z, t.w}, sr));  // cancels at most 3x
 }
 
 // sinh(x) and cosh(x) together (one reduction), |x| < 16.
@@ -91,9 +95,9 @@ GVX_HD void sinhcosh_t(ff x, const TabRef &T, ff *sh, ff *ch) {
   ff tn = fast_two_sum(1.0f, -t.z);
   tn.lo = fsub(tn.lo, t.w);
   ff C = add_same(S, scale(tn, mk));
-  ff s = add(mul(S, h.E), mul(C, h.O));
+  ff s = add_same(mul(S, h.E), mul(C, h.O));  // opposite signs cancel at most 3x
   *sh = negx ? neg(s) : s;
-  *ch = add(mul(C, h.E), mul(S, h.O));
+  *ch = add_same(mul(C, h.E), mul(S, h.O));
 }
 
 // sin(h) and cos(h) for 0 <= h <= pi/2 (+ a few ulps), relative accuracy ~2^-46 for both.
@@ -117,7 +121,7 @@ GVX_HD void sincos_q1_t(ff h, const TabRef &T, ff *sn, ff *cs) {
   sr.lo = fadd(sr.lo, r.lo);
   gvx_f4 t = T.trig[j];
   ff sj = {t.x, t.y}, cj = {t.z, t.w};
-  *sn = add(mul(sj, cr), mul(cj, sr));
+  *sn = add_same(mul(sj, cr), mul(cj, sr));
   *cs = add(mul(cj, cr), neg(mul(sj, sr)));
 }
 
@@ -146,7 +150,7 @@ GVX_HD void sincos_t(double phi, const TabRef &T, ff *sn, ff *cs, bool *ok) {
   sr.lo = fadd(sr.lo, r.lo);
   gvx_f4 t = T.trig[j];
   ff sj = {t.x, t.y}, cj = {t.z, t.w};
-  ff s = add(mul(sj, cr), mul(cj, sr));
+  ff s = add_same(mul(sj, cr), mul(cj, sr));
   ff c = add(mul(cj, cr), neg(mul(sj, sr)));
   *sn = (dhi(phi) >> 31) ? neg(s) : s;
   *cs = q2 ? neg(c) : c;
