@@ -514,28 +514,43 @@ def run_gvx(args):
     return 0
 
 
-def _csrc_hash():
-    import glob
+# The sources each timed kernel is built from (the traffic counters are valid while these match).
+_MASS_SRC = ("mass.cu", "mass_ff.cuh", "ff_tables.cuh", "ff.cuh", "pair_math.cuh", "common.cuh",
+             "gvx_internal.h", "../gen_tables.py")
+KERNEL_SOURCES = {
+    "mass_f64_soa": _MASS_SRC,
+    "mass_f64_aos": _MASS_SRC,
+    "boost_f64_soa": ("boost.cu", "boost_ff.cuh", "ff.cuh", "common.cuh", "gvx_internal.h"),
+}
+
+
+def sources_hash(kernel, read=None):
+    """Short hash of the sources `kernel` is built from; `read(relpath) -> bytes` defaults to the
+    working tree (paths relative to the package's csrc folder)."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2312_02756_gb300", "csrc")
+    read = read or (lambda rel: open(os.path.join(csrc, rel), "rb").read())
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2312_02756_gb300", "csrc", "*"))):
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    for rel in KERNEL_SOURCES[kernel]:
+        h.update(rel.encode())
+        h.update(read(rel))
     return h.hexdigest()[:16]
 
 
 def _profile_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.json),
-    only while the kernel sources are the ones the counters were taken from."""
+    only while the kernel's sources are the ones the counters were taken from."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if data.get("csrc_hash") != _csrc_hash():
-        return None
     entry = data.get(kernel)
-    return entry.get("bytes_per_launch") if isinstance(entry, dict) else None
+    if not isinstance(entry, dict) or kernel not in KERNEL_SOURCES:
+        return None
+    if entry.get("sources_hash") != sources_hash(kernel):
+        return None
+    return entry.get("bytes_per_launch")
 
 
 def main():

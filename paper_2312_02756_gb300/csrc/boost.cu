@@ -121,8 +121,10 @@ __global__ void __launch_bounds__(256) boost_kernel(Lv v, Lv beta, LvOut out, in
 // Adjoint.  grad_v = L grad_out (L symmetric: the same boost applied to grad_out).  With
 // gb = beta . grad_p, k' = dk/dgamma = gamma (gamma + 2)/(gamma + 1)^2, f = k bp + gamma E:
 //   grad_beta = gamma^3 [gb (k' bp + E) + gE (E + bp)] beta + (k gb + gamma gE) p + f grad_p.
-// In FP64, gamma, k, k' = (1 + 2 s)/(1 + s)^2 and gamma^3 (s = 1/gamma = sqrt(1 - b2)) come
-// from float-float arithmetic; the multiply-adds with v, beta and grad_out stay in FP64.
+// This is the FP32 evaluation and the FP64 one outside the float-float domain (there gamma, k,
+// k' = (1 + 2 s)/(1 + s)^2 and gamma^3, s = 1/gamma = sqrt(1 - b2), come from float-float
+// arithmetic and the multiply-adds stay in FP64); FP64 inputs inside it take boost_bwd_ff
+// (boost_ff.cuh), which keeps 21 FP64 operations per vector.
 template <typename T>
 struct BoostCoefBwd {
   BoostCoef<T> c;
@@ -181,6 +183,32 @@ __device__ __forceinline__ void boost_grads(V3<T> b, BoostCoefBwd<T> cb, V4<T> v
   gbeta.z = fma(A, b.z, fma(B, v.z, f * g.z));
 }
 
+// Both adjoint outputs for one vector: the float-float path (boost_ff.cuh) for FP64 inputs in its
+// domain, the FP64 (or FP32) formulas above otherwise.
+template <typename T>
+__device__ __forceinline__ void boost_grads_any(V3<T> b, const ffm::BetaBwdFF &B,
+                                                const BoostCoefBwd<T> *cb, V4<T> x, V4<T> g,
+                                                V4<T> &ogv, V3<T> &ogb) {
+  if constexpr (sizeof(T) == 8) {
+    const double p[4] = {x.x, x.y, x.z, x.w}, q[4] = {g.x, g.y, g.z, g.w};
+    double o[4], ob[3];
+    if (ffm::boost_bwd_ff(B, b.x, b.y, b.z, p, q, o, ob)) {
+      ogv = {o[0], o[1], o[2], o[3]};
+      ogb = {ob[0], ob[1], ob[2]};
+      return;
+    }
+  }
+  boost_grads(b, cb ? *cb : boost_coef_bwd(b), x, g, ogv, ogb);
+}
+
+template <typename T>
+__device__ __forceinline__ ffm::BetaBwdFF beta_bwd_any(V3<T> b) {
+  if constexpr (sizeof(T) == 8) return ffm::beta_bwd_ff(b.x, b.y, b.z);
+  ffm::BetaBwdFF B;
+  B.ok = false;
+  return B;
+}
+
 template <typename T, int LV, int LBETA, int LG, int LGV, int LGB>
 __global__ void __launch_bounds__(256) boost_bwd_kernel(Lv v, Lv beta, Lv gout, LvOut gv,
                                                         LvOut gbeta, int64_t n) {
@@ -191,7 +219,7 @@ __global__ void __launch_bounds__(256) boost_bwd_kernel(Lv v, Lv beta, Lv gout, 
     V4<T> g = ld4<T, LG>(gout, i);
     V4<T> ogv;
     V3<T> ogb;
-    boost_grads(b, boost_coef_bwd(b), x, g, ogv, ogb);
+    boost_grads_any(b, beta_bwd_any(b), (const BoostCoefBwd<T> *)nullptr, x, g, ogv, ogb);
     st4<T, LGV>(gv, i, ogv);
     st3<T, LGB>(gbeta, i, ogb);
   }
@@ -208,14 +236,15 @@ __global__ void __launch_bounds__(kBwdThreads) boost_bwd_shared_kernel(Lv v, Lv 
                                                                        int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   V3<T> b = ld3<T, LBETA>(beta, 0);
-  BoostCoefBwd<T> c = boost_coef_bwd(b);
+  const BoostCoefBwd<T> c = boost_coef_bwd(b);
+  const ffm::BetaBwdFF B = beta_bwd_any(b);
   double acc[3] = {0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     V4<T> x = ld4<T, LV>(v, i);
     V4<T> g = ld4<T, LG>(gout, i);
     V4<T> ogv;
     V3<T> ogb;
-    boost_grads(b, c, x, g, ogv, ogb);
+    boost_grads_any(b, B, &c, x, g, ogv, ogb);
     st4<T, LGV>(gv, i, ogv);
     acc[0] += (double)ogb.x;
     acc[1] += (double)ogb.y;

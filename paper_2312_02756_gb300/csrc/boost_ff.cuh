@@ -67,5 +67,78 @@ GVX_HD bool boost_ff(const BetaFF &B, double bx, double by, double bz, double px
   return true;
 }
 
+// ---- adjoint ------------------------------------------------------------------------------
+// grad_v = L grad_out (L is symmetric) and, with gb = beta.grad_p, tg = gE + gb,
+// k' = dk/dgamma = gamma (gamma + 2)/(gamma + 1)^2 (so k' - 1 = -(s w)^2):
+//   grad_beta = A beta + B p + f grad_p,
+//   A = gamma^3 [gb (t + (k' - 1) bp) + gE t],   B = k gb + gamma gE,   f = k t + w E.
+// bp, t, gb and tg are FP64 (the sums that can cancel); A, B, f and the boost of grad_out are
+// formed in ff from the scaled inputs and return to double by integer operations; the
+// combinations with beta, p and grad_p are FP64 multiply-adds: 21 FP64 operations per vector.
+
+struct BetaBwdFF {
+  ff gf, w, k, kpm1, g3;  // gamma, 1/(1 + s), gamma w, k' - 1, gamma^3
+  double g;               // gamma
+  bool ok;
+};
+
+GVX_HD BetaBwdFF beta_bwd_ff(double bx, double by, double bz) {
+  BetaBwdFF B;
+  bool ok = true;
+  const ff omb = one_minus_sq3(bx, by, bz, &ok);
+  const ff s = sqrt(omb);
+  const ff g = recip(s);
+  B.gf = g;
+  B.w = recip(add_same(make(1.0f), s));
+  B.k = mul(g, B.w);
+  B.kpm1 = neg(sqr(mul(s, B.w)));
+  B.g3 = mul(sqr(g), g);
+  B.g = ok ? to_double_int(g, 0) : 0.0;
+  B.ok = ok;
+  return B;
+}
+
+// Both adjoint outputs for one vector p (px, py, pz, E) and upstream gradient q (the same
+// layout); false outside the domain: beta as for boost_ff, each of p and q with its largest
+// magnitude in [2^-823, 2^1013) (q may also be exactly zero), and their scales together within
+// [2^-800, 2^900].
+GVX_HD bool boost_bwd_ff(const BetaBwdFF &B, double bx, double by, double bz, const double *p,
+                         const double *q, double *gv, double *gbeta) {
+  if (!B.ok) return false;
+  const int ev = max_exponent4(p[0], p[1], p[2], p[3]);
+  const int eq = max_exponent4(q[0], q[1], q[2], q[3]);
+  if (ev < 200 || ev > 2035) return false;
+  if (eq == 0 && ((dhi(q[0]) | dlo(q[0]) | dhi(q[1]) | dlo(q[1]) | dhi(q[2]) | dlo(q[2]) |
+                   dhi(q[3]) | dlo(q[3])) & 0x7fffffffu) == 0u &&
+      ((dlo(q[0]) | dlo(q[1]) | dlo(q[2]) | dlo(q[3])) == 0u)) {
+    for (int c = 0; c < 4; c++) gv[c] = 0.0;  // a zero upstream gradient gives zero gradients
+    for (int c = 0; c < 3; c++) gbeta[c] = 0.0;
+    return true;
+  }
+  if (eq < 200 || eq > 2035 || ev + eq - 2046 < -800 || ev + eq - 2046 > 900) return false;
+  const int sv = ev - 1023, sq = eq - 1023;
+  const double bp = fma(bx, p[0], fma(by, p[1], bz * p[2]));
+  const double t = p[3] + bp;
+  const double gb = fma(bx, q[0], fma(by, q[1], bz * q[2]));
+  const double tg = q[3] + gb;
+  const ff T = from_double_ranged(t, sv), BP = from_double_ranged(bp, sv);
+  const ff En = from_double_ranged(p[3], sv);
+  const ff TG = from_double_ranged(tg, sq), GB = from_double_ranged(gb, sq);
+  const ff GE = from_double_ranged(q[3], sq);
+  const double f = to_double_int(add(mul(B.k, T), mul(B.w, En)), sv);
+  const double fq = to_double_int(add(mul(B.k, TG), mul(B.w, GE)), sq);
+  const ff A = mul(B.g3, add(mul(GB, add(T, mul(B.kpm1, BP))), mul(GE, T)));
+  const double a = to_double_int(renorm(A), sv + sq);
+  const double bq = to_double_int(add(mul(B.k, GB), mul(B.gf, GE)), sq);
+  gv[0] = fma(fq, bx, q[0]);
+  gv[1] = fma(fq, by, q[1]);
+  gv[2] = fma(fq, bz, q[2]);
+  gv[3] = B.g * tg;
+  gbeta[0] = fma(a, bx, fma(bq, p[0], f * q[0]));
+  gbeta[1] = fma(a, by, fma(bq, p[1], f * q[1]));
+  gbeta[2] = fma(a, bz, fma(bq, p[2], f * q[2]));
+  return true;
+}
+
 }  // namespace ffm
 }  // namespace gvx

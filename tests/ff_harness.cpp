@@ -92,6 +92,25 @@ void ffh_conv_ranged(const double *x, int64_t n, int shift, double *hi, double *
   }
 }
 
+// The FP64 boost adjoint's fast path: v (n, 4), beta (n, 3), grad_out (n, 4) -> gv (n, 4),
+// gbeta (n, 3); ok[i] = in domain.
+int64_t ffh_boost_bwd(const double *v, const double *beta, const double *gout, int64_t n,
+                      double *gv, double *gbeta, uint8_t *ok) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const double *b = beta + 3 * i;
+    const BetaBwdFF B = beta_bwd_ff(b[0], b[1], b[2]);
+    bool f = boost_bwd_ff(B, b[0], b[1], b[2], v + 4 * i, gout + 4 * i, gv + 4 * i, gbeta + 3 * i);
+    if (!f) {
+      for (int k = 0; k < 4; k++) gv[4 * i + k] = NAN;
+      for (int k = 0; k < 3; k++) gbeta[3 * i + k] = NAN;
+    }
+    ok[i] = f;
+    c += f;
+  }
+  return c;
+}
+
 // to_double_int and the FP64-add conversion to_double of the ff values (hi[i], lo[i]) * 2^shift.
 void ffh_to_double(const float *hi, const float *lo, int64_t n, int shift, double *out_int,
                    double *out_add) {

@@ -27,6 +27,7 @@ def ffh(tmp_path_factory):
     lib.ffh_mass.restype = ctypes.c_int64
     lib.ffh_mass_grad.restype = ctypes.c_int64
     lib.ffh_boost.restype = ctypes.c_int64
+    lib.ffh_boost_bwd.restype = ctypes.c_int64
     return lib
 
 
@@ -279,3 +280,33 @@ def test_ff_boost_fast_path_against_oracle(ffh, orc):
     # beta = 0 is the identity, bit for bit (gamma = 1 and p + f 0 are exact)
     out, ok = _boost(ffh, w, np.zeros((m, 3)))
     assert ok.all() and np.array_equal(out, w)
+
+
+def test_ff_boost_adjoint_against_oracle(ffh, orc):
+    """The FP64 boost adjoint's fast path (FP64 dot products and sums that can cancel, A, B, f and
+    the boost of the upstream gradient in ff) against the binary128 chain rule, on the FP64
+    workload: normwise, components weighted by max(|x|, 1), within 1e-12 of the weighted
+    reference.  A zero upstream gradient gives exact zeros; inputs outside the domain are left
+    to the FP64 formulas."""
+    from helpers import scaled_grad_err
+    g = syn.rng(60)
+    n = 1 << 15
+    v, b, q = syn.pxpypze(g, n), syn.velocities(g, n, 0.99), syn.upstream(g, (n, 4))
+    v, b, q = (np.ascontiguousarray(x) for x in (v, b, q))
+    gv, gb = np.empty_like(v), np.empty_like(b)
+    ok = np.empty(n, np.uint8)
+    ffh.ffh_boost_bwd(_p(v), _p(b), _p(q), ctypes.c_int64(n), _p(gv), _p(gb), _p(ok))
+    assert ok.all()
+    rv, rb = orc.boost_grad_def(v, b, q)
+    assert scaled_grad_err(gv, rv, q).max() <= 1e-12
+    assert scaled_grad_err(gb, rb, b).max() <= 1e-12
+    z = np.zeros((3, 4))
+    v3, b3 = np.ascontiguousarray(v[:3]), np.ascontiguousarray(b[:3])
+    gv, gb, ok = np.empty((3, 4)), np.empty((3, 3)), np.empty(3, np.uint8)
+    ffh.ffh_boost_bwd(_p(v3), _p(b3), _p(z), ctypes.c_int64(3), _p(gv), _p(gb), _p(ok))
+    assert ok.all() and not gv.any() and not gb.any()
+    bad_q = np.array([[1e-300, 0, 0, 0], [1.0, 2.0, 3.0, np.inf], [1e300, 0, 0, 1e300]])
+    bad_b = np.array([[0.0, 0.0, 0.3], [0.0, 0.0, 0.3], [0.0, 0.0, 0.999995]])
+    ffh.ffh_boost_bwd(_p(v3), _p(np.ascontiguousarray(bad_b)), _p(bad_q), ctypes.c_int64(3),
+                      _p(gv), _p(gb), _p(ok))
+    assert not ok.any()
