@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
   __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
   __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
   __shared__ int64_t s_off[kTE + 1], s_poff[kTE + 1];
+  __shared__ int s_order[kTE], s_start[kTE];
   __shared__ int s_bad;
   const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
   const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
@@ -220,12 +221,10 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
         s_ex[k] = ffm::leg_exponent(x.x, x.w);
       }
       __syncthreads();
-      // (b) the particle's event and scale, its ff leg terms, and its event-sum part
-      ffm::ff acc_f[4] = {ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f)};
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};  // FP64 contributions (pairs off the fast path)
-      int e = sb, sc = kNoFast;
+      // (b) the particle's event and scale and its ff leg terms; and the order of phase (c):
+      // events by decreasing size, so that the partner loops of a warp have similar lengths
       if (k < np) {
-        int hi = sbe - 1;  // the particle's event: the last e with s_off[e] <= pbeg + k
+        int e = sb, hi = sbe - 1;  // the particle's event: the last e with s_off[e] <= pbeg + k
         while (e < hi) {
           const int mid = (e + hi + 1) >> 1;
           if (s_off[mid] <= pbeg + k) e = mid;
@@ -234,42 +233,72 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
         int emax = 0;
         for (int t = (int)(s_off[e] - pbeg); t < (int)(s_off[e + 1] - pbeg); t++)
           emax = s_ex[t] > emax ? s_ex[t] : emax;
-        ffm::LegGradFF L;
+        int sc = kNoFast;
         if (ffm::scale_exponent_ok(emax) && ffm::leg_in_domain(x.x, x.y, x.z, x.w, emax)) {
           bool ok = true;
-          L = ffm::leg_grad_prep(x.x, x.y, x.w, emax - 1023, T, &ok);
+          const ffm::LegGradFF L = ffm::leg_grad_prep(x.x, x.y, x.w, emax - 1023, T, &ok);
           if (ok) {
             sc = emax - 1023;
             s_leg[k] = L;
           }
         }
         s_fs[k] = sc;
+      }
+      const int ns = sbe - sb;
+      if (threadIdx.x < ns) {  // rank of event sb + threadIdx.x: larger first, ties by position
+        const int me = sb + threadIdx.x;
+        const int64_t nme = s_off[me + 1] - s_off[me];
+        int rank = 0;
+        int64_t before = 0;  // particles of the events ranked ahead
+        for (int o = sb; o < sbe; o++) {
+          const int64_t no = s_off[o + 1] - s_off[o];
+          if (no > nme || (no == nme && o < me)) {
+            rank++;
+            before += no;
+          }
+        }
+        s_order[rank] = me;
+        s_start[rank] = (int)before;
+      }
+      __syncthreads();
+      // (c) one particle per thread in that order: its event-sum part, then its partners in
+      // order; fast-path terms accumulate in ff at the event's scale
+      if (k < np) {
+        int r = 0, hi = ns - 1;  // the sorted event holding thread position k
+        while (r < hi) {
+          const int mid = (r + hi + 1) >> 1;
+          if (s_start[mid] <= k) r = mid;
+          else hi = mid - 1;
+        }
+        const int e = s_order[r];
+        const int b0 = (int)(s_off[e] - pbeg);
+        const int li32 = k - s_start[r];
+        const int p = b0 + li32;  // the particle this thread now takes
+        const V4<double> xp = {s_pt[p], s_eta[p], s_phi[p], s_m[p]};
+        const int sc = s_fs[p];
+        ffm::ff acc_f[4] = {ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f)};
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};  // FP64 contributions (off the fast path)
         if (A.has_gsum) {
           const V4<double> gsv = ld4c<LS>(A.gsum, e0 + e);
-          if (sc == kNoFast || !sum_part_ff(L, x.z, gsv, T, acc_f)) {
-            const V4<double> sp = sum_part(x, gsv, T);
+          if (sc == kNoFast || !sum_part_ff(s_leg[p], xp.z, gsv, T, acc_f)) {
+            const V4<double> sp = sum_part(xp, gsv, T);
             acc[0] = sp.x;
             acc[1] = sp.y;
             acc[2] = sp.z;
             acc[3] = sp.w;
           }
         }
-      }
-      __syncthreads();
-      // (c) the partners, in order; fast-path terms accumulate in ff at the event's scale
-      if (k < np) {
-        const int b0 = (int)(s_off[e] - pbeg);
-        const int64_t n = s_off[e + 1] - s_off[e], li = k - b0, pair0 = s_poff[e];
+        const int64_t n = s_off[e + 1] - s_off[e], li = li32, pair0 = s_poff[e];
         for (int64_t lj = 0; lj < n; lj++) {
           if (lj == li) continue;
-          const int64_t r = li < lj ? li : lj, q = li < lj ? lj : li;
-          const double g = __ldg(A.gpm + pair0 + r * n - r * (r + 1) / 2 + (q - r - 1));
+          const int64_t rr = li < lj ? li : lj, q = li < lj ? lj : li;
+          const double g = __ldg(A.gpm + pair0 + rr * n - rr * (rr + 1) / 2 + (q - rr - 1));
           const int j = b0 + (int)lj;
           int done = 0;
           if (sc != kNoFast && s_fs[j] != kNoFast) {
-            const ffm::LegGradFF &a = s_leg[k], &b = s_leg[j];
+            const ffm::LegGradFF &a = s_leg[p], &b = s_leg[j];
             ffm::PairGradFF pg;
-            done = ffm::pair_grad_terms(a, b, x.y, s_eta[j], x.z, s_phi[j], g, T, &pg);
+            done = ffm::pair_grad_terms(a, b, xp.y, s_eta[j], xp.z, s_phi[j], g, T, &pg);
             if (done == 2) {
               ffm::ff t[4];
               ffm::leg_grad_terms(a, b, pg, pg.sdeta, pg.sdphi, t);
@@ -278,7 +307,7 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
           }
           if (!done) {
             V4<double> g1, g2;
-            pair_mass_grad(x, V4<double>{s_pt[j], s_eta[j], s_phi[j], s_m[j]}, g, g1, g2);
+            pair_mass_grad(xp, V4<double>{s_pt[j], s_eta[j], s_phi[j], s_m[j]}, g, g1, g2);
             acc[0] += g1.x;
             acc[1] += g1.y;
             acc[2] += g1.z;
@@ -287,7 +316,7 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
         }
         double out[4] = {0.0, 0.0, 0.0, 0.0};
         if (sc != kNoFast) ffm::leg_grad_out(acc_f, sc, out);
-        st4<double, LG>(A.grad, pbeg + k,
+        st4<double, LG>(A.grad, pbeg + p,
                         V4<double>{out[0] + acc[0], out[1] + acc[1], out[2] + acc[2], out[3] + acc[3]});
       }
       __syncthreads();  // before the next sub-batch overwrites the staged particles
