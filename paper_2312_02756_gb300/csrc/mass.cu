@@ -100,7 +100,7 @@ cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaSt
 // FP64 adjoint: float-float evaluation (mass_ff.cuh, pair_mass_grad_ff) with the FP64 formulas
 // kept for lanes outside its domain.
 template <int LA, int LB, int LGA, int LGB>
-__global__ void __launch_bounds__(256) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ gm,
+__global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ gm,
                                                            LvOut ga, LvOut gb, int64_t n) {
   __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
   __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
