@@ -62,6 +62,9 @@ def _load():
         "orc_boost_grad_def": ([P, P, I64, P, I64, P, P], None),
         "orc_event_pairs_def": ([P, P, I64, P, P, P], INT),
         "orc_event_pairs_grad_def": ([P, P, I64, P, P, P], INT),
+        "orc_pair_select_def": ([P, P, I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                 P, P, P, P], INT),
         "orc_to_cartesian_def": ([P, I64, P], None),
         "orc_lv_mass_def": ([P, I64, P], None),
         "orc_mass_fp64": ([P, P, I64, P, INT], None),
@@ -206,6 +209,28 @@ def event_pairs_grad_def(p, offsets, grad_pair_m, grad_sums=None) -> np.ndarray:
     if rc != 0:
         raise ValueError("malformed offsets")
     return out[:p.shape[0]]
+
+
+def pair_select_def(p, offsets, pt_min, eta_max, lo, hi, n_bins, target, rel_tol=1e-12):
+    """O1 fused selection + pair-mass histogram + best candidate per event (see the C function).
+    Returns (counts uint64[n_bins + 2], near_edge uint64[n_bins + 2], best_k int64[n_events],
+    best_m float64[n_events])."""
+    p = _rows(p, 4) if len(p) else np.zeros((0, 4))
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    n_ev = off.shape[0] - 1
+    if n_ev < 0 or off[-1] != p.shape[0]:
+        raise ValueError("offsets must have n_events+1 entries ending at the particle count")
+    counts = np.zeros(n_bins + 2, dtype=np.uint64)
+    near = np.zeros(n_bins + 2, dtype=np.uint64)
+    best_k = np.empty(max(n_ev, 1), dtype=np.int64)
+    best_m = np.empty(max(n_ev, 1))
+    rc = _load().orc_pair_select_def(_ptr(p), _ptr(off), n_ev, float(pt_min), float(eta_max),
+                                     float(lo), float(hi), int(n_bins), float(target),
+                                     float(rel_tol), _ptr(counts), _ptr(near), _ptr(best_k),
+                                     _ptr(best_m))
+    if rc != 0:
+        raise ValueError("malformed offsets or histogram range")
+    return counts, near, best_k[:n_ev], best_m[:n_ev]
 
 
 def to_cartesian_def(p) -> np.ndarray:

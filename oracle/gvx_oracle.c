@@ -468,6 +468,75 @@ int orc_event_pairs_grad_def(const double *p, const int64_t *off, int64_t n_even
   return 0;
 }
 
+/* Fused per-event selection, pair-mass histogram and best candidate: the analysis step that the
+ * per-event combinatorics serve (Sec. 6 names RDataFrame analyses as the next target; the paper
+ * defines no such step, so its semantics are the ones written here).
+ *   A particle passes when pt >= pt_min and |eta| <= eta_max.
+ *   Every pair i < j of passing particles of an event has its mass m (the pair mass of Sec. 4.1,
+ *   as in orc_event_pairs_def) counted in a histogram of n_bins equal bins over [lo, hi):
+ *   counts[0] holds m < lo, counts[1 + b] the b-th bin, counts[n_bins + 1] m >= hi or NaN.
+ *   The bin of m is floor((m - lo) * inv_w) with inv_w = n_bins / (hi - lo), both evaluated in
+ *   double, and clamped to [0, n_bins - 1] (the clamp only acts on rounding at the upper edge).
+ *   best_k[e] is the packed index k(i, j) (the order of orc_event_pairs_def) of the passing pair
+ *   whose |m - target| is smallest, the smaller k on ties, or -1 when the event has no passing
+ *   pair; best_m[e] is that pair's mass (NaN when none).
+ * near_edge[s] counts the masses of slot s within rel_tol * max(|m|, |edge|) of one of the
+ * slot's edges (lo + b (hi - lo) / n_bins, in double): another rounding of such an m may land
+ * in the neighbouring slot.  Returns 0, or -1 for malformed offsets or n_bins < 1. */
+int orc_pair_select_def(const double *p, const int64_t *off, int64_t n_events, double pt_min,
+                        double eta_max, double lo, double hi, int32_t n_bins, double target,
+                        double rel_tol, uint64_t *counts, uint64_t *near_edge, int64_t *best_k,
+                        double *best_m) {
+  if (n_events < 0 || off[0] != 0 || n_bins < 1 || !(hi > lo)) return -1;
+  for (int64_t e = 0; e < n_events; e++)
+    if (off[e + 1] < off[e]) return -1;
+  for (int32_t s = 0; s < n_bins + 2; s++) counts[s] = near_edge[s] = 0;
+  const double inv_w = (double)n_bins / (hi - lo);
+  for (int64_t e = 0; e < n_events; e++) {
+    const int64_t base = off[e], n = off[e + 1] - off[e];
+    int64_t bk = -1;
+    double bd = 0.0, bm = NAN;
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++) {
+      for (int64_t j = i + 1; j < n; j++, k++) {
+        const double *a = p + 4 * (base + i), *b = p + 4 * (base + j);
+        if (!(a[0] >= pt_min && fabs(a[1]) <= eta_max && b[0] >= pt_min && fabs(b[1]) <= eta_max))
+          continue;
+        const double m = pair_mass_def(a, b);
+        int32_t slot;
+        double e_lo, e_hi;  /* the slot's edges */
+        if (m < lo) {
+          slot = 0;
+          e_lo = e_hi = lo;
+        } else if (!(m < hi)) {
+          slot = n_bins + 1;
+          e_lo = e_hi = hi;
+        } else {
+          int64_t bin = (int64_t)floor((m - lo) * inv_w);
+          if (bin < 0) bin = 0;
+          if (bin > n_bins - 1) bin = n_bins - 1;
+          slot = (int32_t)(bin + 1);
+          e_lo = lo + (double)bin * (hi - lo) / n_bins;
+          e_hi = lo + (double)(bin + 1) * (hi - lo) / n_bins;
+        }
+        counts[slot]++;
+        if (m == m && (fabs(m - e_lo) <= rel_tol * fmax(fabs(m), fabs(e_lo)) ||
+                       fabs(m - e_hi) <= rel_tol * fmax(fabs(m), fabs(e_hi))))
+          near_edge[slot]++;
+        const double d = fabs(m - target);
+        if (d == d && (bk < 0 || d < bd)) {  /* strict: an equal later pair keeps the first */
+          bk = k;
+          bd = d;
+          bm = m;
+        }
+      }
+    }
+    best_k[e] = bk;
+    best_m[e] = bm;
+  }
+  return 0;
+}
+
 /* PtEtaPhiM -> PxPyPzE rounded to double (used by the tests to build boost inputs and
  * multi-body checks). */
 void orc_to_cartesian_def(const double *p, int64_t n, double *out) {

@@ -464,3 +464,93 @@ def test_event_pairs_grad_rejects_bad_input(orc):
         orc.event_pairs_grad_def(p, [0, 3, 2, 5], np.zeros(4))
     with pytest.raises(ValueError):
         orc.event_pairs_grad_def(p, [0, 2, 5], np.zeros(3))  # 1 + 3 pairs expected
+
+
+# ------------------------------------------------------------- fused selection + histogram
+
+def _mp_pair_mass(mp, a, b):
+    """The pair mass from the definition in mpmath (50 digits)."""
+    def cart(x):
+        pt, eta, phi, m = (mp.mpf(float(v)) for v in x)
+        px, py, pz = pt * mp.cos(phi), pt * mp.sin(phi), pt * mp.sinh(eta)
+        return px, py, pz, mp.sqrt(px * px + py * py + pz * pz + m * m)
+    u, w = cart(a), cart(b)
+    s = [u[k] + w[k] for k in range(4)]
+    return mp.sqrt(s[3] ** 2 - s[0] ** 2 - s[1] ** 2 - s[2] ** 2)
+
+
+def test_pair_select_brute_force_mpmath(orc):
+    """Counts and best candidates against a brute-force loop with masses in mpmath: the slot of
+    every pair from its 50-digit mass rounded to double, the best pair from exact |m - target|."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    g = syn.rng(124)
+    off = syn.jagged_offsets(g, 40, lam=4.0, n_max=7)
+    p = syn.ptetaphim(g, int(off[-1]))
+    pt_min, eta_max, lo, hi, nb, target = 15.0, 2.0, 0.0, 300.0, 30, 91.1876
+    counts, near, bk, bm = orc.pair_select_def(p, off, pt_min, eta_max, lo, hi, nb, target)
+    want = np.zeros(nb + 2, dtype=np.uint64)
+    inv_w = nb / (hi - lo)
+    for e in range(len(off) - 1):
+        best = None
+        k = 0
+        n = off[e + 1] - off[e]
+        for i in range(n):
+            for j in range(i + 1, n):
+                a, b = p[off[e] + i], p[off[e] + j]
+                if a[0] >= pt_min and abs(a[1]) <= eta_max and b[0] >= pt_min and abs(b[1]) <= eta_max:
+                    mq = _mp_pair_mass(mp, a, b)
+                    m = float(mq)
+                    slot = 0 if m < lo else nb + 1 if m >= hi else 1 + min(int(np.floor((m - lo) * inv_w)), nb - 1)
+                    want[slot] += 1
+                    d = abs(mq - target)
+                    if best is None or d < best[0]:
+                        best = (d, k, m)
+                k += 1
+        assert bk[e] == (best[1] if best else -1), e
+        if best:
+            assert abs(bm[e] - best[2]) <= 1e-15 * best[2]
+        else:
+            assert np.isnan(bm[e])
+    assert near.sum() == 0  # no mass of this sample sits on a bin edge
+    assert np.array_equal(counts, want)
+
+
+def test_pair_select_invariants(orc):
+    """Every passing pair is counted once (total = sum over events of C(n_pass, 2)); no cut
+    counts all pairs and one bin over everything holds them all; an impossible cut counts
+    nothing and leaves every event without a candidate."""
+    g = syn.rng(125)
+    off = syn.jagged_offsets(g, 500, lam=6.0, n_max=20)
+    p = syn.ptetaphim(g, int(off[-1]))
+    counts, _, bk, _ = orc.pair_select_def(p, off, 30.0, 1.5, 0.0, 500.0, 50, 91.19)
+    passing = (p[:, 0] >= 30.0) & (np.abs(p[:, 1]) <= 1.5)
+    n_pass = np.add.reduceat(passing.astype(np.int64), off[:-1]) if len(p) else 0
+    n_pass = np.where(np.diff(off) > 0, n_pass, 0)
+    assert int(counts.sum()) == int(np.sum(n_pass * (n_pass - 1) // 2))
+    assert np.array_equal(bk >= 0, n_pass >= 2)
+    c = np.diff(off)
+    counts, _, bk, _ = orc.pair_select_def(p, off, 0.0, np.inf, 0.0, 1e9, 1, 91.19)
+    assert counts[1] == np.sum(c * (c - 1) // 2) and counts[0] == 0 and counts[2] == 0
+    counts, _, bk, bm = orc.pair_select_def(p, off, 1e9, np.inf, 0.0, 1e9, 4, 91.19)
+    assert counts.sum() == 0 and np.all(bk == -1) and np.all(np.isnan(bm))
+
+
+def test_pair_select_hand_case_and_ties(orc):
+    """Two massless particles back to back at eta = 0 with pt = 45.5 have m = 91 exactly (bin
+    91 of 1-GeV bins); a duplicated particle makes two pairs with equal masses, and the smaller
+    packed index wins the tie."""
+    p = np.array([[45.5, 0.0, 0.0, 0.0], [45.5, 0.0, -np.pi, 0.0], [10.0, 0.0, 0.5, 0.0],
+                  [20.0, 0.3, 1.0, 0.0], [20.0, 0.3, 1.0, 0.0], [35.0, -0.4, -2.0, 0.0]])
+    off = np.array([0, 3, 6])
+    counts, near, bk, bm = orc.pair_select_def(p, off, 0.0, np.inf, 0.0, 200.0, 200, 91.0)
+    assert bk[0] == 0 and abs(bm[0] - 91.0) <= 1e-13  # k(0, 1) = 0
+    assert counts[1 + 91] >= 1 or near[1 + 91] + near[1 + 90] >= 1
+    # event 1: particles 0 and 1 identical, so pairs (0, 2) and (1, 2) have the same mass
+    m02 = orc.mass_def(p[3:4], p[5:6])[0]
+    counts, _, bk, bm = orc.pair_select_def(p, off, 0.0, np.inf, 0.0, 200.0, 20, m02)
+    assert bk[1] == 1 and bm[1] == m02  # k(0, 2) = 1 beats k(1, 2) = 2
+    # the cuts are inclusive: pt = pt_min and |eta| = eta_max pass (event 0: one pair, event 1:
+    # three pairs)
+    counts, _, _, _ = orc.pair_select_def(p, off, 20.0, 0.4, 0.0, 200.0, 20, 91.0)
+    assert counts.sum() == 4
