@@ -284,6 +284,18 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
             P(gpm.data_ptr()), n_pairs, r(lgs), r(lgp), s))
         t_jb = time_loop(torch, jbwd, stream, steps, warmup)
         status_b = gvx.device_status()
+        # the fused analysis step on the same events: cuts pt >= 20, |eta| <= 2.5, 200 bins of
+        # the selected pair masses over [0, 400), best candidate for 91.1876
+        hist = torch.zeros(202, dtype=torch.int64, device="cuda")
+        bk = torch.empty(n_ev, dtype=torch.int64, device="cuda")
+        bm = torch.empty(n_ev, dtype=torch.float64, device="cuda")
+        jsel = lambda: _lib.check(lib.gvx_event_pair_select(
+            r(lp), P(doff.data_ptr()), n_ev, int(off[-1]), 20.0, 2.5, 0.0, 400.0, 200, 91.1876,
+            P(hist.data_ptr()), P(bk.data_ptr()), P(bm.data_ptr()), s))
+        t_js = time_loop(torch, jsel, stream, steps, warmup)
+        status_s = gvx.device_status()
+        sel_pairs = int(hist.sum().item()) // (steps + warmup)
+        del hist, bk, bm
         graph.close()
         del p, doff, graph, gpm, gsum, gp
         torch.cuda.empty_cache()
@@ -302,6 +314,11 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
                     "GBps": jag_bwd_bytes / (t_jb * 1e-3) / 1e9, "bwd_over_fwd": t_jb / t_j,
                     "device_status": status_b,
                     "how": "gvx_event_pair_masses_bwd, pair-mass and event-sum gradients U[-1, 1]"},
+        "select": {"ms": t_js, "events_per_s": n_ev / (t_js * 1e-3),
+                   "pairs_per_s": n_pairs / (t_js * 1e-3), "selected_pairs": sel_pairs,
+                   "device_status": status_s,
+                   "how": "gvx_event_pair_select: pt >= 20, |eta| <= 2.5, 200 bins over "
+                          "[0, 400), best candidate for 91.1876; no pair mass stored"},
         }
     if "fwd_bwd" in which:
         # forward + backward, FP64 and FP32, N = 2^24

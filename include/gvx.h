@@ -182,6 +182,36 @@ gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *off
                                      gvx_lv *grad_particles, void *stream);
 
 /*
+ * Fused per-event analysis step (FP64): particle selection, a histogram of the pair masses of
+ * the selected particles, and per event the selected pair closest to a target mass -- the use
+ * of the per-event combinatorics in RDataFrame analyses that the paper names as its next target
+ * (Sec. 6; it defines no such step, so the semantics are these).  No pair mass is stored.
+ *   particles, offsets, n_events, n_particles: as gvx_event_pair_masses.
+ *   pt_min, eta_max: a particle is selected when pt >= pt_min and |eta| <= eta_max.
+ *   lo, hi, n_bins: n_bins equal bins over [lo, hi), 1 <= n_bins <= GVX_SELECT_MAX_BINS, lo < hi.
+ *   counts: in/out, n_bins + 2 uint64 in device memory; the counts of this call are ADDED:
+ *           counts[0] m < lo, counts[1 + b] bin b = floor((m - lo) * (n_bins / (hi - lo)))
+ *           (double arithmetic, clamped to [0, n_bins - 1]), counts[n_bins + 1] m >= hi or NaN.
+ *   target: the mass the best candidate is closest to.
+ *   best_k: out, n_events int64 (or NULL): the packed pair index k(i, j) (the order of
+ *           gvx_event_pair_masses) of the selected pair with the smallest |m - target|, the
+ *           smaller k on ties; -1 when the event has no selected pair.
+ *   best_m: out, n_events doubles (or NULL): that pair's mass, NaN when none.
+ * Pair masses are computed as in gvx_event_pair_masses (within 1e-12 relative of the definition;
+ * an event's scale comes from its selected particles, so the last bits may differ).  A mass
+ * within that tolerance of a bin edge or of another candidate's |m - target| may therefore
+ * land in the neighbouring bin or pick the other pair.  Malformed offsets
+ * are detected on the device (GVX_ERR_OFFSETS; such an event reports no candidate).  One launch;
+ * nothing is allocated.
+ */
+#define GVX_SELECT_MAX_BINS 4094
+gvx_status gvx_event_pair_select(const gvx_lv *particles, const int64_t *offsets,
+                                 int64_t n_events, int64_t n_particles, double pt_min,
+                                 double eta_max, double lo, double hi, int32_t n_bins,
+                                 double target, uint64_t *counts, int64_t *best_k, double *best_m,
+                                 void *stream);
+
+/*
  * gvx_event_pair_masses without a workspace argument, for callers that cannot allocate device
  * memory: code that runs where cudaMalloc is not allowed or not wanted -- inside a host callback
  * or a framework plugin that does not own the allocator, in a pipeline with a fixed memory budget

@@ -306,6 +306,36 @@ def event_pair_masses_bwd(particles, offsets, pair_offsets, grad_pair_m, grad_su
     return gp
 
 
+def event_pair_select(particles, offsets, pt_min, eta_max, lo, hi, n_bins, target, counts=None,
+                      layout=None, stream=None):
+    """gvx_event_pair_select: the fused selection + pair-mass histogram + best candidate per
+    event (FP64, one launch, no pair mass stored).  Returns (counts, best_k, best_m): counts is
+    an int64 tensor of n_bins + 2 slots (under, bins, over) that this call adds to (a new zero
+    tensor when ``counts`` is None); best_k the packed pair index per event (-1 when none),
+    best_m its mass (NaN when none)."""
+    _require_cuda(particles, offsets)
+    if particles.dtype != torch.float64:
+        raise TypeError("the jagged form takes float64 particles")
+    if offsets.dtype != torch.int64 or not offsets.is_contiguous():
+        raise TypeError("offsets must be a contiguous int64 tensor")
+    lp = _layout_of(particles, 4, layout)
+    n_events = offsets.numel() - 1
+    dev = particles.device
+    if counts is None:
+        counts = torch.zeros(int(n_bins) + 2, dtype=torch.int64, device=dev)
+    elif counts.dtype != torch.int64 or counts.numel() != int(n_bins) + 2 or not counts.is_contiguous():
+        raise ValueError("counts must be a contiguous int64 tensor of n_bins + 2 slots")
+    best_k = torch.empty(max(n_events, 1), dtype=torch.int64, device=dev)
+    best_m = torch.empty(max(n_events, 1), dtype=torch.float64, device=dev)
+    st = load_library().gvx_event_pair_select(
+        ctypes.byref(_lv(particles, lp, 4)), ctypes.c_void_p(offsets.data_ptr()), n_events,
+        _count(particles, lp), float(pt_min), float(eta_max), float(lo), float(hi), int(n_bins),
+        float(target), ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(best_k.data_ptr()),
+        ctypes.c_void_p(best_m.data_ptr()), _stream(stream))
+    _lib.check(st, "gvx_event_pair_select")
+    return counts, best_k[:n_events], best_m[:n_events]
+
+
 class EventPairMassesGraph:
     """gvx_event_pair_masses captured once into a CUDA graph for fixed inputs and outputs.
 

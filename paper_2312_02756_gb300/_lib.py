@@ -30,7 +30,7 @@ EXPORTS = (
     "gvx_event_pair_masses_autotune", "gvx_event_pair_masses_graph_create",
     "gvx_graph_launch", "gvx_graph_destroy", "gvx_device_status",
     "gvx_testing_skip_first_tile", "gvx_event_pair_masses_noalloc",
-    "gvx_event_pair_masses_bwd",
+    "gvx_event_pair_masses_bwd", "gvx_event_pair_select",
 )
 
 
@@ -84,6 +84,9 @@ def _sigs(lib):
         "gvx_testing_skip_first_tile": ([I32], None),
         "gvx_event_pair_masses_noalloc": ([LVP, P, I64, I64, P, P, I64, LVP, P], S),
         "gvx_event_pair_masses_bwd": ([LVP, P, P, I64, I64, P, I64, LVP, LVP, P], S),
+        "gvx_event_pair_select": ([LVP, P, I64, I64, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, I32, ctypes.c_double, P, P,
+                                   P, P], S),
     }
     for name, (args, res) in table.items():
         fn = getattr(lib, name)

@@ -1,6 +1,7 @@
 // The C ABI (include/gvx.h): host-side validation, dispatch to the kernel translation units,
 // the device status word, the jagged-kernel autotuner table and captured graphs.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -305,6 +306,26 @@ gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *off
                                                grad_event_sum ? &gs : nullptr,
                                                gvx::as_out(*grad_particles),
                                                (cudaStream_t)stream));
+}
+
+gvx_status gvx_event_pair_select(const gvx_lv *particles, const int64_t *offsets,
+                                 int64_t n_events, int64_t n_particles, double pt_min,
+                                 double eta_max, double lo, double hi, int32_t n_bins,
+                                 double target, uint64_t *counts, int64_t *best_k, double *best_m,
+                                 void *stream) {
+  if (n_events < 0 || n_particles < 0) return GVX_ERR_SIZE;
+  if (n_bins < 1 || n_bins > GVX_SELECT_MAX_BINS) return GVX_ERR_SIZE;
+  if (!(hi > lo) || !(fabs(hi - lo) < INFINITY)) return GVX_ERR_ARG;
+  if (!offsets || !counts) return GVX_ERR_NULL;
+  if ((uintptr_t)offsets % 8 || (uintptr_t)counts % 8 || (uintptr_t)best_k % 8 ||
+      (uintptr_t)best_m % 8)
+    return GVX_ERR_ALIGN;
+  if (n_events == 0) return GVX_OK;
+  if (n_particles > 0) GVX_TRY(check_lv(particles, GVX_F64, 4));
+  gvx::Lv p = particles ? gvx::as_in(*particles) : gvx::Lv{{0, 0, 0, 0}, GVX_SOA};
+  return from_cuda(gvx::launch_pair_select(p, offsets, n_events, n_particles, pt_min, eta_max,
+                                           lo, hi, n_bins, target, counts, best_k, best_m,
+                                           (cudaStream_t)stream));
 }
 
 int32_t gvx_event_pair_masses_num_shapes(void) { return gvx::event_pairs_num_shapes(); }
