@@ -495,6 +495,10 @@ def run_gvx(args):
     traffic = _profile_traffic(dom)
     if traffic is not None:
         roofline["traffic"] = traffic
+    issue = issue_roofline(dom, kern[dom]["ms"], clk.get("sm_mhz") if isinstance(clk, dict) else None,
+                           props.multi_processor_count)
+    if issue is not None:
+        roofline["issue"] = issue
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -531,13 +535,15 @@ def run_gvx(args):
     return 0
 
 
-# The sources each timed kernel is built from (the traffic counters are valid while these match).
+# The sources each timed kernel's device code is built from (the committed counters are valid
+# while these match; gvx_internal.h, which only declares the host-side launch functions, is left
+# out).
 _MASS_SRC = ("mass.cu", "mass_ff.cuh", "ff_tables.cuh", "ff.cuh", "pair_math.cuh", "common.cuh",
-             "gvx_internal.h", "../gen_tables.py")
+             "../gen_tables.py")
 KERNEL_SOURCES = {
     "mass_f64_soa": _MASS_SRC,
     "mass_f64_aos": _MASS_SRC,
-    "boost_f64_soa": ("boost.cu", "boost_ff.cuh", "ff.cuh", "common.cuh", "gvx_internal.h"),
+    "boost_f64_soa": ("boost.cu", "boost_ff.cuh", "ff.cuh", "common.cuh"),
 }
 
 
@@ -554,9 +560,9 @@ def sources_hash(kernel, read=None):
     return h.hexdigest()[:16]
 
 
-def _profile_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.json),
-    only while the kernel's sources are the ones the counters were taken from."""
+def _profile_entry(kernel):
+    """The committed ncu figures for `kernel` (profiles/traffic.json), only while the kernel's
+    sources are the ones the counters were taken from."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(path))
@@ -567,7 +573,29 @@ def _profile_traffic(kernel):
         return None
     if entry.get("sources_hash") != sources_hash(kernel):
         return None
-    return entry.get("bytes_per_launch")
+    return entry
+
+
+def _profile_traffic(kernel):
+    """DRAM bytes per launch of `kernel` (see _profile_entry)."""
+    entry = _profile_entry(kernel)
+    return entry.get("bytes_per_launch") if entry else None
+
+
+def issue_roofline(kernel, ms, sm_mhz, n_sms):
+    """The instruction-issue view of a kernel bound by issue rather than by DRAM: warp
+    instructions per launch (ncu, scaled like the traffic) over the launch time, against the
+    issue peak of the GPU -- four warp instructions per SM per clock at the sampled SM clock."""
+    entry = _profile_entry(kernel)
+    inst = entry.get("warp_inst_per_launch") if entry else None
+    if inst is None or not sm_mhz or not n_sms:
+        return None
+    achieved = inst / (ms * 1e-3)
+    peak = 4.0 * n_sms * sm_mhz * 1e6
+    return {"bound": "issue", "unit": "warp instructions/s", "achieved": achieved, "peak": peak,
+            "frac": achieved / peak, "warp_inst_per_launch": inst,
+            "peak_source": "4 issue slots x %d SMs x median sampled SM clock %.0f MHz"
+                           % (n_sms, sm_mhz)}
 
 
 def main():
