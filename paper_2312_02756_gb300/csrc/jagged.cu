@@ -74,34 +74,6 @@ __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long 
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Exclusive scan of one int64 per thread; *total gets the block sum.  Ends synchronised.
-template <int NT>
-__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *s_warp, int64_t *total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int64_t w = lane < NT / 32 ? s_warp[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < NT / 32) s_warp[lane] = w;
-  }
-  __syncthreads();
-  int64_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0);
-  *total = s_warp[NT / 32 - 1];
-  __syncthreads();
-  return excl;
-}
-
 template <int NT, int LP, int LS>
 __device__ void big_event(const JArgs &A, int64_t e, int64_t pbeg, int64_t n, int64_t out0,
                           double *s_red) {

@@ -3,16 +3,22 @@
 // RDataFrame-style use of the per-event combinatorics that GenVectorX names as its next target,
 // Sec. 6; the pair mass is that of Sec. 4.1, Fig. 1).  No pair mass is written to memory.
 //
-// One warp per event, warps of a CTA on different events.  Events of at most kLegCap particles:
-// the lanes load the particles, test the cuts, compact the selected ones in order (ballots),
-// find their scale (warp max of their leg exponents), and cache their float-float legs in the
-// warp's shared-memory slice; the lanes then walk the pairs of selected particles (their packed
-// index k in the order of gvx_event_pair_masses follows from the original positions) with the
-// float-float pair arithmetic of the FP64 mass kernel (the FP64 formulas outside its domain).  Each pair's slot goes to a per-CTA shared-memory histogram (integer atomics, so the
-// totals do not depend on the order), and each lane keeps its best (|m - target|, k); a shuffle
-// reduction picks the smallest |m - target|, then the smallest k.  Larger events take the same
-// loop with every pair evaluated from global memory.  At the end each CTA adds its histogram to
-// the caller's counts.
+// CTAs take tiles of kTE consecutive events (grid-stride) and stage them in sub-batches of whole
+// events of at most kNT particles.  Per sub-batch:
+//   (a) one thread per particle: load, cuts, and a block scan of the selection flags that gives
+//       every selected particle its place in a compacted list;
+//   (b) one thread per selected particle: the scale of its event (the largest leg exponent of
+//       the event's selected particles) and its float-float leg, stored at its compacted place;
+//       one thread per event: its number of selected pairs, and a block scan of those;
+//   (c) one thread per selected pair (in rounds of kRound): its packed index k in the order of
+//       gvx_event_pair_masses, its mass with the float-float pair arithmetic of the FP64 mass
+//       kernel (FP64 formulas outside its domain), its histogram slot (shared-memory integer
+//       atomics, so the totals do not depend on the order) and its |m - target| in shared
+//       memory; then one thread per event walks its pairs of the round in order and keeps the
+//       first smallest |m - target| -- exact, and the smaller k on ties.
+// Events of more than kNT particles are handled alone by the whole block, every pair from global
+// memory, with a block reduction of (|m - target|, k).  At the end each CTA adds its histogram
+// to the caller's counts.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -25,12 +31,15 @@
 namespace gvx {
 namespace {
 
-constexpr int kNT = 256;
-constexpr int kWarps = kNT / 32;
-constexpr int kLegCap = 64;  // particles per event cached in shared memory
-constexpr unsigned kPass = 1u, kFast = 2u;
-// per warp: kLegCap legs (4 ff) + eta, phi (doubles) + flags
-constexpr size_t kWarpSmem = (size_t)kLegCap * (sizeof(ffm::LegFF) + 2 * sizeof(double) + sizeof(unsigned));
+constexpr int kTE = 64;       // events per tile
+constexpr int kNT = 256;      // threads per CTA, and particles per sub-batch
+constexpr int kRound = 512;   // selected pairs evaluated per round
+constexpr int kNoFast = -100000;
+// dynamic shared memory, first part: per compacted particle a leg, eta, phi, scale and original
+// position; per sub-batch particle its leg exponent and scan value; per round of pairs |m - t|,
+// m and k
+constexpr size_t kDynFixed = (size_t)kNT * (sizeof(ffm::LegFF) + 2 * sizeof(double) + 4 * sizeof(int)) +
+                             sizeof(int) + (size_t)kRound * (2 * sizeof(double) + sizeof(long long));
 
 struct SArgs {
   Lv p;
@@ -67,127 +76,215 @@ __device__ __forceinline__ double pair_mass_raw(V4<double> x, V4<double> y, cons
   return m;
 }
 
+// (d, k) before (d', k'): the smaller |m - target|, then the smaller k; k < 0 is "none".
+__device__ __forceinline__ bool better(double d, long long k, double d0, long long k0) {
+  return k >= 0 && (k0 < 0 || d < d0 || (d == d0 && k < k0));
+}
+
+// One event of more than kNT particles, by the whole block from global memory.
+template <int LP>
+__device__ void big_event_select(const SArgs &A, const ffm::TabRef &T, unsigned *s_hist,
+                                 int64_t pb, int64_t n, double *best_d, long long *best_k,
+                                 double *best_m, double *s_rd, long long *s_rk, double *s_rm) {
+  double bd = INFINITY, bm = NAN;
+  long long bk = -1;
+  const long long npairs = (long long)n * (n - 1) / 2;
+  for (long long k = threadIdx.x; k < npairs; k += kNT) {
+    int64_t i, j;
+    decode_pair_wide(k, n, i, j);
+    const V4<double> x = ld4c<LP>(A.p, pb + i), y = ld4c<LP>(A.p, pb + j);
+    if (!(passes(x.x, x.y, A) && passes(y.x, y.y, A))) continue;
+    const double m = pair_mass_raw(x, y, T);
+    atomicAdd(&s_hist[slot_of(m, A)], 1u);
+    const double d = fabs(m - A.target);
+    if (better(d, k, bd, bk)) {
+      bd = d;
+      bk = k;
+      bm = m;
+    }
+  }
+  s_rd[threadIdx.x] = bd;
+  s_rk[threadIdx.x] = bk;
+  s_rm[threadIdx.x] = bm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < kNT; t++)
+      if (better(s_rd[t], s_rk[t], bd, bk) || t == 0) {
+        bd = s_rd[t];
+        bk = s_rk[t];
+        bm = s_rm[t];
+      }
+    *best_d = bd;
+    *best_k = bk;
+    *best_m = bm;
+  }
+  __syncthreads();
+}
+
 template <int LP>
 __global__ void __launch_bounds__(kNT) pair_select_kernel(SArgs A) {
   extern __shared__ double s_dyn[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // dynamic shared memory: legs, eta, phi and flags of every warp's slice, then the histogram
-  ffm::LegFF *legs = reinterpret_cast<ffm::LegFF *>(s_dyn);
-  double *etas = reinterpret_cast<double *>(legs + kWarps * kLegCap);
-  double *phis = etas + kWarps * kLegCap;
-  unsigned *flags = reinterpret_cast<unsigned *>(phis + kWarps * kLegCap);
-  unsigned *s_hist = flags + kWarps * kLegCap;
-  ffm::LegFF *s_leg = legs + warp * kLegCap;
-  double *s_eta = etas + warp * kLegCap, *s_phi = phis + warp * kLegCap;
-  unsigned *s_flag = flags + warp * kLegCap;
+  ffm::LegFF *s_leg = reinterpret_cast<ffm::LegFF *>(s_dyn);          // by compacted place
+  double *s_eta = reinterpret_cast<double *>(s_leg + kNT), *s_phi = s_eta + kNT;
+  double *s_d = s_phi + kNT, *s_m = s_d + kRound;                       // by pair of the round
+  long long *s_k = reinterpret_cast<long long *>(s_m + kRound);
+  int *s_fs = reinterpret_cast<int *>(s_k + kRound), *s_orig = s_fs + kNT;  // by compacted place
+  int *s_ex = s_orig + kNT, *s_cs = s_ex + kNT;  // by particle of the sub-batch (s_cs: kNT + 1)
+  unsigned *s_hist = reinterpret_cast<unsigned *>(s_cs + kNT + 1);
   __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
   __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
+  __shared__ int64_t s_off[kTE + 1], s_pp[kTE + 1], s_warp[kNT / 32];
+  __shared__ double s_bd[kTE], s_bm[kTE];
+  __shared__ long long s_bk[kTE];
+  __shared__ int s_bad;
   for (int s = threadIdx.x; s < A.n_bins + 2; s += kNT) s_hist[s] = 0u;
   const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);  // ends with a barrier
 
-  const int64_t nw = (int64_t)gridDim.x * kWarps;
-  for (int64_t e = (int64_t)blockIdx.x * kWarps + warp; e < A.n_events; e += nw) {
-    const int64_t b0 = A.off[e], b1 = A.off[e + 1], n = b1 - b0;
-    if (b0 < 0 || n < 0 || b1 > A.n_particles || (e == 0 && b0 != 0) ||
-        (e == A.n_events - 1 && b1 != A.n_particles)) {
-      if (lane == 0) {
-        raise_status(A.status, GVX_ERR_OFFSETS);
-        if (A.best_k) A.best_k[e] = -1;
-        if (A.best_m) A.best_m[e] = NAN;
+  const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t e0 = tile * kTE;
+    const int ne = (int)(A.n_events - e0 < kTE ? A.n_events - e0 : kTE);
+    __syncthreads();  // the previous tile is done with the shared arrays
+    if (threadIdx.x == 0) s_bad = 0;
+    if (threadIdx.x <= ne) s_off[threadIdx.x] = A.off[e0 + threadIdx.x];
+    if (threadIdx.x < ne) {
+      s_bd[threadIdx.x] = INFINITY;
+      s_bk[threadIdx.x] = -1;
+      s_bm[threadIdx.x] = NAN;
+    }
+    __syncthreads();
+    if (threadIdx.x < ne) {
+      const int64_t a = s_off[threadIdx.x], b = s_off[threadIdx.x + 1];
+      bool bad = a < 0 || b < a || b > A.n_particles;
+      if (e0 + threadIdx.x == 0 && a != 0) bad = true;
+      if (e0 + threadIdx.x == A.n_events - 1 && b != A.n_particles) bad = true;
+      if (bad) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) {  // nothing of the tile is read; its events report no candidate
+      if (threadIdx.x == 0) raise_status(A.status, GVX_ERR_OFFSETS);
+      if (threadIdx.x < ne) {
+        if (A.best_k) A.best_k[e0 + threadIdx.x] = -1;
+        if (A.best_m) A.best_m[e0 + threadIdx.x] = NAN;
       }
       continue;
     }
-    double bd = INFINITY, bm = NAN;  // this lane's best |m - target|, its mass and index
-    long long bk = -1;
-    const int64_t npairs = n * (n - 1) / 2;
-    if (n <= kLegCap) {
-      // particles: cuts, then the selected ones compacted in order (ballots), their scale (warp
-      // max of their leg exponents) and their legs
-      V4<double> x[2];
-      unsigned sel[2];
-      int ex = 0;
-      for (int r = 0; r < 2; r++) {
-        const int t = lane + 32 * r;
-        x[r] = t < n ? ld4c<LP>(A.p, b0 + t) : V4<double>{0.0, 0.0, 0.0, 0.0};
-        const bool pass = t < n && passes(x[r].x, x[r].y, A);
-        sel[r] = __ballot_sync(0xffffffffu, pass);
-        const int et = pass ? ffm::leg_exponent(x[r].x, x[r].w) : 0;
-        ex = et > ex ? et : ex;
+    int sb = 0;
+    while (sb < ne) {
+      const int64_t pb = s_off[sb];
+      const bool fits =
+          threadIdx.x >= sb && threadIdx.x < ne && s_off[threadIdx.x + 1] - pb <= kNT;
+      const int sbe = sb + __syncthreads_count(fits);
+      if (sbe == sb) {  // one event larger than a sub-batch
+        big_event_select<LP>(A, T, s_hist, pb, s_off[sb + 1] - pb, &s_bd[sb], &s_bk[sb],
+                             &s_bm[sb], s_d, s_k, s_m);
+        sb++;
+        continue;
       }
-      const int emax = __reduce_max_sync(0xffffffffu, ex);
-      const int sc = emax - 1023;
-      const int ns = __popc(sel[0]) + __popc(sel[1]);
-      for (int r = 0; r < 2; r++) {
-        const int t = lane + 32 * r;
-        if ((sel[r] >> lane) & 1u) {
-          const int c = (r ? __popc(sel[0]) : 0) + __popc(sel[r] & ((1u << lane) - 1u));
-          s_eta[c] = x[r].y;
-          s_phi[c] = x[r].z;
-          unsigned f = kPass | ((unsigned)t << 8);  // the original position rides in the flags
-          if (ffm::scale_exponent_ok(emax) &&
-              ffm::leg_in_domain(x[r].x, x[r].y, x[r].z, x[r].w, emax)) {
-            bool ok = true;
-            s_leg[c] = ffm::make_leg_ff(x[r].x, x[r].y, x[r].w, sc, T, &ok);
-            f |= kFast;
-          }
-          s_flag[c] = f;
+      const int np = (int)(s_off[sbe] - pb), nev = sbe - sb;
+      const int k = threadIdx.x;
+      // (a) cuts and compaction
+      V4<double> x = {0.0, 0.0, 0.0, 0.0};
+      bool pass = false;
+      if (k < np) {
+        x = ld4<double, LP>(A.p, pb + k);
+        pass = passes(x.x, x.y, A);
+        s_ex[k] = pass ? ffm::leg_exponent(x.x, x.w) : 0;
+      }
+      int64_t nsel;
+      const int c = (int)block_excl_scan<kNT>(pass ? 1 : 0, s_warp, &nsel);  // ends synchronised
+      if (k < np) s_cs[k] = c;
+      if (k == 0) s_cs[np] = (int)nsel;
+      // (b) legs of the selected particles; selected pairs per event
+      if (pass) {
+        int e = sb, hi = sbe - 1;  // the particle's event: the last e with s_off[e] <= pb + k
+        while (e < hi) {
+          const int mid = (e + hi + 1) >> 1;
+          if (s_off[mid] <= pb + k) e = mid;
+          else hi = mid - 1;
         }
-      }
-      __syncwarp();
-      const int64_t nsp = (int64_t)ns * (ns - 1) / 2;
-      for (long long q = lane; q < nsp; q += 32) {
-        int64_t ci, cj;
-        decode_pair(q, ns, ci, cj);
-        const unsigned fi = s_flag[ci], fj = s_flag[cj];
-        const int64_t i = fi >> 8, j = fj >> 8;  // original positions, i < j
-        const long long k = i * n - i * (i + 1) / 2 + (j - i - 1);
-        double m;
-        bool done = false;
-        if (fi & fj & kFast) {
+        int emax = 0;
+        for (int t = (int)(s_off[e] - pb); t < (int)(s_off[e + 1] - pb); t++)
+          emax = s_ex[t] > emax ? s_ex[t] : emax;
+        int sc = kNoFast;
+        if (ffm::scale_exponent_ok(emax) && ffm::leg_in_domain(x.x, x.y, x.z, x.w, emax)) {
           bool ok = true;
-          const ffm::ff m2 = ffm::pair_m2_ff(s_leg[ci], s_leg[cj], s_eta[ci], s_eta[cj],
-                                              s_phi[ci], s_phi[cj], T, &ok);
-          done = ffm::finish_mass(m2, sc, ok, &m);
+          s_leg[c] = ffm::make_leg_ff(x.x, x.y, x.w, emax - 1023, T, &ok);
+          sc = emax - 1023;
         }
-        if (!done) m = pair_mass_raw(ld4c<LP>(A.p, b0 + i), ld4c<LP>(A.p, b0 + j), T);
-        atomicAdd(&s_hist[slot_of(m, A)], 1u);
-        const double d = fabs(m - A.target);
-        if (d < bd) {  // k grows along the lane's loop: an equal later pair keeps the first
-          bd = d;
-          bk = k;
-          bm = m;
-        }
+        s_fs[c] = sc;
+        s_orig[c] = k;
+        s_eta[c] = x.y;
+        s_phi[c] = x.z;
       }
-      __syncwarp();  // the slice is reused by the warp's next event
-    } else {
-      for (long long k = lane; k < npairs; k += 32) {
-        int64_t i, j;
-        decode_pair_wide(k, n, i, j);
-        const V4<double> x = ld4c<LP>(A.p, b0 + i), y = ld4c<LP>(A.p, b0 + j);
-        if (!(passes(x.x, x.y, A) && passes(y.x, y.y, A))) continue;
-        const double m = pair_mass_raw(x, y, T);
-        atomicAdd(&s_hist[slot_of(m, A)], 1u);
-        const double d = fabs(m - A.target);
-        if (d < bd) {
-          bd = d;
-          bk = k;
-          bm = m;
-        }
+      __syncthreads();  // s_cs complete
+      int64_t npairs_ev = 0;
+      if (threadIdx.x < nev) {
+        const int st = (int)(s_off[sb + threadIdx.x] - pb), en = (int)(s_off[sb + threadIdx.x + 1] - pb);
+        const int64_t ns = s_cs[en] - s_cs[st];
+        npairs_ev = ns * (ns - 1) / 2;
       }
+      int64_t total;
+      const int64_t pex = block_excl_scan<kNT>(npairs_ev, s_warp, &total);  // ends synchronised
+      if (threadIdx.x < nev) s_pp[threadIdx.x] = pex;
+      if (threadIdx.x == 0) s_pp[nev] = total;
+      __syncthreads();
+      // (c) the selected pairs, in rounds
+      for (int64_t r0 = 0; r0 < total; r0 += kRound) {
+        const int64_t r1 = total - r0 < kRound ? total : r0 + kRound;
+        for (int64_t q = r0 + threadIdx.x; q < r1; q += kNT) {
+          int e = 0, hi = nev - 1;  // the pair's event within the sub-batch
+          while (e < hi) {
+            const int mid = (e + hi + 1) >> 1;
+            if (s_pp[mid] <= q) e = mid;
+            else hi = mid - 1;
+          }
+          const int st = (int)(s_off[sb + e] - pb);
+          const int64_t n = s_off[sb + e + 1] - s_off[sb + e];
+          const int64_t ns = s_cs[st + (int)n] - s_cs[st];
+          int64_t a, b;
+          decode_pair(q - s_pp[e], ns, a, b);
+          const int ci = s_cs[st] + (int)a, cj = s_cs[st] + (int)b;
+          const int64_t i = s_orig[ci] - st, j = s_orig[cj] - st;  // positions in the event
+          double m;
+          bool done = false;
+          const int sc = s_fs[ci];
+          if (sc != kNoFast && s_fs[cj] != kNoFast) {
+            bool ok = true;
+            const ffm::ff m2 = ffm::pair_m2_ff(s_leg[ci], s_leg[cj], s_eta[ci], s_eta[cj],
+                                                s_phi[ci], s_phi[cj], T, &ok);
+            done = ffm::finish_mass(m2, sc, ok, &m);
+          }
+          if (!done) m = pair_mass_raw(ld4c<LP>(A.p, pb + st + i), ld4c<LP>(A.p, pb + st + j), T);
+          atomicAdd(&s_hist[slot_of(m, A)], 1u);
+          s_d[q - r0] = fabs(m - A.target);
+          s_m[q - r0] = m;
+          s_k[q - r0] = i * n - i * (i + 1) / 2 + (j - i - 1);
+        }
+        __syncthreads();
+        if (threadIdx.x < nev) {  // each event's pairs of the round, in order
+          const int e = threadIdx.x;
+          const int64_t q0 = s_pp[e] > r0 ? s_pp[e] : r0, q1 = s_pp[e + 1] < r1 ? s_pp[e + 1] : r1;
+          double bd = s_bd[sb + e], bm = s_bm[sb + e];
+          long long bk = s_bk[sb + e];
+          for (int64_t q = q0; q < q1; q++)
+            if (better(s_d[q - r0], s_k[q - r0], bd, bk)) {
+              bd = s_d[q - r0];
+              bk = s_k[q - r0];
+              bm = s_m[q - r0];
+            }
+          s_bd[sb + e] = bd;
+          s_bk[sb + e] = bk;
+          s_bm[sb + e] = bm;
+        }
+        __syncthreads();
+      }
+      sb = sbe;
     }
-    for (int o = 16; o > 0; o >>= 1) {  // smallest |m - target|, then smallest k
-      const double od = __shfl_down_sync(0xffffffffu, bd, o);
-      const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
-      const double om = __shfl_down_sync(0xffffffffu, bm, o);
-      if (ok >= 0 && (bk < 0 || od < bd || (od == bd && ok < bk))) {
-        bd = od;
-        bk = ok;
-        bm = om;
-      }
-    }
-    if (lane == 0) {
-      if (A.best_k) A.best_k[e] = bk;
-      if (A.best_m) A.best_m[e] = bk >= 0 ? bm : NAN;
+    __syncthreads();
+    if (threadIdx.x < ne) {
+      if (A.best_k) A.best_k[e0 + threadIdx.x] = s_bk[threadIdx.x];
+      if (A.best_m) A.best_m[e0 + threadIdx.x] = s_bk[threadIdx.x] >= 0 ? s_bm[threadIdx.x] : NAN;
     }
   }
   __syncthreads();
@@ -198,18 +295,11 @@ __global__ void __launch_bounds__(kNT) pair_select_kernel(SArgs A) {
 template <int LP>
 cudaError_t launch_l(const SArgs &A, cudaStream_t s) {
   constexpr auto k = pair_select_kernel<LP>;
-  const size_t smem = kWarps * kWarpSmem + (size_t)(A.n_bins + 2) * sizeof(unsigned);
+  const size_t smem = kDynFixed + (size_t)(A.n_bins + 2) * sizeof(unsigned);
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kNT, smem);
-  if (err != cudaSuccess) return err;
-  if (per_sm < 1) per_sm = 1;
-  int64_t need = (A.n_events + kWarps - 1) / kWarps;
-  int64_t cap = (int64_t)num_sms() * per_sm * kWaves;
-  int64_t grid = need < cap ? need : cap;
-  if (grid < 1) grid = 1;
-  k<<<(unsigned)grid, kNT, smem, s>>>(A);
+  const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
+  k<<<balanced_grid_of<k>(kNT, smem, n_tiles, 1), kNT, smem, s>>>(A);
   return cudaGetLastError();
 }
 
