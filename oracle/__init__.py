@@ -62,6 +62,8 @@ def _load():
         "orc_boost_grad_def": ([P, P, I64, P, I64, P, P], None),
         "orc_event_pairs_def": ([P, P, I64, P, P, P], INT),
         "orc_event_pairs_grad_def": ([P, P, I64, P, P, P], INT),
+        "orc_lorentz_apply_def": ([P, I64, P, I64, P], None),
+        "orc_mass_cart_def": ([P, P, I64, INT, P], None),
         "orc_pair_select_def": ([P, P, I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                  P, P, P, P], INT),
@@ -231,6 +233,31 @@ def pair_select_def(p, offsets, pt_min, eta_max, lo, hi, n_bins, target, rel_tol
     if rc != 0:
         raise ValueError("malformed offsets or histogram range")
     return counts, near, best_k[:n_ev], best_m[:n_ev]
+
+
+def lorentz_apply_def(L, v) -> np.ndarray:
+    """O1 general Lorentz transformation: L (4, 4) shared or (n, 4, 4) per vector, applied to
+    PxPyPzE rows v (n, 4), in binary128, rounded once."""
+    v = _rows(v, 4)
+    Lm = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
+    if Lm.shape == (4, 4):
+        stride = 0
+    elif Lm.shape == (v.shape[0], 4, 4):
+        stride = 1
+    else:
+        raise ValueError("L must be (4, 4) or (n, 4, 4)")
+    out = np.empty_like(v)
+    _load().orc_lorentz_apply_def(_ptr(Lm), stride, _ptr(v), v.shape[0], _ptr(out))
+    return out
+
+
+def mass_cart_def(a, b, coords="pxpypze") -> np.ndarray:
+    """O1 pair mass for Cartesian legs: coords 'pxpypze' (E stored) or 'pxpypzm' (m stored)."""
+    a, b = _rows(a, 4), _rows(b, 4)
+    code = {"pxpypze": 0, "pxpypzm": 1}[coords]
+    m = np.empty(a.shape[0])
+    _load().orc_mass_cart_def(_ptr(a), _ptr(b), a.shape[0], code, _ptr(m))
+    return m
 
 
 def to_cartesian_def(p) -> np.ndarray:

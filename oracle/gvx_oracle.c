@@ -537,6 +537,51 @@ int orc_pair_select_def(const double *p, const int64_t *off, int64_t n_events, d
   return 0;
 }
 
+/* A general 4-D Lorentz transformation applied to PxPyPzE vectors (Sec. 4.1: transformations
+ * are 4x4 matrices applied to every vector of an array; Sec. 3.1: vectors in any coordinate
+ * system).  out[i] = L[i * l_stride] v[i], L row-major 4x4 in (x, y, z, t) order, evaluated in
+ * binary128 and rounded once.  l_stride 0 applies one matrix to every vector.  The matrix is
+ * taken as given (no check that it preserves the metric). */
+void orc_lorentz_apply_def(const double *L16, int64_t l_stride, const double *v, int64_t n,
+                           double *out) {
+  for (int64_t i = 0; i < n; i++) {
+    const double *L = L16 + 16 * l_stride * i;
+    for (int r = 0; r < 4; r++) {
+      qreal acc = 0;
+      for (int k = 0; k < 4; k++) acc += (qreal)L[4 * r + k] * (qreal)v[4 * i + k];
+      out[4 * i + r] = (double)acc;
+    }
+  }
+}
+
+/* A Cartesian leg as PxPyPzE in binary128: coords 0 gives (px, py, pz, E) as stored, coords 1
+ * gives (px, py, pz, m) and E = sqrt(px^2 + py^2 + pz^2 + m^2) (the stored m enters through m^2). */
+static void cart_leg_q(const double *x, int coords, qreal out[4]) {
+  out[0] = x[0];
+  out[1] = x[1];
+  out[2] = x[2];
+  if (coords == 0) {
+    out[3] = x[3];
+  } else {
+    qreal m = x[3];
+    out[3] = Q_SQRT(out[0] * out[0] + out[1] * out[1] + out[2] * out[2] + m * m);
+  }
+}
+
+/* Invariant mass of pairs given in a Cartesian coordinate system (Sec. 3.1: the kernels are
+ * templated on the 4-D system; Sec. 4.1 Fig. 1 adds the pair and takes mass()): coords 0 =
+ * PxPyPzE, 1 = PxPyPzM.  m[i] = mass(a[i] + b[i]) with mass() as in lv_mass_q (a negative
+ * E^2 - |p|^2 gives -sqrt of its magnitude, GenVector's convention for spacelike vectors). */
+void orc_mass_cart_def(const double *a, const double *b, int64_t n, int coords, double *m) {
+  for (int64_t i = 0; i < n; i++) {
+    qreal va[4], vb[4], w[4];
+    cart_leg_q(a + 4 * i, coords, va);
+    cart_leg_q(b + 4 * i, coords, vb);
+    for (int k = 0; k < 4; k++) w[k] = va[k] + vb[k];
+    m[i] = (double)lv_mass_q(w);
+  }
+}
+
 /* PtEtaPhiM -> PxPyPzE rounded to double (used by the tests to build boost inputs and
  * multi-body checks). */
 void orc_to_cartesian_def(const double *p, int64_t n, double *out) {

@@ -554,3 +554,106 @@ def test_pair_select_hand_case_and_ties(orc):
     # three pairs)
     counts, _, _, _ = orc.pair_select_def(p, off, 20.0, 0.4, 0.0, 200.0, 20, 91.0)
     assert counts.sum() == 4
+
+
+# ------------------------------------------------- other coordinate systems, general transformations
+
+def _mp_matvec(mp, L, v):
+    return [sum(mp.mpf(float(L[r, k])) * mp.mpf(float(v[k])) for k in range(4)) for r in range(4)]
+
+
+def test_lorentz_apply_identity_rotation_and_brute_force(orc):
+    """The identity returns the input exactly; a rotation about z matches its closed form; on
+    random matrices every component equals the 50-digit product rounded (within one ulp); a
+    per-vector matrix array gives each vector its own matrix."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    g = syn.rng(126)
+    v = syn.pxpypze(g, 200)
+    assert np.array_equal(orc.lorentz_apply_def(np.eye(4), v), v)
+    th = 0.7
+    R = np.eye(4)
+    R[0, 0], R[0, 1], R[1, 0], R[1, 1] = np.cos(th), -np.sin(th), np.sin(th), np.cos(th)
+    out = orc.lorentz_apply_def(R, v)
+    want = np.stack([v[:, 0] * R[0, 0] + v[:, 1] * R[0, 1], v[:, 0] * R[1, 0] + v[:, 1] * R[1, 1],
+                     v[:, 2], v[:, 3]], axis=1)
+    assert np.all(np.abs(out - want) <= 4e-16 * np.abs(v).sum(axis=1, keepdims=True))
+    Ls = g.uniform(-2, 2, (50, 4, 4))
+    out = orc.lorentz_apply_def(Ls, v[:50])
+    for i in range(50):
+        ref = _mp_matvec(mp, Ls[i], v[i])
+        for r in range(4):
+            assert abs(out[i, r] - float(ref[r])) <= np.spacing(abs(float(ref[r]))), (i, r)
+
+
+def test_lorentz_apply_composition_and_metric(orc):
+    """L1 (L2 v) = (L1 L2) v up to rounding (the product taken in mpmath), and a boost matrix
+    keeps the mass of the vector."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    g = syn.rng(127)
+    v = syn.pxpypze(g, 100)
+    L1 = orc.boost_matrix_def(np.array([0.3, -0.2, 0.5]))
+    L2 = orc.boost_matrix_def(np.array([-0.6, 0.1, 0.0]))
+    L12 = np.array([[float(sum(mp.mpf(L1[r, k]) * mp.mpf(L2[k, c]) for k in range(4)))
+                     for c in range(4)] for r in range(4)])
+    a = orc.lorentz_apply_def(L1, orc.lorentz_apply_def(L2, v))
+    b = orc.lorentz_apply_def(L12, v)
+    scale = np.abs(v).sum(axis=1, keepdims=True) * 10
+    assert np.all(np.abs(a - b) <= 1e-14 * scale)
+    m0, m1 = orc.lv_mass_def(v), orc.lv_mass_def(orc.lorentz_apply_def(L1, v))
+    assert np.all(np.abs(m1 - m0) <= 1e-10 * v[:, 3])
+
+
+def _mp_cart_mass(mp, a, b, coords):
+    def leg(x):
+        px, py, pz, w = (mp.mpf(float(t)) for t in x)
+        E = w if coords == "pxpypze" else mp.sqrt(px * px + py * py + pz * pz + w * w)
+        return px, py, pz, E
+    u, w = leg(a), leg(b)
+    s = [u[k] + w[k] for k in range(4)]
+    m2 = s[3] ** 2 - s[0] ** 2 - s[1] ** 2 - s[2] ** 2
+    return mp.sqrt(m2) if m2 >= 0 else -mp.sqrt(-m2)
+
+
+def test_mass_cart_brute_force_and_closed_form(orc):
+    """Cartesian pair masses (E or m stored) against 50-digit brute force on random and
+    near-collinear light pairs; massless legs (E = |p| exactly representable: Pythagorean
+    momenta) against 2 (|p1||p2| - p1.p2) in closed form."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    g = syn.rng(128)
+    v = syn.pxpypze(g, 400)
+    a, b = v[:200], v[200:].copy()
+    b[:50, :3] = a[:50, :3] * (1 + 1e-7)  # near-collinear
+    b[:50, 3] = np.sqrt(np.sum(b[:50, :3] ** 2, axis=1) + 1e-6)
+    for coords in ("pxpypze", "pxpypzm"):
+        aa, bb = a.copy(), b.copy()
+        if coords == "pxpypzm":
+            aa[:, 3], bb[:, 3] = g.uniform(0, 10, 200), g.uniform(0, 1e-3, 200)
+        m = orc.mass_cart_def(aa, bb, coords)
+        for i in range(0, 200, 3):
+            ref = _mp_cart_mass(mp, aa[i], bb[i], coords)
+            assert abs(m[i] - float(ref)) <= 1e-15 * abs(float(ref)) + 1e-300, (coords, i)
+    # massless legs: (3, 4, 12) has |p| = 13 exactly
+    a = np.array([[3.0, 4.0, 12.0, 13.0], [0.0, 0.0, 5.0, 5.0]])
+    b = np.array([[-4.0, 3.0, 12.0, 13.0], [0.0, 3.0, 4.0, 5.0]])
+    m = orc.mass_cart_def(a, b)
+    p1, p2 = a[:, :3], b[:, :3]
+    want = np.sqrt(2 * (np.linalg.norm(p1, axis=1) * np.linalg.norm(p2, axis=1) - np.sum(p1 * p2, axis=1)))
+    assert np.all(np.abs(m - want) <= 1e-15 * want)
+
+
+def test_mass_cart_rotation_invariance(orc):
+    """A rotation by 90 degrees about z maps doubles to doubles exactly and leaves every pair
+    mass unchanged; the stored m of the PxPyPzM form enters through m^2 only."""
+    g = syn.rng(129)
+    v = syn.pxpypze(g, 600)
+    a, b = v[:300], v[300:]
+    rot = lambda x: np.stack([-x[:, 1], x[:, 0], x[:, 2], x[:, 3]], axis=1)
+    assert np.array_equal(orc.mass_cart_def(a, b), orc.mass_cart_def(rot(a), rot(b)))
+    am = a.copy()
+    am[:, 3] = g.uniform(0, 10, 300)
+    neg = am.copy()
+    neg[:, 3] *= -1
+    assert np.array_equal(orc.mass_cart_def(am, b, "pxpypzm"), orc.mass_cart_def(neg, b, "pxpypzm"))
