@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "inv-mass & boost vectors/s at N=2^26 FP64/FP32, % roofline; fwd+bwd vs fwd"
 UNIT = "vectors/s"
 N_FULL = 1 << 26
-FORMS = ("fp32", "jagged", "fwd_bwd")
+FORMS = ("fp32", "jagged", "fwd_bwd", "coords")
 WORKLOAD = ("FP64 invariant mass of 2^26 PtEtaPhiM pairs in SoA and in AoS, plus FP64 boost of "
             "2^26 PxPyPzE vectors by per-vector beta (|beta| <= 0.99)")
 BYTES_MASS_F64 = 72    # 2 legs x 4 doubles in + 1 double out, per pair
@@ -356,6 +356,32 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
                        "boost_fwd_ms": t_bf, "boost_fwd_bwd_ms": t_bfb, "boost_ratio": t_bfb / t_bf}
         out["workload"] = "N = 2^24 pairs / vectors, SoA, upstream gradients uniform in [-1, 1]"
         res["fwd_bwd"] = out
+    if "coords" in which:
+        # other coordinate systems: FP64 pair masses of 2^26 Cartesian pairs (E stored) and a
+        # general Lorentz transformation (one shared 4x4 matrix) of 2^26 PxPyPzE vectors
+        g = syn.rng(5)
+        a = torch.as_tensor(syn.pxpypze(g, N_FULL).T.copy()).cuda()
+        b = torch.as_tensor(syn.pxpypze(g, N_FULL).T.copy()).cuda()
+        m = torch.empty(N_FULL, dtype=torch.float64, device="cuda")
+        la, lb = Step._lv(a, 0, 4), Step._lv(b, 0, 4)
+        t_c = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass_cart(
+            r(la), r(lb), P(m.data_ptr()), N_FULL, 1, 0, s)), stream, steps, warmup)
+        L = torch.as_tensor(np.array([[1.2, 0.1, 0.0, 0.5], [0.1, 1.1, 0.2, 0.0],
+                                      [0.0, 0.2, 1.3, 0.4], [0.5, 0.0, 0.4, 1.5]])).cuda()
+        o = torch.empty_like(a)
+        lo = Step._lv(o, 0, 4)
+        t_l = time_loop(torch, lambda: _lib.check(lib.gvx_lorentz_apply(
+            P(L.data_ptr()), 0, r(la), r(lo), N_FULL, 0, s)), stream, steps, warmup)
+        del a, b, m, o, L
+        torch.cuda.empty_cache()
+        res["coords"] = {
+            "workload": "FP64, 2^26 elements, SoA: pair masses of PxPyPzE legs; a shared 4x4 "
+                        "Lorentz transformation of PxPyPzE vectors",
+            "mass_pxpypze_ms": t_c, "mass_pxpypze_pairs_per_s": N_FULL / (t_c * 1e-3),
+            "mass_pxpypze_GBps": 72 * N_FULL / (t_c * 1e-3) / 1e9,
+            "lorentz_apply_ms": t_l, "lorentz_apply_vectors_per_s": N_FULL / (t_l * 1e-3),
+            "lorentz_apply_GBps": 64 * N_FULL / (t_l * 1e-3) / 1e9,
+        }
     return res
 
 

@@ -66,6 +66,9 @@ typedef enum {
 
 typedef enum { GVX_F64 = 0, GVX_F32 = 1 } gvx_dtype;
 typedef enum { GVX_SOA = 0, GVX_AOS = 1 } gvx_layout;
+/* 4-D coordinate systems of a Lorentz-vector array (the component order of an AoS struct or of
+ * the four SoA arrays). */
+typedef enum { GVX_PTETAPHIM = 0, GVX_PXPYPZE = 1, GVX_PXPYPZM = 2 } gvx_coords;
 
 typedef struct {
   void *c[4];     /* see "Layout of a Lorentz-vector array" above */
@@ -117,6 +120,30 @@ gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *
  */
 gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, gvx_lv *out,
                      int64_t n, int32_t dtype, void *stream);
+
+/*
+ * Pair masses of Cartesian legs: m[i] = mass(a[i] + b[i]) for coords GVX_PXPYPZE (components
+ * px, py, pz, E) or GVX_PXPYPZM (px, py, pz, m; E = sqrt(|p|^2 + m^2)) -- the invariant mass of
+ * Sec. 4.1 on the other 4-D coordinate systems of Sec. 3.1.  A spacelike sum gives -sqrt of
+ * |E^2 - |P|^2| (GenVector's convention).  FP64: within 1e-12 relative of the definition for
+ * legs with E^2 >= |p|^2 (the cancellation-free form with an exact cross product and an exact
+ * E^2 - |p|^2); FP32 legs are evaluated the same way in FP64 and rounded once (a float E next to
+ * a float |p| leaves E^2 - |p|^2 as rounding noise of either sign).  Layouts
+ * and alignment as gvx_invariant_mass; coords GVX_PTETAPHIM is gvx_invariant_mass itself.
+ */
+gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n,
+                                   int32_t coords, int32_t dtype, void *stream);
+
+/*
+ * A general 4-D Lorentz transformation (Sec. 4.1: 4x4 matrices applied to every vector of an
+ * array): out[i] = L_i v[i] for PxPyPzE vectors, L row-major 4x4 in (x, y, z, t) order.
+ * l_stride 0: L holds one matrix (16 scalars) for every vector; 1: L holds n matrices, 16
+ * scalars each, contiguous.  Four FMA chains per vector in the working precision (no structure
+ * of L is assumed, so the error is a few ulps of sum_k |L_rk v_k| per component).  L must be
+ * aligned to 16 bytes when l_stride is 1.
+ */
+gvx_status gvx_lorentz_apply(const void *L, int64_t l_stride, const gvx_lv *v, gvx_lv *out,
+                             int64_t n, int32_t dtype, void *stream);
 
 /* Bytes of workspace gvx_boost_bwd needs (0 unless beta_stride == 0). */
 size_t gvx_boost_bwd_workspace(int64_t n, int64_t beta_stride, int32_t dtype);

@@ -140,6 +140,51 @@ def invariant_mass(a: torch.Tensor, b: torch.Tensor, layout_a=None, layout_b=Non
 
 # ---------------------------------------------------------------------------------------- boost
 
+_COORDS = {"pxpypze": 1, "pxpypzm": 2}
+
+
+def invariant_mass_cart(a: torch.Tensor, b: torch.Tensor, coords: str = "pxpypze",
+                        layout_a=None, layout_b=None) -> torch.Tensor:
+    """Pair masses of Cartesian legs (gvx_invariant_mass_cart): coords 'pxpypze' (E stored) or
+    'pxpypzm' (m stored), FP64 or FP32, SoA or AoS like invariant_mass."""
+    _require_cuda(a, b)
+    la, lb = _layout_of(a, 4, layout_a), _layout_of(b, 4, layout_b)
+    if a.dtype != b.dtype:
+        raise TypeError("both legs must have the same dtype")
+    n = _count(a, la)
+    if _count(b, lb) != n:
+        raise ValueError("both legs must hold the same number of vectors")
+    m = torch.empty(n, dtype=a.dtype, device=a.device)
+    st = load_library().gvx_invariant_mass_cart(
+        ctypes.byref(_lv(a, la, 4)), ctypes.byref(_lv(b, lb, 4)), ctypes.c_void_p(m.data_ptr()), n,
+        _COORDS[coords], _dtype_code(a), _stream())
+    _lib.check(st, "gvx_invariant_mass_cart")
+    return m
+
+
+def lorentz_apply(L: torch.Tensor, v: torch.Tensor, layout=None) -> torch.Tensor:
+    """A general Lorentz transformation (gvx_lorentz_apply): L (4, 4) for every vector or
+    (n, 4, 4) one per vector, applied to PxPyPzE vectors v ((n, 4) or (4, n))."""
+    _require_cuda(L, v)
+    lv = _layout_of(v, 4, layout)
+    n = _count(v, lv)
+    if L.dtype != v.dtype:
+        raise TypeError("L and v must have the same dtype")
+    L = L.contiguous()
+    if tuple(L.shape) == (4, 4):
+        stride = 0
+    elif tuple(L.shape) == (n, 4, 4):
+        stride = 1
+    else:
+        raise ValueError("L must be (4, 4) or (n, 4, 4)")
+    out = torch.empty_like(v)
+    st = load_library().gvx_lorentz_apply(ctypes.c_void_p(L.data_ptr()), stride,
+                                          ctypes.byref(_lv(v, lv, 4)), ctypes.byref(_lv(out, lv, 4)),
+                                          n, _dtype_code(v), _stream())
+    _lib.check(st, "gvx_lorentz_apply")
+    return out
+
+
 def _beta_args(beta: torch.Tensor, n: int, layout=None):
     if beta.dim() == 1:
         if beta.numel() != 3 or not beta.is_contiguous():

@@ -215,6 +215,35 @@ gvx_status gvx_invariant_mass(const gvx_lv *a, const gvx_lv *b, void *m, int64_t
       gvx::launch_mass(gvx::as_in(*a), gvx::as_in(*b), m, n, dtype, (cudaStream_t)stream));
 }
 
+gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n,
+                                   int32_t coords, int32_t dtype, void *stream) {
+  if (coords == GVX_PTETAPHIM) return gvx_invariant_mass(a, b, m, n, dtype, stream);
+  if (coords != GVX_PXPYPZE && coords != GVX_PXPYPZM) return GVX_ERR_ARG;
+  if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
+  if (n < 0) return GVX_ERR_SIZE;
+  if (n == 0) return GVX_OK;
+  GVX_TRY(check_lv(a, dtype, 4));
+  GVX_TRY(check_lv(b, dtype, 4));
+  if (!m) return GVX_ERR_NULL;
+  if ((uintptr_t)m % scalar_size(dtype)) return GVX_ERR_ALIGN;
+  return from_cuda(gvx::launch_mass_cart(gvx::as_in(*a), gvx::as_in(*b), m, n, coords, dtype,
+                                         (cudaStream_t)stream));
+}
+
+gvx_status gvx_lorentz_apply(const void *L, int64_t l_stride, const gvx_lv *v, gvx_lv *out,
+                             int64_t n, int32_t dtype, void *stream) {
+  if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
+  if (n < 0) return GVX_ERR_SIZE;
+  if (l_stride != 0 && l_stride != 1) return GVX_ERR_ARG;
+  if (n == 0) return GVX_OK;
+  if (!L) return GVX_ERR_NULL;
+  if ((uintptr_t)L % (l_stride ? 16 : scalar_size(dtype))) return GVX_ERR_ALIGN;
+  GVX_TRY(check_lv(v, dtype, 4));
+  GVX_TRY(check_lv(out, dtype, 4));
+  return from_cuda(gvx::launch_lorentz_apply(L, l_stride, gvx::as_in(*v), gvx::as_out(*out), n,
+                                             dtype, (cudaStream_t)stream));
+}
+
 gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *grad_m,
                                   gvx_lv *grad_a, gvx_lv *grad_b, int64_t n, int32_t dtype,
                                   void *stream) {

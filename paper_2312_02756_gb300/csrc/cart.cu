@@ -1,0 +1,133 @@
+// Other 4-D coordinate systems and general Lorentz transformations (GenVectorX Sec. 3.1: vectors
+// are templated on their coordinate system; Sec. 4.1: transformations are 4x4 matrices applied
+// to every vector of an array).
+//
+// gvx_invariant_mass_cart: pair masses of Cartesian legs, PxPyPzE or PxPyPzM, with the
+// cancellation-free form of cart_mass.cuh (an FMA-exact cross product and E^2 - |p|^2), in FP64
+// for both storage precisions.  It runs on the FP64 pipe, roots and divisions included: correct
+// first; the float-float treatment of the PtEtaPhiM kernel is the next step for it.
+//
+// gvx_lorentz_apply: out = L v for a row-major 4x4 matrix L, shared or one per vector, as four
+// FMA chains per vector in the working precision.
+#include <cuda_runtime.h>
+
+#include "cart_mass.cuh"
+#include "common.cuh"
+
+namespace gvx {
+namespace {
+
+template <typename T, int LA, int LB, int COORDS>
+__global__ void __launch_bounds__(256) mass_cart_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const V4<T> x = ld4<T, LA>(a, i), y = ld4<T, LB>(b, i);
+    // FP32 legs are evaluated in FP64 (exact upcasts): a float E next to a float |p| leaves q as
+    // rounding noise of either sign, and only FP64 carries the sums of mixed sign that follow
+    const double pa[4] = {x.x, x.y, x.z, x.w}, pb[4] = {y.x, y.y, y.z, y.w};
+    st_s(m + i, (T)cart::mass(pa, pb, COORDS));
+  }
+}
+
+template <typename T, int LV, int LO, bool SHARED>
+__global__ void __launch_bounds__(256) lorentz_apply_kernel(const T *__restrict__ L, Lv v, LvOut out,
+                                                            int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  T l0[16];
+  if (SHARED) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) l0[k] = L[k];
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const V4<T> x = ld4<T, LV>(v, i);
+    T l[16];
+    if (SHARED) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) l[k] = l0[k];
+    } else if constexpr (sizeof(T) == 8) {  // 16-byte loads of the vector's own matrix
+      const double2 *q = reinterpret_cast<const double2 *>(L) + 8 * i;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const double2 t = __ldcs(q + k);
+        l[2 * k] = t.x;
+        l[2 * k + 1] = t.y;
+      }
+    } else {
+      const float4 *q = reinterpret_cast<const float4 *>(L) + 4 * i;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const float4 t = __ldcs(q + k);
+        l[4 * k] = t.x;
+        l[4 * k + 1] = t.y;
+        l[4 * k + 2] = t.z;
+        l[4 * k + 3] = t.w;
+      }
+    }
+    V4<T> o;
+    o.x = fma(l[0], x.x, fma(l[1], x.y, fma(l[2], x.z, l[3] * x.w)));
+    o.y = fma(l[4], x.x, fma(l[5], x.y, fma(l[6], x.z, l[7] * x.w)));
+    o.z = fma(l[8], x.x, fma(l[9], x.y, fma(l[10], x.z, l[11] * x.w)));
+    o.w = fma(l[12], x.x, fma(l[13], x.y, fma(l[14], x.z, l[15] * x.w)));
+    st4<T, LO>(out, i, o);
+  }
+}
+
+template <typename T, int COORDS>
+cudaError_t launch_cart_t(const Lv &a, const Lv &b, T *m, int64_t n, cudaStream_t s) {
+  const int threads = 256;
+  if (a.layout == GVX_SOA && b.layout == GVX_SOA) {
+    constexpr auto k = mass_cart_kernel<T, GVX_SOA, GVX_SOA, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  } else if (a.layout == GVX_SOA) {
+    constexpr auto k = mass_cart_kernel<T, GVX_SOA, GVX_AOS, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  } else if (b.layout == GVX_SOA) {
+    constexpr auto k = mass_cart_kernel<T, GVX_AOS, GVX_SOA, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  } else {
+    constexpr auto k = mass_cart_kernel<T, GVX_AOS, GVX_AOS, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, bool SHARED>
+cudaError_t launch_apply_t(const T *L, const Lv &v, const LvOut &out, int64_t n, cudaStream_t s) {
+  const int threads = 256;
+  if (v.layout == GVX_SOA && out.layout == GVX_SOA) {
+    constexpr auto k = lorentz_apply_kernel<T, GVX_SOA, GVX_SOA, SHARED>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(L, v, out, n);
+  } else if (v.layout == GVX_SOA) {
+    constexpr auto k = lorentz_apply_kernel<T, GVX_SOA, GVX_AOS, SHARED>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(L, v, out, n);
+  } else if (out.layout == GVX_SOA) {
+    constexpr auto k = lorentz_apply_kernel<T, GVX_AOS, GVX_SOA, SHARED>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(L, v, out, n);
+  } else {
+    constexpr auto k = lorentz_apply_kernel<T, GVX_AOS, GVX_AOS, SHARED>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(L, v, out, n);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_mass_cart(const Lv &a, const Lv &b, void *m, int64_t n, int coords, int dtype,
+                             cudaStream_t s) {
+  if (dtype == GVX_F64)
+    return coords == GVX_PXPYPZE ? launch_cart_t<double, 0>(a, b, (double *)m, n, s)
+                                 : launch_cart_t<double, 1>(a, b, (double *)m, n, s);
+  return coords == GVX_PXPYPZE ? launch_cart_t<float, 0>(a, b, (float *)m, n, s)
+                               : launch_cart_t<float, 1>(a, b, (float *)m, n, s);
+}
+
+cudaError_t launch_lorentz_apply(const void *L, int64_t l_stride, const Lv &v, const LvOut &out,
+                                 int64_t n, int dtype, cudaStream_t s) {
+  if (dtype == GVX_F64)
+    return l_stride == 0 ? launch_apply_t<double, true>((const double *)L, v, out, n, s)
+                         : launch_apply_t<double, false>((const double *)L, v, out, n, s);
+  return l_stride == 0 ? launch_apply_t<float, true>((const float *)L, v, out, n, s)
+                       : launch_apply_t<float, false>((const float *)L, v, out, n, s);
+}
+
+}  // namespace gvx

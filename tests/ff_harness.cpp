@@ -6,6 +6,7 @@
 #include "../paper_2312_02756_gb300/csrc/ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/boost_ff.cuh"
+#include "../paper_2312_02756_gb300/csrc/cart_mass.cuh"
 
 using namespace gvx::ffm;
 
@@ -107,6 +108,18 @@ int64_t ffh_boost_bwd(const double *v, const double *beta, const double *gout, i
     }
     ok[i] = f;
     c += f;
+  }
+  return c;
+}
+
+// The Cartesian pair mass (FP64): a, b (n, 4) with coords 0 (E stored) or 1 (m stored).
+int64_t ffh_mass_cart(const double *a, const double *b, int64_t n, int coords, double *m,
+                      uint8_t *ok) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    m[i] = gvx::cart::mass(a + 4 * i, b + 4 * i, coords);
+    ok[i] = 1;
+    c += 1;
   }
   return c;
 }

@@ -28,6 +28,7 @@ def ffh(tmp_path_factory):
     lib.ffh_mass_grad.restype = ctypes.c_int64
     lib.ffh_boost.restype = ctypes.c_int64
     lib.ffh_boost_bwd.restype = ctypes.c_int64
+    lib.ffh_mass_cart.restype = ctypes.c_int64
     return lib
 
 
@@ -310,3 +311,34 @@ def test_ff_boost_adjoint_against_oracle(ffh, orc):
     ffh.ffh_boost_bwd(_p(v3), _p(np.ascontiguousarray(bad_b)), _p(bad_q), ctypes.c_int64(3),
                       _p(gv), _p(gb), _p(ok))
     assert not ok.any()
+
+
+def _cart_inputs(seed, n):
+    g = syn.rng(seed)
+    a, b = syn.pxpypze(g, n), syn.pxpypze(g, n)
+    k = n // 4  # near-collinear light pairs: the cancellation the form is for
+    b[:k, :3] = a[:k, :3] * g.uniform(0.5, 2.0, (k, 1))
+    b[:k, :3] += a[:k, :3] * g.uniform(-1e-9, 1e-9, (k, 3))
+    mb = g.uniform(0, 1e-3, k)
+    b[:k, 3] = np.sqrt(np.sum(b[:k, :3] ** 2, axis=1) + mb * mb)
+    return a, b
+
+
+def test_ff_cartesian_mass_against_oracle(ffh, orc):
+    """The FP64 Cartesian pair mass (FMA-exact cross product and E^2 - |p|^2) against the
+    binary128 definition, PxPyPzE and PxPyPzM legs, including near-collinear light pairs:
+    within 1e-12 relative."""
+    for coords, code in (("pxpypze", 0), ("pxpypzm", 1)):
+        a, b = _cart_inputs(130 + code, 20000)
+        if code == 1:
+            g = syn.rng(140)
+            a[:, 3] = g.uniform(0, 10, len(a))
+            b[: len(b) // 4, 3] = g.uniform(0, 1e-3, len(b) // 4)
+        a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+        m, ok = np.empty(len(a)), np.empty(len(a), np.uint8)
+        ffh.ffh_mass_cart(_p(a), _p(b), ctypes.c_int64(len(a)), code, _p(m), _p(ok))
+        ok = ok.astype(bool)
+        ref = orc.mass_cart_def(a, b, coords)
+        assert ok.all(), coords
+        err = np.abs(m[ok] - ref[ok]) / ref[ok]
+        assert err.max() <= 1e-12, (coords, err.max())
