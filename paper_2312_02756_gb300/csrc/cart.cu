@@ -2,15 +2,19 @@
 // are templated on their coordinate system; Sec. 4.1: transformations are 4x4 matrices applied
 // to every vector of an array).
 //
-// gvx_invariant_mass_cart: pair masses of Cartesian legs, PxPyPzE or PxPyPzM, with the
-// cancellation-free form of cart_mass.cuh (an FMA-exact cross product and E^2 - |p|^2), in FP64
-// for both storage precisions.  It runs on the FP64 pipe, roots and divisions included: correct
-// first; the float-float treatment of the PtEtaPhiM kernel is the next step for it.
+// gvx_invariant_mass_cart: pair masses of Cartesian legs, PxPyPzE or PxPyPzM.  PxPyPzE pairs take
+// the exact fixed-point evaluation of cart_fixed.cuh (integer and FP32 pipes); PxPyPzM pairs, and
+// the rare PxPyPzE pairs outside its domain, the cancellation-free FP64 form of cart_mass.cuh (an
+// FMA-exact cross product and E^2 - |p|^2), on the FP64 pipe for both storage precisions.
 //
-// gvx_lorentz_apply: out = L v for a row-major 4x4 matrix L, shared or one per vector, as four
-// FMA chains per vector in the working precision.
+// gvx_lorentz_apply: out = L v for a row-major 4x4 matrix L, shared or one per vector.  One
+// shared FP64 matrix takes the float-float row sums of apply_ff.cuh; a matrix per vector (whose
+// own 128 bytes make the launch memory-bound) and FP32 take four FMA chains per vector in the
+// working precision.
 #include <cuda_runtime.h>
 
+#include "apply_ff.cuh"
+#include "cart_fixed.cuh"
 #include "cart_mass.cuh"
 #include "common.cuh"
 
@@ -22,11 +26,31 @@ __global__ void __launch_bounds__(256) mass_cart_kernel(Lv a, Lv b, T *__restric
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const V4<T> x = ld4<T, LA>(a, i), y = ld4<T, LB>(b, i);
-    // FP32 legs are evaluated in FP64 (exact upcasts): a float E next to a float |p| leaves q as
-    // rounding noise of either sign, and only FP64 carries the sums of mixed sign that follow
-    const double pa[4] = {x.x, x.y, x.z, x.w}, pb[4] = {y.x, y.y, y.z, y.w};
-    st_s(m + i, (T)cart::mass(pa, pb, COORDS));
+    T r;
+    bool fast = false;
+    if constexpr (COORDS == 0) {
+      const T ta[4] = {x.x, x.y, x.z, x.w}, tb[4] = {y.x, y.y, y.z, y.w};
+      fast = cfix::mass_pxpypze(ta, tb, &r);
+    }
+    if (!fast) {
+      // FP32 legs are evaluated in FP64 (exact upcasts): a float E next to a float |p| leaves q
+      // as rounding noise of either sign, and only FP64 carries the sums of mixed sign that follow
+      const double pa[4] = {x.x, x.y, x.z, x.w}, pb[4] = {y.x, y.y, y.z, y.w};
+      r = (T)cart::mass(pa, pb, COORDS);
+    }
+    st_s(m + i, r);
   }
+}
+
+// out = L v by four FMA chains in the working precision.
+template <typename T>
+__device__ __forceinline__ V4<T> apply_fma(const T *l, const V4<T> &x) {
+  V4<T> o;
+  o.x = fma(l[0], x.x, fma(l[1], x.y, fma(l[2], x.z, l[3] * x.w)));
+  o.y = fma(l[4], x.x, fma(l[5], x.y, fma(l[6], x.z, l[7] * x.w)));
+  o.z = fma(l[8], x.x, fma(l[9], x.y, fma(l[10], x.z, l[11] * x.w)));
+  o.w = fma(l[12], x.x, fma(l[13], x.y, fma(l[14], x.z, l[15] * x.w)));
+  return o;
 }
 
 template <typename T, int LV, int LO, bool SHARED>
@@ -37,6 +61,24 @@ __global__ void __launch_bounds__(256) lorentz_apply_kernel(const T *__restrict_
   if (SHARED) {
 #pragma unroll
     for (int k = 0; k < 16; k++) l0[k] = L[k];
+  }
+  if constexpr (SHARED && sizeof(T) == 8) {
+    // one matrix for every vector: the float-float row sums of apply_ff.cuh, FP64 FMA chains
+    // for a matrix or a vector outside their domain
+    const ffm::LorentzFF M = ffm::lorentz_ff(l0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const V4<T> x = ld4<T, LV>(v, i);
+      const double xv[4] = {x.x, x.y, x.z, x.w};
+      double o[4];
+      V4<T> r;
+      if (M.ok && ffm::apply_ff(M, xv, o)) {
+        r = {o[0], o[1], o[2], o[3]};
+      } else {
+        r = apply_fma(l0, x);
+      }
+      st4<T, LO>(out, i, r);
+    }
+    return;
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const V4<T> x = ld4<T, LV>(v, i);
@@ -63,12 +105,7 @@ __global__ void __launch_bounds__(256) lorentz_apply_kernel(const T *__restrict_
         l[4 * k + 3] = t.w;
       }
     }
-    V4<T> o;
-    o.x = fma(l[0], x.x, fma(l[1], x.y, fma(l[2], x.z, l[3] * x.w)));
-    o.y = fma(l[4], x.x, fma(l[5], x.y, fma(l[6], x.z, l[7] * x.w)));
-    o.z = fma(l[8], x.x, fma(l[9], x.y, fma(l[10], x.z, l[11] * x.w)));
-    o.w = fma(l[12], x.x, fma(l[13], x.y, fma(l[14], x.z, l[15] * x.w)));
-    st4<T, LO>(out, i, o);
+    st4<T, LO>(out, i, apply_fma(l, x));
   }
 }
 

@@ -7,6 +7,8 @@
 #include "../paper_2312_02756_gb300/csrc/mass_ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/boost_ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/cart_mass.cuh"
+#include "../paper_2312_02756_gb300/csrc/cart_fixed.cuh"
+#include "../paper_2312_02756_gb300/csrc/apply_ff.cuh"
 
 using namespace gvx::ffm;
 
@@ -120,6 +122,40 @@ int64_t ffh_mass_cart(const double *a, const double *b, int64_t n, int coords, d
     m[i] = gvx::cart::mass(a + 4 * i, b + 4 * i, coords);
     ok[i] = 1;
     c += 1;
+  }
+  return c;
+}
+
+// The fixed-point fast path of the PxPyPzE pair mass: FP64 legs (m) and the same legs rounded
+// to float (m32); ok / ok32 = inside the fast path.
+int64_t ffh_mass_cart_fixed(const double *a, const double *b, int64_t n, double *m, uint8_t *ok,
+                            float *m32, uint8_t *ok32) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    double out = NAN;
+    ok[i] = gvx::cfix::mass_pxpypze(a + 4 * i, b + 4 * i, &out);
+    m[i] = out;
+    c += ok[i];
+    float fa[4], fb[4], o32 = NAN;
+    for (int k = 0; k < 4; k++) {
+      fa[k] = (float)a[4 * i + k];
+      fb[k] = (float)b[4 * i + k];
+    }
+    ok32[i] = gvx::cfix::mass_pxpypze(fa, fb, &o32);
+    m32[i] = o32;
+  }
+  return c;
+}
+
+// The float-float Lorentz transformation with one shared matrix L (16, row-major): v, out (n, 4);
+// returns -1 when L is outside the domain, else the number of vectors taken (ok[i]).
+int64_t ffh_apply(const double *L, const double *v, int64_t n, double *out, uint8_t *ok) {
+  const LorentzFF M = lorentz_ff(L);
+  if (!M.ok) return -1;
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    ok[i] = apply_ff(M, v + 4 * i, out + 4 * i);
+    c += ok[i];
   }
   return c;
 }

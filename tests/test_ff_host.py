@@ -29,6 +29,8 @@ def ffh(tmp_path_factory):
     lib.ffh_boost.restype = ctypes.c_int64
     lib.ffh_boost_bwd.restype = ctypes.c_int64
     lib.ffh_mass_cart.restype = ctypes.c_int64
+    lib.ffh_mass_cart_fixed.restype = ctypes.c_int64
+    lib.ffh_apply.restype = ctypes.c_int64
     return lib
 
 
@@ -342,3 +344,129 @@ def test_ff_cartesian_mass_against_oracle(ffh, orc):
         assert ok.all(), coords
         err = np.abs(m[ok] - ref[ok]) / ref[ok]
         assert err.max() <= 1e-12, (coords, err.max())
+
+
+def _cart_fixed(ffh, a, b):
+    a, b = np.ascontiguousarray(a, dtype=np.float64), np.ascontiguousarray(b, dtype=np.float64)
+    n = len(a)
+    m, ok = np.empty(n), np.empty(n, np.uint8)
+    m32, ok32 = np.empty(n, np.float32), np.empty(n, np.uint8)
+    ffh.ffh_mass_cart_fixed(_p(a), _p(b), ctypes.c_int64(n), _p(m), _p(ok), _p(m32), _p(ok32))
+    return m, ok.astype(bool), m32, ok32.astype(bool)
+
+
+def test_fixed_point_pxpypze_mass_against_oracle(ffh, orc):
+    """The exact fixed-point PxPyPzE pair mass (FP64 legs) against the binary128 definition:
+    within 2^-44 relative wherever it takes the pair, and it takes every random pair; the
+    near-collinear light pairs it takes are just as accurate."""
+    g = syn.rng(150)
+    n = 40000
+    a, b = syn.pxpypze(g, n), syn.pxpypze(g, n)
+    m, ok, _, _ = _cart_fixed(ffh, a, b)
+    ref = orc.mass_cart_def(a, b, "pxpypze")
+    assert ok.all()
+    assert np.max(np.abs(m - ref) / ref) <= 2.0 ** -44
+    a, b = _cart_inputs(151, 20000)
+    m, ok, _, _ = _cart_fixed(ffh, a, b)
+    ref = orc.mass_cart_def(a, b, "pxpypze")
+    assert ok[len(a) // 4:].all()  # the unrelated pairs
+    assert np.max(np.abs(m[ok] - ref[ok]) / np.abs(ref[ok])) <= 2.0 ** -44
+
+
+def test_fixed_point_pxpypze_mass_threshold_and_edges(ffh, orc):
+    """Pairs are taken exactly when |m^2| >= 2^-38 of the squared scale (the power of two
+    2^(2 sc) with the largest component in [2^sc, 2^(sc+1))), so a zero or vanishing mass goes
+    to the FP64 form; a spacelike sum gives -sqrt(-m^2); a component 2^-100 below the others is
+    kept to the fixed-point resolution; non-finite or far out-of-range inputs are refused."""
+    E = 1.5  # scale exponent 0
+    rows = []
+    for r in (2.0 ** -18.9, 2.0 ** -19.1, 2.0 ** -10, 0.5):  # m / 2^sc around the 2^-19 edge
+        rows.append(([0.0, 0.0, 1.0, np.hypot(1.0, r / 2)], [0.0, 0.0, 1.0, np.hypot(1.0, r / 2)]))
+    rows.append(([0.0, 0.0, E, E], [0.0, 0.0, E, E]))                 # massless, collinear: 0
+    rows.append(([1.0, 0.0, 0.0, 0.1], [1.0, 0.0, 0.0, 0.1]))         # spacelike sum
+    rows.append(([1e-30, 2.0, -1.0, 3.0], [0.5, -1e-300, 0.25, 1.25]))  # tiny components
+    rows.append(([np.inf, 0.0, 0.0, 1.0], [0.0, 0.0, 0.0, 1.0]))
+    rows.append(([0.0, 0.0, 0.0, 1e300], [0.0, 0.0, 0.0, 1e300]))
+    rows.append(([0.0, 0.0, 0.0, 1e-300], [0.0, 0.0, 0.0, 1e-300]))
+    a = np.array([r[0] for r in rows])
+    b = np.array([r[1] for r in rows])
+    m, ok, _, _ = _cart_fixed(ffh, a, b)
+    ref = orc.mass_cart_def(a, b, "pxpypze")
+    # E = sqrt(1 + r^2/4) in [1, 2): scale exponent 0 and m^2 = 4 (E^2 - 1) = r^2, so the
+    # threshold 2^-38 falls at r = 2^-19
+    assert ok[:4].tolist() == [True, False, True, True]
+    assert not ok[4]
+    assert ok[5] and m[5] < 0
+    assert ok[6]
+    assert not ok[7:].any()
+    sel = ok & np.isfinite(ref)
+    assert np.all(np.abs(m[sel] - ref[sel]) <= 2.0 ** -44 * np.abs(ref[sel]))
+
+
+def test_fixed_point_pxpypze_mass_f32(ffh, orc):
+    """FP32 legs through the same fixed-point path, rounded once to float: within one rounding
+    of the binary128 mass of the float inputs."""
+    g = syn.rng(152)
+    a, b = syn.to_f32(syn.pxpypze(g, 40000)), syn.to_f32(syn.pxpypze(g, 40000))
+    _, _, m32, ok32 = _cart_fixed(ffh, a.astype(np.float64), b.astype(np.float64))
+    ref = orc.mass_cart_def(a.astype(np.float64), b.astype(np.float64), "pxpypze")
+    assert ok32.all()
+    assert np.max(np.abs(m32.astype(np.float64) - ref) / np.abs(ref)) <= 2.0 ** -24 * 1.01
+
+
+def _apply(ffh, L, v):
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out, ok = np.full(v.shape, np.nan), np.zeros(len(v), np.uint8)
+    c = ffh.ffh_apply(_p(L), _p(v), ctypes.c_int64(len(v)), _p(out), _p(ok))
+    return c, out, ok.astype(bool)
+
+
+def _apply_bound(L, v):
+    """2^-42 sum_j |L_ij v_j| + 2^-70 max_j |L_ij| max_j |v_j|, per component."""
+    Lf = np.broadcast_to(L, (len(v), 4, 4))
+    s = np.einsum("nrk,nk->nr", np.abs(Lf), np.abs(v))
+    floor = np.max(np.abs(Lf), axis=2) * np.max(np.abs(v), axis=1)[:, None]
+    return 2.0 ** -42 * s + 2.0 ** -70 * floor
+
+
+def test_ff_lorentz_apply_against_oracle(ffh, orc):
+    """The float-float shared-matrix transformation against the binary128 product, for a dense
+    random matrix, a large boost (gamma ~ 700: rows that cancel) and a rotation whose entries
+    include the FP64 remnants of cos(pi/2): within the stated bound, every vector taken."""
+    g = syn.rng(160)
+    v = syn.pxpypze(g, 20000)
+    v[:100, 0] = 1e-30  # a component far below the others
+    mats = [g.uniform(-2, 2, (4, 4)), orc.boost_matrix_def(np.array([0.6, -0.5, np.sqrt(0.389998)]))]
+    c, s = np.cos(np.pi / 2), np.sin(np.pi / 2)
+    R = np.eye(4)
+    R[:2, :2] = [[c, -s], [s, c]]
+    mats.append(R)
+    for L in mats:
+        cnt, out, ok = _apply(ffh, L, v)
+        assert cnt == len(v) and ok.all()
+        ref = orc.lorentz_apply_def(L, v)
+        assert np.all(np.abs(out - ref) <= _apply_bound(L, v)), np.max(np.abs(out - ref) / _apply_bound(L, v))
+
+
+def test_ff_lorentz_apply_domain(ffh, orc):
+    """Zero rows are exact; a matrix with a non-finite entry, a row of denormals alone or a
+    row scale beyond 2^400 is refused as a whole; a vector that is all zero, non-finite or
+    scaled beyond 2^400 is refused alone."""
+    g = syn.rng(161)
+    L = g.uniform(-2, 2, (4, 4))
+    L[2] = 0.0
+    v = syn.pxpypze(g, 8)
+    v[1] = 0.0
+    v[2, 3] = np.inf
+    v[3] *= 2.0 ** 420
+    v[4] *= 2.0 ** -420
+    cnt, out, ok = _apply(ffh, L, v)
+    assert ok.tolist() == [True, False, False, False, False, True, True, True]
+    assert np.all(out[ok][:, 2] == 0.0)
+    ref = orc.lorentz_apply_def(L, v[ok])
+    assert np.all(np.abs(out[ok] - ref) <= _apply_bound(L, v[ok]))
+    for bad in (np.inf, 5e-324, 2.0 ** 410):
+        L2 = L.copy()
+        L2[1] = [bad, 0.0, 0.0, 0.0]
+        assert _apply(ffh, L2, v)[0] == -1

@@ -1,10 +1,11 @@
 """GPU parity of the Cartesian-input pair mass (gvx_invariant_mass_cart) and of the general
 Lorentz transformation (gvx_lorentz_apply) against the binary128 oracle.
 
-Cartesian mass, FP64: 1e-12 relative (the cancellation-free form with an FMA-exact cross product
-and E^2 - |p|^2).  FP32 legs are evaluated in FP64 and rounded once: within one float ulp of the
-oracle on the exact upcast inputs.  Lorentz apply: each component within a few ulps of sum_k |L_rk v_k|
-(no structure of L is assumed: 4 u for FP64, 4 u for FP32 with u the unit roundoff).
+Cartesian mass, FP64: 1e-12 relative (PxPyPzE pairs through the exact fixed-point evaluation,
+the others through the cancellation-free FP64 form).  FP32 legs: within one rounding of the
+oracle on the exact upcast inputs.  Lorentz apply: each component within 4 u sum_k |L_rk v_k|
+(u the unit roundoff) for the FMA chains (FP32, a matrix per vector), and within
+2^-42 sum_k |L_rk v_k| + 2^-70 max_k |L_rk| max_k |v_k| for one shared FP64 matrix (float-float).
 """
 import numpy as np
 import pytest
@@ -101,9 +102,40 @@ def test_lorentz_apply(orc, dtype, u, shared):
         out = gvx.lorentz_apply(torch.as_tensor(L, dtype=tdt).cuda(), dev(v, layout, tdt), layout=layout)
         got = host(out, layout).astype(np.float64)
         ref = orc.lorentz_apply_def(L, v)
-        Lf = np.broadcast_to(L, (n, 4, 4))
-        scale = np.einsum("nrk,nk->nr", np.abs(Lf), np.abs(v))
-        assert np.all(np.abs(got - ref) <= 4 * u * scale + 1e-300), (dtype, shared, layout)
+        assert np.all(np.abs(got - ref) <= _apply_bound(L, v, dtype == "f64" and shared, u)), \
+            (dtype, shared, layout)
+
+
+def _apply_bound(L, v, ff, u=2.0 ** -53):
+    Lf = np.broadcast_to(L, (len(v), 4, 4))
+    scale = np.einsum("nrk,nk->nr", np.abs(Lf), np.abs(v))
+    if not ff:
+        return 4 * u * scale + 1e-300
+    floor = np.max(np.abs(Lf), axis=2) * np.max(np.abs(v), axis=1)[:, None]
+    return 2.0 ** -42 * scale + 2.0 ** -70 * floor
+
+
+def test_lorentz_apply_f64_shared_domain(orc):
+    """Vectors outside the float-float domain (all zero, scaled beyond 2^400 either way) and a
+    matrix outside it (a row of denormals alone) take the FP64 FMA chains: every component
+    within the bound either way, zero rows exact."""
+    import paper_2312_02756_gb300 as gvx
+    torch = torch_cuda()
+    g = syn.rng(85)
+    v = syn.pxpypze(g, 4096)
+    v[::7] = 0.0
+    v[1::7] *= 2.0 ** 420
+    v[2::7] *= 2.0 ** -420
+    v[3::7, 0] = 1e-30
+    L = g.uniform(-2, 2, (4, 4))
+    L[2] = 0.0
+    L_den = L.copy()
+    L_den[1] = [5e-324, 0.0, -1e-310, 0.0]
+    for M in (L, L_den):
+        out = gvx.lorentz_apply(torch.as_tensor(M).cuda(), dev(v)).cpu().numpy()
+        ref = orc.lorentz_apply_def(M, v)
+        assert np.all(np.abs(out - ref) <= _apply_bound(M, v, True))
+        assert np.all(out[:, 2] == 0.0)
 
 
 def test_lorentz_apply_boost_matrix_matches_boost(orc):
