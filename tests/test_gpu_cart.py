@@ -140,8 +140,8 @@ def test_lorentz_apply_f64_shared_domain(orc):
 
 
 def test_lorentz_apply_boost_matrix_matches_boost(orc):
-    """A boost matrix applied as a general transformation agrees with gvx_boost within the
-    general transformation's bound."""
+    """A boost matrix applied as a general transformation agrees with gvx_boost within the sum
+    of the two kernels' bounds."""
     import paper_2312_02756_gb300 as gvx
     torch = torch_cuda()
     g = syn.rng(84)
@@ -151,4 +151,5 @@ def test_lorentz_apply_boost_matrix_matches_boost(orc):
     out = gvx.lorentz_apply(torch.as_tensor(L).cuda(), dev(v)).cpu().numpy()
     ref = gvx.boost(dev(v), torch.as_tensor(beta).cuda()).cpu().numpy()
     scale = np.abs(v) @ np.abs(L).T
-    assert np.all(np.abs(out - ref) <= 1e-14 * scale)
+    # the transformation's float-float bound plus the boost's own (normwise on E')
+    assert np.all(np.abs(out - ref) <= 2.0 ** -42 * (scale + scale[:, 3:4]))
