@@ -518,11 +518,11 @@ def run_gvx(args):
     if not hbm:
         roofline["peak"] = 6800.0
         roofline["frac"] = achieved / 6800.0
-    traffic = _profile_traffic(dom)
+    traffic = _profile_traffic(dom, N_FULL)
     if traffic is not None:
         roofline["traffic"] = traffic
     issue = issue_roofline(dom, kern[dom]["ms"], clk.get("sm_mhz") if isinstance(clk, dict) else None,
-                           props.multi_processor_count)
+                           props.multi_processor_count, N_FULL)
     if issue is not None:
         roofline["issue"] = issue
     line = {
@@ -602,13 +602,18 @@ def _profile_entry(kernel):
     return entry
 
 
-def _profile_traffic(kernel):
-    """DRAM bytes per launch of `kernel` (see _profile_entry)."""
+PROFILE_N = 1 << 26  # the element count the committed per-launch figures are given for
+
+
+def _profile_traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` at n elements (see _profile_entry), scaled from the
+    committed figure by the element count (every element is read once)."""
     entry = _profile_entry(kernel)
-    return entry.get("bytes_per_launch") if entry else None
+    b = entry.get("bytes_per_launch") if entry else None
+    return None if b is None else b * n / PROFILE_N
 
 
-def issue_roofline(kernel, ms, sm_mhz, n_sms):
+def issue_roofline(kernel, ms, sm_mhz, n_sms, n):
     """The instruction-issue view of a kernel bound by issue rather than by DRAM: warp
     instructions per launch (ncu, scaled like the traffic) over the launch time, against the
     issue peak of the GPU -- four warp instructions per SM per clock at the sampled SM clock."""
@@ -616,6 +621,7 @@ def issue_roofline(kernel, ms, sm_mhz, n_sms):
     inst = entry.get("warp_inst_per_launch") if entry else None
     if inst is None or not sm_mhz or not n_sms:
         return None
+    inst = inst * n / PROFILE_N
     achieved = inst / (ms * 1e-3)
     peak = 4.0 * n_sms * sm_mhz * 1e6
     return {"bound": "issue", "unit": "warp instructions/s", "achieved": achieved, "peak": peak,

@@ -72,8 +72,9 @@ GVX_HD ff dot4_ff(const ff *l, const ff *x) {
   return {s, e};
 }
 
-// out = L v for one vector; false (out untouched) outside the domain.
-GVX_HD bool apply_ff(const LorentzFF &M, const double *v, double *out) {
+// out = L v for one vector, with the scaled ff matrix l (row-major) and its row scale exponents
+// r from lorentz_ff; false (out untouched) outside the domain.
+GVX_HD bool apply_ff(const ff *l, const int *r, const double *v, double *out) {
   int emax = 0;
 #pragma unroll
   for (int j = 0; j < 4; j++) {
@@ -86,7 +87,7 @@ GVX_HD bool apply_ff(const LorentzFF &M, const double *v, double *out) {
 #pragma unroll
   for (int j = 0; j < 4; j++) x[j] = from_double_ranged(v[j], s);
 #pragma unroll
-  for (int i = 0; i < 4; i++) out[i] = to_double(dot4_ff(M.l + 4 * i, x), M.r[i] + s);
+  for (int i = 0; i < 4; i++) out[i] = to_double(dot4_ff(l + 4 * i, x), r[i] + s);
   return true;
 }
 

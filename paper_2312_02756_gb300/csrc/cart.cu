@@ -63,15 +63,26 @@ __global__ void __launch_bounds__(256) lorentz_apply_kernel(const T *__restrict_
     for (int k = 0; k < 16; k++) l0[k] = L[k];
   }
   if constexpr (SHARED && sizeof(T) == 8) {
-    // one matrix for every vector: the float-float row sums of apply_ff.cuh, FP64 FMA chains
-    // for a matrix or a vector outside their domain
-    const ffm::LorentzFF M = ffm::lorentz_ff(l0);
+    // one matrix for every vector: the float-float row sums of apply_ff.cuh (the scaled matrix
+    // in shared memory, read by broadcast), FP64 FMA chains for a matrix or a vector outside
+    // their domain
+    __shared__ ffm::ff s_l[16];
+    __shared__ int s_r[4];
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+      const ffm::LorentzFF M = ffm::lorentz_ff(l0);
+      for (int k = 0; k < 16; k++) s_l[k] = M.l[k];
+      for (int k = 0; k < 4; k++) s_r[k] = M.r[k];
+      s_ok = M.ok;
+    }
+    __syncthreads();
+    const bool ok = s_ok != 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
       const V4<T> x = ld4<T, LV>(v, i);
       const double xv[4] = {x.x, x.y, x.z, x.w};
       double o[4];
       V4<T> r;
-      if (M.ok && ffm::apply_ff(M, xv, o)) {
+      if (ok && ffm::apply_ff(s_l, s_r, xv, o)) {
         r = {o[0], o[1], o[2], o[3]};
       } else {
         r = apply_fma(l0, x);

@@ -3,15 +3,15 @@
 //
 // The plain definition m^2 = (E1 + E2)^2 - (px1 + px2)^2 - (py1 + py2)^2 - (pz1 + pz2)^2 cancels
 // catastrophically in floating point for light, collinear pairs.  Here the eight components are
-// scaled by the power of two 2^-s that brings the largest magnitude into [1, 2) and truncated to
-// signed integers in units of 2^-90 (magnitudes below 2^91), so the four component sums are
-// exact.  Each sum is squared with 64-bit limb products and kept, truncated, in units of 2^-116;
-// the signed total fits a 128-bit integer.  The only errors are the two truncations: in scaled
-// units |error of m^2| < 4 (2 * 2 * 2 * 2^-90 + 2^-116) < 2^-84.  The result is kept when
-// |m^2| >= 2^-38 (scaled), i.e. with relative error below 2^-46; it is rounded to float-float (47
-// bits), its square root taken in float-float, and scaled back: the relative error of m is
-// below 2^-44.  Integer and FP32 pipes only, plus one FP64 add for the final rounding (none for
-// FP32 output).
+// scaled by the power of two 2^-sc that brings the largest magnitude into [1, 2) and truncated to
+// integers in units of 2^-83 (magnitudes below 2^84, three 32-bit words), so the four component
+// sums are exact.  Each sum is squared from 32-bit limb products (IMADs) and kept, truncated, in
+// units of 2^-102; the signed total fits a 128-bit integer.  The only errors are the
+// truncations: in scaled units |error of m^2| < 4 (2 * 4 * 2^-82 + 3 * 2^-102) < 2^-76.9.  The
+// result is kept when |m^2| >= 2^-31 (scaled), i.e. with relative error below 2^-45.9; it is then
+// rounded to float-float (47 bits), its square root taken in float-float, and scaled back: the
+// relative error of m is below 2^-44.  Integer and FP32 pipes only, plus one FP64 add for the
+// final rounding (none for FP32 output).
 //
 // Outside the fast path (a non-finite component, a scale exponent outside [-900, 900] for double
 // or [-100, 100] for float input, or |m^2| below the threshold, zero included) the functions
@@ -27,15 +27,15 @@ using ffm::ff;
 typedef unsigned __int128 u128;
 typedef __int128 i128;
 
-constexpr int kFrac = 90;                // input units: 2^-90 of the scale
-constexpr int kM2Units = 2 * kFrac - 64;  // m^2 units: 2^-116
-constexpr int kMinLead = kM2Units - 38;   // |m^2| >= 2^-38: leading bit at or above 78
+constexpr int kFrac = 83;                 // input units: 2^-83 of the scale
+constexpr int kM2Units = 2 * kFrac - 64;   // m^2 units: 2^-102
+constexpr int kMinLead = kM2Units - 31;    // |m^2| >= 2^-31: leading bit at or above 71
 
-GVX_HD uint64_t mul64hi(uint64_t a, uint64_t b) {
+GVX_HD uint32_t mul32hi(uint32_t a, uint32_t b) {
 #if defined(__CUDA_ARCH__)
-  return __umul64hi(a, b);
+  return __umulhi(a, b);
 #else
-  return (uint64_t)(((u128)a * b) >> 64);
+  return (uint32_t)(((uint64_t)a * b) >> 32);
 #endif
 }
 
@@ -79,33 +79,36 @@ struct Fmt<float> {
   static constexpr int kSig = 23, kBias = 127, kMaxE = 0xff, kScaleLim = 100;
 };
 
-// x * 2^(kFrac - sc), truncated toward zero, for the largest biased exponent emax of the pair
-// (sc = emax - bias, so |x| 2^-sc < 2).  x = sig * 2^(e - bias - kSig), hence the shift
-// k = e - emax + kFrac - kSig <= kFrac - kSig.
+// |x| * 2^(kFrac - sc), truncated, for the largest biased exponent emax of the pair (sc = emax -
+// bias, so |x| 2^-sc < 2): x = sig * 2^(e - bias - kSig), so the significand moves left by
+// k = e - emax + kFrac - kSig (at most 31 for double, 60 for float) or right by -k.
 template <typename T>
-GVX_HD i128 to_fixed(const Decoded &d, int emax) {
-  const int k = d.e - emax + kFrac - Fmt<T>::kSig;
-  u128 v;
-  if (d.e == 0 || k <= -(Fmt<T>::kSig + 1)) {
-    v = 0;
-  } else if (k >= 0) {
-    v = (u128)d.sig << k;
-  } else {
-    v = (u128)(d.sig >> -k);
+GVX_HD u128 align(const Decoded &d, int emax) {
+  const int k = d.e == 0 ? -64 : d.e - emax + kFrac - Fmt<T>::kSig;
+  if (k < 0) return (u128)(k > -64 ? d.sig >> -k : 0);
+  if (sizeof(T) == 8) {  // k <= 31: the low 64 bits and the top word separately
+    const uint32_t top = k ? (uint32_t)(d.sig >> 32) >> (32 - k) : 0u;
+    return ((u128)top << 64) | (uint64_t)(d.sig << k);
   }
-  return d.neg ? -(i128)v : (i128)v;
+  return (u128)d.sig << k;  // float: a 24-bit significand, k <= 60
 }
 
-// floor(S^2 / 2^64) for |S| < 2^92: with |S| = h 2^64 + l (h < 2^28),
-// S^2 / 2^64 = h^2 2^64 + 2 h l + l^2 / 2^64.
-GVX_HD u128 square_shift64(i128 S) {
-  const u128 U = S < 0 ? (u128)(-S) : (u128)S;
-  const uint32_t h = (uint32_t)(U >> 64);
-  const uint64_t l = (uint64_t)U;
-  return ((u128)((uint64_t)h * h) << 64) + (mul32x64(h, l) << 1) + mul64hi(l, l);
+// |a +- b| for magnitudes a, b < 2^84 with signs na, nb: their sum or their difference.
+GVX_HD u128 abs_sum(u128 a, bool na, u128 b, bool nb) {
+  if (na == nb) return a + b;
+  return a >= b ? a - b : b - a;
 }
 
-// The scaled m^2 (units 2^-116) of two PxPyPzE legs and the scale exponent sc; false when a
+// floor-ish(U^2 / 2^64) for U < 2^85, within 3 units: with U = h 2^64 + l1 2^32 + l0,
+// U^2 / 2^64 = h^2 2^64 + 2 h (l1 2^32 + l0) + l1^2 + 2 l1 l0 / 2^32 + l0^2 / 2^64, the last term
+// dropped and the one before it truncated.
+GVX_HD u128 square_shift64(u128 U) {
+  const uint32_t h = (uint32_t)(U >> 64), l1 = (uint32_t)((uint64_t)U >> 32), l0 = (uint32_t)U;
+  return ((u128)((uint64_t)h * h) << 64) + mul32x64(2u * h, (uint64_t)U) +
+         ((uint64_t)l1 * l1 + 2ull * mul32hi(l1, l0));
+}
+
+// The scaled m^2 (units 2^-102) of two PxPyPzE legs and the scale exponent sc; false when a
 // component is not finite or sc is out of range.
 template <typename T>
 GVX_HD bool m2_fixed(const T *a, const T *b, i128 *m2, int *sc) {
@@ -120,26 +123,27 @@ GVX_HD bool m2_fixed(const T *a, const T *b, i128 *m2, int *sc) {
   for (int k = 0; k < 8; k++) emax = d[k].e > emax ? d[k].e : emax;
   const int s = emax - Fmt<T>::kBias;
   if (emax == Fmt<T>::kMaxE || s < -Fmt<T>::kScaleLim || s > Fmt<T>::kScaleLim) return false;
-  i128 acc = 0;
+  u128 pos = 0, neg = 0;
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    const i128 S = to_fixed<T>(d[k], emax) + to_fixed<T>(d[k + 4], emax);
-    const u128 q = square_shift64(S);
-    acc = k == 3 ? acc + (i128)q : acc - (i128)q;  // components 0..2 are p, 3 is E
+    const u128 q = square_shift64(
+        abs_sum(align<T>(d[k], emax), d[k].neg, align<T>(d[k + 4], emax), d[k + 4].neg));
+    if (k == 3) pos = q;  // components 0..2 are p, 3 is E
+    else neg += q;
   }
-  *m2 = acc;
+  *m2 = (i128)pos - (i128)neg;
   *sc = s;
   return true;
 }
 
-// |q| * 2^-116 as ff, truncated to 47 bits, for q with its leading bit p in [78, 121].
+// |q| * 2^-102 as ff, truncated to 47 bits, for q with its leading bit p in [71, 107].
 GVX_HD ff fixed_to_ff(u128 q, int p) {
   const uint64_t t = (uint64_t)(q >> (p - 46));  // 47 bits, leading 1 at bit 46
   const uint32_t top = (uint32_t)(t >> 23);       // leading 1 at bit 23 (implicit in hi)
   const uint32_t rest = (uint32_t)t & 0x7fffffu;
-  const uint32_t eh = (uint32_t)(p - kM2Units + 127);  // biased exponent of hi: 2^(p - 116)
+  const uint32_t eh = (uint32_t)(p - kM2Units + 127);  // biased exponent of hi: 2^(p - 102)
   const float hi = ffm::u2f((eh << 23) | (top & 0x7fffffu));
-  const uint32_t base = (eh - 23u) << 23;  // 2^(p - 139): the rest has weight 2^(p - 162)
+  const uint32_t base = (eh - 23u) << 23;  // 2^(p - 125): the rest has weight 2^(p - 148)
   return {hi, ffm::fsub(ffm::u2f(base | rest), ffm::u2f(base))};
 }
 
@@ -172,7 +176,7 @@ GVX_HD bool mass_pxpypze(const double *a, const double *b, double *out) {
 }
 
 // The same for FP32 legs, rounded once to float (hi + lo in one float add, then an exact
-// power-of-two scaling: the scaled mass lies in [2^-19, 2^3) and |sc| <= 100).
+// power-of-two scaling: the scaled mass lies in [2^-16, 2^3) and |sc| <= 100).
 GVX_HD bool mass_pxpypze(const float *a, const float *b, float *out) {
   i128 m2;
   int sc;

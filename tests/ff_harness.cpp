@@ -154,7 +154,7 @@ int64_t ffh_apply(const double *L, const double *v, int64_t n, double *out, uint
   if (!M.ok) return -1;
   int64_t c = 0;
   for (int64_t i = 0; i < n; i++) {
-    ok[i] = apply_ff(M, v + 4 * i, out + 4 * i);
+    ok[i] = apply_ff(M.l, M.r, v + 4 * i, out + 4 * i);
     c += ok[i];
   }
   return c;

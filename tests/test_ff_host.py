@@ -374,13 +374,13 @@ def test_fixed_point_pxpypze_mass_against_oracle(ffh, orc):
 
 
 def test_fixed_point_pxpypze_mass_threshold_and_edges(ffh, orc):
-    """Pairs are taken exactly when |m^2| >= 2^-38 of the squared scale (the power of two
+    """Pairs are taken exactly when |m^2| >= 2^-31 of the squared scale (the power of two
     2^(2 sc) with the largest component in [2^sc, 2^(sc+1))), so a zero or vanishing mass goes
     to the FP64 form; a spacelike sum gives -sqrt(-m^2); a component 2^-100 below the others is
-    kept to the fixed-point resolution; non-finite or far out-of-range inputs are refused."""
+    dropped below the fixed-point resolution; non-finite or far out-of-range inputs are refused."""
     E = 1.5  # scale exponent 0
     rows = []
-    for r in (2.0 ** -18.9, 2.0 ** -19.1, 2.0 ** -10, 0.5):  # m / 2^sc around the 2^-19 edge
+    for r in (2.0 ** -15.4, 2.0 ** -15.6, 2.0 ** -10, 0.5):  # m / 2^sc around the 2^-15.5 edge
         rows.append(([0.0, 0.0, 1.0, np.hypot(1.0, r / 2)], [0.0, 0.0, 1.0, np.hypot(1.0, r / 2)]))
     rows.append(([0.0, 0.0, E, E], [0.0, 0.0, E, E]))                 # massless, collinear: 0
     rows.append(([1.0, 0.0, 0.0, 0.1], [1.0, 0.0, 0.0, 0.1]))         # spacelike sum
@@ -393,7 +393,7 @@ def test_fixed_point_pxpypze_mass_threshold_and_edges(ffh, orc):
     m, ok, _, _ = _cart_fixed(ffh, a, b)
     ref = orc.mass_cart_def(a, b, "pxpypze")
     # E = sqrt(1 + r^2/4) in [1, 2): scale exponent 0 and m^2 = 4 (E^2 - 1) = r^2, so the
-    # threshold 2^-38 falls at r = 2^-19
+    # threshold 2^-31 falls at r = 2^-15.5
     assert ok[:4].tolist() == [True, False, True, True]
     assert not ok[4]
     assert ok[5] and m[5] < 0
