@@ -11,7 +11,8 @@
 //   * the four products of a row are formed by TwoProduct with the cross terms of the low parts,
 //     their high parts added by TwoSum, and the low parts and the TwoSum errors collected in
 //     one float;
-//   * the result, hi + lo scaled by 2^(r_i + s), is rounded to double by one FP64 add.
+//   * the result, hi + lo scaled by 2^(r_i + s), is rounded to double by one FP64 add (each
+//     float moved into a double exactly by integer operations).
 // Error of each component: below 2^-42 sum_j |L_ij v_j| + 2^-70 max_j |L_ij| max_j |v_j| (the
 // second term covers what the conversions flush to zero).
 //
@@ -56,6 +57,15 @@ GVX_HD LorentzFF lorentz_ff(const double *L) {
   return M;
 }
 
+// f * 2^(shift) as a double, exactly, for k = (896 + shift) << 20 and a float f that is 0 or
+// normal: the float's exponent and fraction move into the double's fields by one add on the
+// high word.  A denormal f counts as 0.
+GVX_HD double f2d_rebias(float f, uint32_t k) {
+  const uint32_t u = f2u(f);
+  if ((u & 0x7f800000u) == 0u) return 0.0;
+  return hilo2d((((u & 0x7fffffffu) >> 3) + k) | (u & 0x80000000u), u << 29);
+}
+
 // sum_j l[j] x[j] for ff l, x: the high parts' products by TwoProduct and TwoSum, everything
 // else collected in one float.  Returned unnormalized (the caller rounds hi + lo once).
 GVX_HD ff dot4_ff(const ff *l, const ff *x) {
@@ -87,7 +97,11 @@ GVX_HD bool apply_ff(const ff *l, const int *r, const double *v, double *out) {
 #pragma unroll
   for (int j = 0; j < 4; j++) x[j] = from_double_ranged(v[j], s);
 #pragma unroll
-  for (int i = 0; i < 4; i++) out[i] = to_double(dot4_ff(l + 4 * i, x), r[i] + s);
+  for (int i = 0; i < 4; i++) {
+    const ff y = dot4_ff(l + 4 * i, x);
+    const uint32_t k = (uint32_t)(896 + r[i] + s) << 20;  // float -> double exponent rebias
+    out[i] = f2d_rebias(y.hi, k) + f2d_rebias(y.lo, k);
+  }
   return true;
 }
 

@@ -54,7 +54,7 @@ __device__ __forceinline__ V4<T> apply_fma(const T *l, const V4<T> &x) {
 }
 
 template <typename T, int LV, int LO, bool SHARED>
-__global__ void __launch_bounds__(256) lorentz_apply_kernel(const T *__restrict__ L, Lv v, LvOut out,
+__global__ void __launch_bounds__(256, 4) lorentz_apply_kernel(const T *__restrict__ L, Lv v, LvOut out,
                                                             int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   T l0[16];
@@ -77,8 +77,13 @@ __global__ void __launch_bounds__(256) lorentz_apply_kernel(const T *__restrict_
     }
     __syncthreads();
     const bool ok = s_ok != 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-      const V4<T> x = ld4<T, LV>(v, i);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    V4<T> xn = {0, 0, 0, 0};
+    if (i < n) xn = ld4<T, LV>(v, i);
+    for (; i < n; i += stride) {
+      // the next vector's loads go out before this one's arithmetic: two vectors in flight
+      const V4<T> x = xn;
+      if (i + stride < n) xn = ld4<T, LV>(v, i + stride);
       const double xv[4] = {x.x, x.y, x.z, x.w};
       double o[4];
       V4<T> r;
