@@ -357,7 +357,7 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
         out["workload"] = "N = 2^24 pairs / vectors, SoA, upstream gradients uniform in [-1, 1]"
         res["fwd_bwd"] = out
     if "coords" in which:
-        # other coordinate systems: FP64 pair masses of 2^26 Cartesian pairs (E stored) and a
+        # other coordinate systems: FP64 pair masses of 2^26 Cartesian pairs (E, then m stored) and a
         # general Lorentz transformation (one shared 4x4 matrix) of 2^26 PxPyPzE vectors
         g = syn.rng(5)
         a = torch.as_tensor(syn.pxpypze(g, N_FULL).T.copy()).cuda()
@@ -366,6 +366,12 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
         la, lb = Step._lv(a, 0, 4), Step._lv(b, 0, 4)
         t_c = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass_cart(
             r(la), r(lb), P(m.data_ptr()), N_FULL, 1, 0, s)), stream, steps, warmup)
+        # the same legs with the fourth component read as a mass in [0, 10] (PxPyPzM)
+        gm = syn.rng(6)
+        a[3] = torch.as_tensor(gm.uniform(0.0, 10.0, N_FULL)).cuda()
+        b[3] = torch.as_tensor(gm.uniform(0.0, 10.0, N_FULL)).cuda()
+        t_cm = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass_cart(
+            r(la), r(lb), P(m.data_ptr()), N_FULL, 2, 0, s)), stream, steps, warmup)
         L = torch.as_tensor(np.array([[1.2, 0.1, 0.0, 0.5], [0.1, 1.1, 0.2, 0.0],
                                       [0.0, 0.2, 1.3, 0.4], [0.5, 0.0, 0.4, 1.5]])).cuda()
         o = torch.empty_like(a)
@@ -375,10 +381,13 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
         del a, b, m, o, L
         torch.cuda.empty_cache()
         res["coords"] = {
-            "workload": "FP64, 2^26 elements, SoA: pair masses of PxPyPzE legs; a shared 4x4 "
-                        "Lorentz transformation of PxPyPzE vectors",
+            "workload": "FP64, 2^26 elements, SoA: pair masses of PxPyPzE legs and of PxPyPzM "
+                        "legs (masses in [0, 10]); a shared 4x4 Lorentz transformation of "
+                        "PxPyPzE vectors",
             "mass_pxpypze_ms": t_c, "mass_pxpypze_pairs_per_s": N_FULL / (t_c * 1e-3),
             "mass_pxpypze_GBps": 72 * N_FULL / (t_c * 1e-3) / 1e9,
+            "mass_pxpypzm_ms": t_cm, "mass_pxpypzm_pairs_per_s": N_FULL / (t_cm * 1e-3),
+            "mass_pxpypzm_GBps": 72 * N_FULL / (t_cm * 1e-3) / 1e9,
             "lorentz_apply_ms": t_l, "lorentz_apply_vectors_per_s": N_FULL / (t_l * 1e-3),
             "lorentz_apply_GBps": 64 * N_FULL / (t_l * 1e-3) / 1e9,
         }

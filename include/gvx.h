@@ -125,11 +125,16 @@ gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, g
  * Pair masses of Cartesian legs: m[i] = mass(a[i] + b[i]) for coords GVX_PXPYPZE (components
  * px, py, pz, E) or GVX_PXPYPZM (px, py, pz, m; E = sqrt(|p|^2 + m^2)) -- the invariant mass of
  * Sec. 4.1 on the other 4-D coordinate systems of Sec. 3.1.  A spacelike sum gives -sqrt of
- * |E^2 - |P|^2| (GenVector's convention).  FP64: within 1e-12 relative of the definition for
- * legs with E^2 >= |p|^2 (the cancellation-free form with an exact cross product and an exact
- * E^2 - |p|^2); FP32 legs are evaluated the same way in FP64 and rounded once (a float E next to
- * a float |p| leaves E^2 - |p|^2 as rounding noise of either sign).  Layouts
- * and alignment as gvx_invariant_mass; coords GVX_PTETAPHIM is gvx_invariant_mass itself.
+ * |E^2 - |P|^2| (GenVector's convention).  PxPyPzE: the definition evaluated exactly in
+ * fixed-point integers (every component truncated to 2^-83 of the pair's largest), within 2^-44
+ * relative; PxPyPzM: p1 x p2, p1.p2, |p_i|^2 and m_i^2 in fixed point at each leg's own scale and
+ * the cancellation-free combination m1^2 + m2^2 + 2 (E1 E2 - p1.p2) in float-float, within 2^-43
+ * relative.  Pairs whose |m^2| falls below 2^-31 of the larger leg's squared scale (a power of
+ * two within 2x of its largest component), or outside the fixed-point range, take a
+ * cancellation-free FP64 form (an FMA-exact cross product and E^2 - |p|^2): within 1e-12
+ * relative for legs with E^2 >= |p|^2.  FP32 legs go through the same evaluations and are rounded
+ * once.  Layouts and alignment as gvx_invariant_mass; coords GVX_PTETAPHIM is
+ * gvx_invariant_mass itself.
  */
 gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n,
                                    int32_t coords, int32_t dtype, void *stream);
@@ -138,9 +143,12 @@ gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, in
  * A general 4-D Lorentz transformation (Sec. 4.1: 4x4 matrices applied to every vector of an
  * array): out[i] = L_i v[i] for PxPyPzE vectors, L row-major 4x4 in (x, y, z, t) order.
  * l_stride 0: L holds one matrix (16 scalars) for every vector; 1: L holds n matrices, 16
- * scalars each, contiguous.  Four FMA chains per vector in the working precision (no structure
- * of L is assumed, so the error is a few ulps of sum_k |L_rk v_k| per component).  L must be
- * aligned to 16 bytes when l_stride is 1.
+ * scalars each, contiguous.  No structure of L is assumed.  FP32, and FP64 with a matrix per
+ * vector: four FMA chains per vector, within 4 u sum_k |L_rk v_k| per component (u the unit
+ * roundoff).  FP64 with one shared matrix: float-float row sums (rows and vectors scaled by
+ * powers of two), within 2^-42 sum_k |L_rk v_k| + 2^-70 max_k |L_rk| max_k |v_k| per component;
+ * vectors (or a matrix) outside its range (scale exponents beyond +-400, zero vectors, Inf/NaN)
+ * take the FMA chains.  L must be aligned to 16 bytes when l_stride is 1.
  */
 gvx_status gvx_lorentz_apply(const void *L, int64_t l_stride, const gvx_lv *v, gvx_lv *out,
                              int64_t n, int32_t dtype, void *stream);

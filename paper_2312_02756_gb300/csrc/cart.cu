@@ -2,10 +2,10 @@
 // are templated on their coordinate system; Sec. 4.1: transformations are 4x4 matrices applied
 // to every vector of an array).
 //
-// gvx_invariant_mass_cart: pair masses of Cartesian legs, PxPyPzE or PxPyPzM.  PxPyPzE pairs take
-// the exact fixed-point evaluation of cart_fixed.cuh (integer and FP32 pipes); PxPyPzM pairs, and
-// the rare PxPyPzE pairs outside its domain, the cancellation-free FP64 form of cart_mass.cuh (an
-// FMA-exact cross product and E^2 - |p|^2), on the FP64 pipe for both storage precisions.
+// gvx_invariant_mass_cart: pair masses of Cartesian legs, PxPyPzE or PxPyPzM, through the
+// fixed-point evaluations of cart_fixed.cuh (integer and FP32 pipes); the rare pairs outside
+// their domain take the cancellation-free FP64 form of cart_mass.cuh (an FMA-exact cross product
+// and E^2 - |p|^2), on the FP64 pipe for both storage precisions.
 //
 // gvx_lorentz_apply: out = L v for a row-major 4x4 matrix L, shared or one per vector.  One
 // shared FP64 matrix takes the float-float row sums of apply_ff.cuh; a matrix per vector (whose
@@ -28,9 +28,9 @@ __global__ void __launch_bounds__(256) mass_cart_kernel(Lv a, Lv b, T *__restric
     const V4<T> x = ld4<T, LA>(a, i), y = ld4<T, LB>(b, i);
     T r;
     bool fast = false;
-    if constexpr (COORDS == 0) {
+    {
       const T ta[4] = {x.x, x.y, x.z, x.w}, tb[4] = {y.x, y.y, y.z, y.w};
-      fast = cfix::mass_pxpypze(ta, tb, &r);
+      fast = COORDS == 0 ? cfix::mass_pxpypze(ta, tb, &r) : cfix::mass_pxpypzm(ta, tb, &r);
     }
     if (!fast) {
       // FP32 legs are evaluated in FP64 (exact upcasts): a float E next to a float |p| leaves q

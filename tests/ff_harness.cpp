@@ -126,14 +126,15 @@ int64_t ffh_mass_cart(const double *a, const double *b, int64_t n, int coords, d
   return c;
 }
 
-// The fixed-point fast path of the PxPyPzE pair mass: FP64 legs (m) and the same legs rounded
-// to float (m32); ok / ok32 = inside the fast path.
-int64_t ffh_mass_cart_fixed(const double *a, const double *b, int64_t n, double *m, uint8_t *ok,
-                            float *m32, uint8_t *ok32) {
+// The fixed-point fast paths of the Cartesian pair mass (coords 0: PxPyPzE, 1: PxPyPzM): FP64
+// legs (m) and the same legs rounded to float (m32); ok / ok32 = inside the fast path.
+int64_t ffh_mass_cart_fixed(const double *a, const double *b, int64_t n, int coords, double *m,
+                            uint8_t *ok, float *m32, uint8_t *ok32) {
   int64_t c = 0;
   for (int64_t i = 0; i < n; i++) {
     double out = NAN;
-    ok[i] = gvx::cfix::mass_pxpypze(a + 4 * i, b + 4 * i, &out);
+    ok[i] = coords == 0 ? gvx::cfix::mass_pxpypze(a + 4 * i, b + 4 * i, &out)
+                        : gvx::cfix::mass_pxpypzm(a + 4 * i, b + 4 * i, &out);
     m[i] = out;
     c += ok[i];
     float fa[4], fb[4], o32 = NAN;
@@ -141,7 +142,7 @@ int64_t ffh_mass_cart_fixed(const double *a, const double *b, int64_t n, double 
       fa[k] = (float)a[4 * i + k];
       fb[k] = (float)b[4 * i + k];
     }
-    ok32[i] = gvx::cfix::mass_pxpypze(fa, fb, &o32);
+    ok32[i] = coords == 0 ? gvx::cfix::mass_pxpypze(fa, fb, &o32) : gvx::cfix::mass_pxpypzm(fa, fb, &o32);
     m32[i] = o32;
   }
   return c;

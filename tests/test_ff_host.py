@@ -346,12 +346,13 @@ def test_ff_cartesian_mass_against_oracle(ffh, orc):
         assert err.max() <= 1e-12, (coords, err.max())
 
 
-def _cart_fixed(ffh, a, b):
+def _cart_fixed(ffh, a, b, coords=0):
     a, b = np.ascontiguousarray(a, dtype=np.float64), np.ascontiguousarray(b, dtype=np.float64)
     n = len(a)
     m, ok = np.empty(n), np.empty(n, np.uint8)
     m32, ok32 = np.empty(n, np.float32), np.empty(n, np.uint8)
-    ffh.ffh_mass_cart_fixed(_p(a), _p(b), ctypes.c_int64(n), _p(m), _p(ok), _p(m32), _p(ok32))
+    ffh.ffh_mass_cart_fixed(_p(a), _p(b), ctypes.c_int64(n), coords, _p(m), _p(ok), _p(m32),
+                            _p(ok32))
     return m, ok.astype(bool), m32, ok32.astype(bool)
 
 
@@ -470,3 +471,52 @@ def test_ff_lorentz_apply_domain(ffh, orc):
         L2 = L.copy()
         L2[1] = [bad, 0.0, 0.0, 0.0]
         assert _apply(ffh, L2, v)[0] == -1
+
+
+def _pxpypzm_inputs(seed, n):
+    """PxPyPzM legs: random pairs, then a quarter near-collinear with light second legs, and a
+    quarter soft-hard (|p| ratios up to 3e4)."""
+    g = syn.rng(seed)
+    a, b = syn.pxpypze(g, n), syn.pxpypze(g, n)
+    a[:, 3] = g.uniform(0, 10, n)
+    b[:, 3] = g.uniform(0, 10, n)
+    k = n // 4
+    b[:k, :3] = a[:k, :3] * g.uniform(0.5, 2.0, (k, 1)) + a[:k, :3] * g.uniform(-1e-6, 1e-6, (k, 3))
+    b[:k, 3] = g.uniform(0, 1e-3, k)
+    b[k:2 * k, :3] *= 1e-4
+    return a, b
+
+
+def test_fixed_point_pxpypzm_mass_against_oracle(ffh, orc):
+    """The PxPyPzM fast path (per-leg fixed point, float-float on non-negative terms) against the
+    binary128 definition: within 2^-43 relative wherever it takes the pair; it takes every
+    random pair and every soft-hard pair, FP64 and FP32 (one rounding)."""
+    a, b = _pxpypzm_inputs(170, 40000)
+    m, ok, m32, ok32 = _cart_fixed(ffh, a, b, coords=1)
+    ref = orc.mass_cart_def(a, b, "pxpypzm")
+    k = len(a) // 4
+    assert ok[k:].all()
+    assert np.max(np.abs(m[ok] - ref[ok]) / ref[ok]) <= 2.0 ** -43
+    a32, b32 = syn.to_f32(a).astype(np.float64), syn.to_f32(b).astype(np.float64)
+    _, _, m32, ok32 = _cart_fixed(ffh, a32, b32, coords=1)
+    ref32 = orc.mass_cart_def(a32, b32, "pxpypzm")
+    assert ok32[k:].all()
+    assert np.max(np.abs(m32[ok32].astype(np.float64) - ref32[ok32]) / ref32[ok32]) <= 2.0 ** -24 * 1.01
+
+
+def test_fixed_point_pxpypzm_mass_edges(ffh, orc):
+    """Collinear massless legs (m = 0: refused), back-to-back legs, legs at rest, a dot product
+    of exactly zero, scales 61 binades apart (refused) and a non-finite leg (refused)."""
+    rows = [([0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 3.0, 0.0]),
+            ([1.0, 2.0, 3.0, 0.5], [-1.0, -2.0, -3.0, 0.5]),
+            ([0.0, 0.0, 0.0, 2.0], [0.0, 0.0, 0.0, 3.0]),
+            ([1.0, 0.0, 0.0, 0.1], [0.0, 1.0, 0.0, 0.2]),
+            ([1.0, 0.0, 0.0, 0.0], [2.0 ** -61, 0.0, 0.0, 2.0 ** -61]),
+            ([np.nan, 0.0, 0.0, 1.0], [1.0, 0.0, 0.0, 1.0])]
+    a = np.array([r[0] for r in rows])
+    b = np.array([r[1] for r in rows])
+    m, ok, _, _ = _cart_fixed(ffh, a, b, coords=1)
+    assert ok.tolist() == [False, True, True, True, False, False]
+    ref = orc.mass_cart_def(a[ok], b[ok], "pxpypzm")
+    assert np.all(np.abs(m[ok] - ref) <= 2.0 ** -43 * ref)
+    assert m[2] == 5.0
