@@ -194,14 +194,16 @@ GVX_HD bool mass_pxpypze(const float *a, const float *b, float *out) {
 //   E1 E2 - p1.p2 = (|p1 x p2|^2 + m1^2 P2^2 + m2^2 P1^2 + m1^2 m2^2) / (E1 E2 + p1.p2)   (p1.p2 > 0)
 //                 = E1 E2 + |p1.p2|                                                        (otherwise),
 // the numerator being E1^2 E2^2 - (p1.p2)^2 by Lagrange's identity.  Every term is non-negative
-// and the only cancelling quantities are the components of p1 x p2.  An absolute error in m_i^2
-// reaches m^2 multiplied by about E_o / E_i, so each leg is scaled by its own power of two
-// 2^-s_i and truncated to units of 2^-83 of it; P_i^2 and m_i^2 (units 2^-102 of 2^(2 s_i)),
-// p1.p2 and p1 x p2 (units 2^-102 of 2^(s1 + s2)) come from limb products, and the rest is
-// float-float arithmetic on non-negative numbers at the scale 2^(s1 + s2).  In units of the
-// larger leg's squared scale H the fixed-point errors stay below 2^-75; the result is kept when
+// and the only cancelling quantities are the components of p1 x p2: those come from the
+// fixed-point limb products (components truncated to units of 2^-83 of their leg's scale, the
+// products kept to units of 2^-102 of 2^(s1 + s2)); P_i^2, m_i^2 and p1.p2 (which only ever
+// enters next to E1 E2) are float-float arithmetic on the scaled components, like the rest.
+// Each leg has its own power-of-two scale 2^s_i: an absolute error in m_i^2 reaches m^2
+// multiplied by about E_o / E_i, so the resolution must follow each leg.  In units of the larger
+// leg's squared scale H the fixed-point errors stay below 2^-76; the result is kept when
 // m^2 >= 2^-31 H, so its relative error (with the float-float steps) is below 2^-43.
-// Domain: both legs finite with scale exponents within the format's limit and at most 60 apart.
+// Domain: both legs finite with scale exponents within half the format's limit and at most 60
+// apart.
 
 // (A B) / 2^64 for magnitudes A, B < 2^85, within 4 units: with A = ah 2^64 + a1 2^32 + a0,
 // A B / 2^64 = ah bh 2^64 + ah (b1 2^32 + b0) + bh (a1 2^32 + a0) + a1 b1 + (a1 b0 + a0 b1) / 2^32
@@ -212,8 +214,6 @@ GVX_HD u128 mul_shift64(u128 A, u128 B) {
   return ((u128)((uint64_t)ah * bh) << 64) + mul32x64(ah, (uint64_t)B) + mul32x64(bh, (uint64_t)A) +
          ((uint64_t)a1 * b1 + mul32hi(a1, b0) + mul32hi(a0, b1));
 }
-
-GVX_HD i128 signed_of(u128 q, bool neg) { return neg ? -(i128)q : (i128)q; }
 
 // |q| * 2^-102 as ff (truncated to 47 bits), for any q < 2^112; 0 gives 0.
 GVX_HD ff fixed_to_ff_any(u128 q) {
@@ -232,15 +232,19 @@ GVX_HD ff fixed_to_ff_any(u128 q) {
   return {hi, ffm::fsub(ffm::u2f(base | rest), ffm::u2f(base))};
 }
 
-GVX_HD ff signed_ff(i128 v) {
-  const ff r = fixed_to_ff_any(v < 0 ? (u128)(-v) : (u128)v);
-  return v < 0 ? ffm::neg(r) : r;
+// x 2^-s as ff: a double through the ranged conversion (below 2^-74 counts as 0), a float exactly.
+GVX_HD ff scaled_ff(double x, int s) { return ffm::from_double_ranged(x, s); }
+GVX_HD ff scaled_ff(float x, int s) { return {ffm::fmul(x, ffm::pow2f(-s)), 0.0f}; }
+
+// |component of p1 x p2| = |s_a A - s_b B| for the magnitudes A, B of the two products.
+GVX_HD ff cross_component(u128 A, bool na, u128 B, bool nb) {
+  return fixed_to_ff_any(abs_sum(A, na, B, !nb));
 }
 
-// The scaled mass sqrt(m^2 / 2^(2 e)) in ff (with the sign of m^2) and the exponent e of the pair
-// mass of two PxPyPzM legs; false outside the fast path.
+// The scaled mass sqrt(m^2 / 2^(2 e)) in ff and the exponent e of the pair mass of two PxPyPzM
+// legs; false outside the fast path.
 template <typename T>
-GVX_HD bool mass_pxpypzm_scaled(const T *a, const T *b, ff *m, int *e_out, bool *neg_out) {
+GVX_HD bool mass_pxpypzm_scaled(const T *a, const T *b, ff *m, int *e_out) {
   Decoded d[8];
   int e1 = 0, e2 = 0;
 #pragma unroll
@@ -255,57 +259,57 @@ GVX_HD bool mass_pxpypzm_scaled(const T *a, const T *b, ff *m, int *e_out, bool 
   if (e1 == Fmt<T>::kMaxE || e2 == Fmt<T>::kMaxE || s1 < -lim || s1 > lim || s2 < -lim || s2 > lim ||
       s1 - s2 > 60 || s2 - s1 > 60)
     return false;
-  u128 A[4], B[4];
+  using namespace ffm;
+  // |p1 x p2| components from exact limb products (scale 2^(s1 + s2))
+  u128 A[3], B[3];
 #pragma unroll
-  for (int k = 0; k < 4; k++) {
+  for (int k = 0; k < 3; k++) {
     A[k] = align<T>(d[k], e1);
     B[k] = align<T>(d[k + 4], e2);
   }
-  // leg quantities (units 2^-102 of 2^(2 s_i)) and pair quantities (of 2^(s1 + s2))
-  const u128 P1 = square_shift64(A[0]) + square_shift64(A[1]) + square_shift64(A[2]);
-  const u128 P2 = square_shift64(B[0]) + square_shift64(B[1]) + square_shift64(B[2]);
-  const u128 q1 = square_shift64(A[3]), q2 = square_shift64(B[3]);
-  const i128 dot = signed_of(mul_shift64(A[0], B[0]), d[0].neg != d[4].neg) +
-                   signed_of(mul_shift64(A[1], B[1]), d[1].neg != d[5].neg) +
-                   signed_of(mul_shift64(A[2], B[2]), d[2].neg != d[6].neg);
-  const i128 cx = signed_of(mul_shift64(A[1], B[2]), d[1].neg != d[6].neg) -
-                  signed_of(mul_shift64(A[2], B[1]), d[2].neg != d[5].neg);
-  const i128 cy = signed_of(mul_shift64(A[2], B[0]), d[2].neg != d[4].neg) -
-                  signed_of(mul_shift64(A[0], B[2]), d[0].neg != d[6].neg);
-  const i128 cz = signed_of(mul_shift64(A[0], B[1]), d[0].neg != d[5].neg) -
-                  signed_of(mul_shift64(A[1], B[0]), d[1].neg != d[4].neg);
-  using namespace ffm;
-  const ff fP1 = fixed_to_ff_any(P1), fP2 = fixed_to_ff_any(P2);
-  const ff fq1 = fixed_to_ff_any(q1), fq2 = fixed_to_ff_any(q2);
-  const ff fd = signed_ff(dot);
-  const ff E1E2 = ffm::sqrt(mul(add_same(fP1, fq1), add_same(fP2, fq2)));  // scale 2^(s1 + s2)
+  const ff cx = cross_component(mul_shift64(A[1], B[2]), d[1].neg != d[6].neg,
+                                mul_shift64(A[2], B[1]), d[2].neg != d[5].neg);
+  const ff cy = cross_component(mul_shift64(A[2], B[0]), d[2].neg != d[4].neg,
+                                mul_shift64(A[0], B[2]), d[0].neg != d[6].neg);
+  const ff cz = cross_component(mul_shift64(A[0], B[1]), d[0].neg != d[5].neg,
+                                mul_shift64(A[1], B[0]), d[1].neg != d[4].neg);
+  // the rest in ff on the scaled components
+  ff x[4], y[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    x[k] = scaled_ff(a[k], s1);
+    y[k] = scaled_ff(b[k], s2);
+  }
+  const ff P1 = add_same(add_same(sqr(x[0]), sqr(x[1])), sqr(x[2]));
+  const ff P2 = add_same(add_same(sqr(y[0]), sqr(y[1])), sqr(y[2]));
+  const ff q1 = sqr(x[3]), q2 = sqr(y[3]);
+  const ff dot = add(add(mul(x[0], y[0]), mul(x[1], y[1])), mul(x[2], y[2]));
+  const ff E1E2 = ffm::sqrt(mul(add_same(P1, q1), add_same(P2, q2)));  // scale 2^(s1 + s2)
   ff T2;
-  if (fd.hi > 0.0f) {
-    const ff c2 = add_same(add_same(sqr(signed_ff(cx)), sqr(signed_ff(cy))), sqr(signed_ff(cz)));
-    const ff N = add_same(add_same(c2, mul(fq1, fP2)), add_same(mul(fq2, fP1), mul(fq1, fq2)));
-    T2 = scale(div(N, add_same(E1E2, fd)), 2.0f);
+  if (dot.hi > 0.0f) {
+    const ff c2 = add_same(add_same(sqr(cx), sqr(cy)), sqr(cz));
+    const ff N = add_same(add_same(c2, mul(q1, P2)), add_same(mul(q2, P1), mul(q1, q2)));
+    T2 = scale(div(N, add_same(E1E2, dot)), 2.0f);
   } else {
-    T2 = scale(add_same(E1E2, neg(fd)), 2.0f);
+    T2 = scale(add_same(E1E2, neg(dot)), 2.0f);
   }
   // m^2 / 2^(s1 + s2) = q1 2^(s1 - s2) + q2 2^(s2 - s1) + 2 T; an odd s1 + s2 moves one factor 2
   // inside the root
   const int odd = (s1 + s2) & 1;
-  const ff m2 = renorm(add_same(add_same(scale(fq1, pow2f(s1 - s2 + odd)), scale(fq2, pow2f(s2 - s1 + odd))),
+  const ff m2 = renorm(add_same(add_same(scale(q1, pow2f(s1 - s2 + odd)), scale(q2, pow2f(s2 - s1 + odd))),
                                 scale(T2, odd ? 2.0f : 1.0f)));
   // threshold: m^2 >= 2^-31 2^(2 max(s1, s2)), i.e. the scaled value >= 2^(|s1 - s2| - 31 + odd)
   const int gap = s1 > s2 ? s1 - s2 : s2 - s1;
   if (!(m2.hi >= pow2f(gap - 31 + odd))) return false;
   *m = ffm::sqrt(m2);
   *e_out = (s1 + s2 - odd) / 2;
-  *neg_out = false;
   return true;
 }
 
 GVX_HD bool mass_pxpypzm(const double *a, const double *b, double *out) {
   ff m;
   int e;
-  bool neg;
-  if (!mass_pxpypzm_scaled(a, b, &m, &e, &neg)) return false;
+  if (!mass_pxpypzm_scaled(a, b, &m, &e)) return false;
   *out = ffm::to_double(m, e);
   return true;
 }
@@ -313,8 +317,7 @@ GVX_HD bool mass_pxpypzm(const double *a, const double *b, double *out) {
 GVX_HD bool mass_pxpypzm(const float *a, const float *b, float *out) {
   ff m;
   int e;
-  bool neg;
-  if (!mass_pxpypzm_scaled(a, b, &m, &e, &neg)) return false;
+  if (!mass_pxpypzm_scaled(a, b, &m, &e)) return false;
   *out = ffm::fmul(ffm::fadd(m.hi, m.lo), ffm::pow2f(e));
   return true;
 }
