@@ -1,4 +1,8 @@
 """Shared helpers for the GPU parity tests (tolerances, device transfer, error measures)."""
+import ctypes
+import os
+import subprocess
+
 import numpy as np
 import pytest
 
@@ -86,3 +90,21 @@ def edge_pairs():
     a = np.array([r[0] for r in rows], dtype=np.float64)
     b = np.array([r[1] for r in rows], dtype=np.float64)
     return a, b
+
+
+def build_ff_harness(out_dir):
+    """Compile tests/ff_harness.cpp (the library's float-float and fixed-point headers built for
+    the host) into out_dir and load it."""
+    from paper_2312_02756_gb300 import gen_tables
+    out_dir = str(out_dir)
+    gen_tables.write(os.path.join(out_dir, "gvx_tables.inc"))
+    out = os.path.join(out_dir, "ffh.so")
+    here = os.path.dirname(os.path.abspath(__file__))
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                    "-shared", "-I" + out_dir, os.path.join(here, "ff_harness.cpp"), "-o", out],
+                   check=True)
+    lib = ctypes.CDLL(out)
+    for name in ("ffh_mass", "ffh_mass_grad", "ffh_boost", "ffh_boost_bwd", "ffh_mass_cart",
+                 "ffh_mass_cart_fixed", "ffh_apply"):
+        getattr(lib, name).restype = ctypes.c_int64
+    return lib

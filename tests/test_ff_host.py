@@ -16,22 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 @pytest.fixture(scope="module")
 def ffh(tmp_path_factory):
-    from paper_2312_02756_gb300 import gen_tables
-    d = tmp_path_factory.mktemp("ffh")
-    gen_tables.write(str(d / "gvx_tables.inc"))
-    out = str(d / "ffh.so")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                    "-shared", "-I" + str(d), os.path.join(HERE, "ff_harness.cpp"), "-o", out],
-                   check=True)
-    lib = ctypes.CDLL(out)
-    lib.ffh_mass.restype = ctypes.c_int64
-    lib.ffh_mass_grad.restype = ctypes.c_int64
-    lib.ffh_boost.restype = ctypes.c_int64
-    lib.ffh_boost_bwd.restype = ctypes.c_int64
-    lib.ffh_mass_cart.restype = ctypes.c_int64
-    lib.ffh_mass_cart_fixed.restype = ctypes.c_int64
-    lib.ffh_apply.restype = ctypes.c_int64
-    return lib
+    from helpers import build_ff_harness
+    return build_ff_harness(tmp_path_factory.mktemp("ffh"))
 
 
 def _p(a):

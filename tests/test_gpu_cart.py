@@ -153,3 +153,35 @@ def test_lorentz_apply_boost_matrix_matches_boost(orc):
     scale = np.abs(v) @ np.abs(L).T
     # the transformation's float-float bound plus the boost's own (normwise on E')
     assert np.all(np.abs(out - ref) <= 2.0 ** -42 * (scale + scale[:, 3:4]))
+
+
+def test_device_fast_paths_match_host_build(orc, tmp_path):
+    """The device builds of the fixed-point pair masses and of the float-float transformation give
+    the same bits as the same headers compiled for the host (whose accuracy the CPU tests check
+    case by case), wherever the host build takes the fast path."""
+    import ctypes
+    import paper_2312_02756_gb300 as gvx
+    from helpers import build_ff_harness
+    torch = torch_cuda()
+    ffh = build_ff_harness(tmp_path)
+    P = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    g = syn.rng(86)
+    n = 1 << 16
+    for coords, code in (("pxpypze", 0), ("pxpypzm", 1)):
+        a, b = _legs(87 + code, n, coords)
+        m = _mass(a, b, coords)
+        hm, ok = np.empty(n), np.empty(n, np.uint8)
+        m32, ok32 = np.empty(n, np.float32), np.empty(n, np.uint8)
+        ffh.ffh_mass_cart_fixed(P(a), P(b), ctypes.c_int64(n), code, P(hm), P(ok), P(m32), P(ok32))
+        ok = ok.astype(bool)
+        assert ok.mean() > 0.7
+        assert np.array_equal(m[ok], hm[ok]), coords
+        d32 = _mass(a.astype(np.float32), b.astype(np.float32), coords, dtype=torch.float32)
+        ok32 = ok32.astype(bool)
+        assert np.array_equal(d32[ok32], m32[ok32]), coords
+    v = syn.pxpypze(g, n)
+    L = np.ascontiguousarray(g.uniform(-2, 2, (4, 4)))
+    out = gvx.lorentz_apply(torch.as_tensor(L).cuda(), dev(v)).cpu().numpy()
+    hout, hok = np.empty_like(v), np.empty(n, np.uint8)
+    assert ffh.ffh_apply(P(L), P(v), ctypes.c_int64(n), P(hout), P(hok)) == n
+    assert np.array_equal(out, hout)
