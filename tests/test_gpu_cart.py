@@ -156,9 +156,11 @@ def test_lorentz_apply_boost_matrix_matches_boost(orc):
 
 
 def test_device_fast_paths_match_host_build(orc, tmp_path):
-    """The device builds of the fixed-point pair masses and of the float-float transformation give
-    the same bits as the same headers compiled for the host (whose accuracy the CPU tests check
-    case by case), wherever the host build takes the fast path."""
+    """The device builds of the fixed-point pair masses and of the float-float transformation
+    agree with the same headers compiled for the host (whose accuracy the CPU tests check case by
+    case), wherever the host build takes the fast path: the transformation bit for bit, the masses
+    within 2^-44 relative (FP32: one float ulp), since the float-float square root starts from the
+    device's approximate reciprocal square root and from the host's own."""
     import ctypes
     import paper_2312_02756_gb300 as gvx
     from helpers import build_ff_harness
@@ -175,10 +177,11 @@ def test_device_fast_paths_match_host_build(orc, tmp_path):
         ffh.ffh_mass_cart_fixed(P(a), P(b), ctypes.c_int64(n), code, P(hm), P(ok), P(m32), P(ok32))
         ok = ok.astype(bool)
         assert ok.mean() > 0.7
-        assert np.array_equal(m[ok], hm[ok]), coords
+        assert np.all(np.abs(m[ok] - hm[ok]) <= 2.0 ** -44 * np.abs(hm[ok])), coords
         d32 = _mass(a.astype(np.float32), b.astype(np.float32), coords, dtype=torch.float32)
         ok32 = ok32.astype(bool)
-        assert np.array_equal(d32[ok32], m32[ok32]), coords
+        dm = np.abs(d32[ok32].astype(np.float64) - m32[ok32].astype(np.float64))
+        assert np.all(dm <= 2.0 ** -23 * np.abs(m32[ok32].astype(np.float64))), coords
     v = syn.pxpypze(g, n)
     L = np.ascontiguousarray(g.uniform(-2, 2, (4, 4)))
     out = gvx.lorentz_apply(torch.as_tensor(L).cuda(), dev(v)).cpu().numpy()
