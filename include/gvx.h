@@ -130,8 +130,7 @@ gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, g
  * relative; PxPyPzM: p1 x p2, p1.p2, |p_i|^2 and m_i^2 in fixed point at each leg's own scale and
  * the cancellation-free combination m1^2 + m2^2 + 2 (E1 E2 - p1.p2) in float-float, within 2^-43
  * relative.  Pairs whose |m^2| falls below 2^-31 of the larger leg's squared scale (a power of
- * two within 2x of its largest component), with a nonzero component more than 2^31 (FP32: 2^60)
- * below that scale, or outside the fixed-point range, take a
+ * two within 2x of its largest component), or outside the fixed-point range, take a
  * cancellation-free FP64 form (an FMA-exact cross product and E^2 - |p|^2): within 1e-12
  * relative for legs with E^2 >= |p|^2.  FP32 legs go through the same evaluations and are rounded
  * once.  Layouts and alignment as gvx_invariant_mass; coords GVX_PTETAPHIM is
