@@ -14,9 +14,8 @@
 // final rounding (none for FP32 output).
 //
 // Outside the fast path (a non-finite component, a scale exponent outside [-900, 900] for double
-// or [-100, 100] for float input, a nonzero component more than 2^31 (float: 2^60) below the
-// largest, or |m^2| below the threshold, zero included) the functions return false and the caller
-// evaluates the cancellation-free FP64 form.
+// or [-100, 100] for float input, or |m^2| below the threshold, zero included) the functions
+// return false and the caller evaluates the cancellation-free FP64 form.
 #pragma once
 
 #include "ff.cuh"
@@ -82,17 +81,11 @@ struct Fmt<float> {
 
 // |x| * 2^(kFrac - sc), truncated, for the largest biased exponent emax of the pair (sc = emax -
 // bias, so |x| 2^-sc < 2): x = sig * 2^(e - bias - kSig), so the significand moves left by
-// k = e - emax + kFrac - kSig (at most 31 for double, 60 for float).  A nonzero x that would move
-// right (more than 2^31, or 2^60 for float, below the largest component) sets *tiny instead: such
-// pairs are rare and take the FP64 form, which keeps the shift a single left funnel.
+// k = e - emax + kFrac - kSig (at most 31 for double, 60 for float) or right by -k.
 template <typename T>
-GVX_HD u128 align(const Decoded &d, int emax, bool *tiny) {
-  const int k = d.e - emax + kFrac - Fmt<T>::kSig;
-  if (d.e == 0) return 0;
-  if (k < 0) {
-    *tiny = true;
-    return 0;
-  }
+GVX_HD u128 align(const Decoded &d, int emax) {
+  const int k = d.e == 0 ? -64 : d.e - emax + kFrac - Fmt<T>::kSig;
+  if (k < 0) return (u128)(k > -64 ? d.sig >> -k : 0);
   if (sizeof(T) == 8) {  // k <= 31: the low 64 bits and the top word separately
     const uint32_t top = k ? (uint32_t)(d.sig >> 32) >> (32 - k) : 0u;
     return ((u128)top << 64) | (uint64_t)(d.sig << k);
@@ -131,15 +124,13 @@ GVX_HD bool m2_fixed(const T *a, const T *b, i128 *m2, int *sc) {
   const int s = emax - Fmt<T>::kBias;
   if (emax == Fmt<T>::kMaxE || s < -Fmt<T>::kScaleLim || s > Fmt<T>::kScaleLim) return false;
   u128 pos = 0, neg = 0;
-  bool tiny = false;
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    const u128 q = square_shift64(abs_sum(align<T>(d[k], emax, &tiny), d[k].neg,
-                                          align<T>(d[k + 4], emax, &tiny), d[k + 4].neg));
+    const u128 q = square_shift64(
+        abs_sum(align<T>(d[k], emax), d[k].neg, align<T>(d[k + 4], emax), d[k + 4].neg));
     if (k == 3) pos = q;  // components 0..2 are p, 3 is E
     else neg += q;
   }
-  if (tiny) return false;
   *m2 = (i128)pos - (i128)neg;
   *sc = s;
   return true;
@@ -271,13 +262,11 @@ GVX_HD bool mass_pxpypzm_scaled(const T *a, const T *b, ff *m, int *e_out) {
   using namespace ffm;
   // |p1 x p2| components from exact limb products (scale 2^(s1 + s2))
   u128 A[3], B[3];
-  bool tiny = false;
 #pragma unroll
   for (int k = 0; k < 3; k++) {
-    A[k] = align<T>(d[k], e1, &tiny);
-    B[k] = align<T>(d[k + 4], e2, &tiny);
+    A[k] = align<T>(d[k], e1);
+    B[k] = align<T>(d[k + 4], e2);
   }
-  if (tiny) return false;
   const ff cx = cross_component(mul_shift64(A[1], B[2]), d[1].neg != d[6].neg,
                                 mul_shift64(A[2], B[1]), d[2].neg != d[5].neg);
   const ff cy = cross_component(mul_shift64(A[2], B[0]), d[2].neg != d[4].neg,
