@@ -64,6 +64,7 @@ def _load():
         "orc_event_pairs_grad_def": ([P, P, I64, P, P, P], INT),
         "orc_lorentz_apply_def": ([P, I64, P, I64, P], None),
         "orc_mass_cart_def": ([P, P, I64, INT, P], None),
+        "orc_to_pxpypze_def": ([P, I64, INT, P], None),
         "orc_pair_select_def": ([P, P, I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                  P, P, P, P], INT),
@@ -251,13 +252,25 @@ def lorentz_apply_def(L, v) -> np.ndarray:
     return out
 
 
+COORDS = {"pxpypze": 0, "pxpypzm": 1, "ptetaphie": 2, "ptetaphim": 3}
+
+
 def mass_cart_def(a, b, coords="pxpypze") -> np.ndarray:
-    """O1 pair mass for Cartesian legs: coords 'pxpypze' (E stored) or 'pxpypzm' (m stored)."""
+    """O1 pair mass for legs in any of the coordinate systems 'pxpypze' (E stored), 'pxpypzm'
+    (m stored), 'ptetaphie' (pt, eta, phi, E) or 'ptetaphim'."""
     a, b = _rows(a, 4), _rows(b, 4)
-    code = {"pxpypze": 0, "pxpypzm": 1}[coords]
+    code = COORDS[coords]
     m = np.empty(a.shape[0])
     _load().orc_mass_cart_def(_ptr(a), _ptr(b), a.shape[0], code, _ptr(m))
     return m
+
+
+def to_pxpypze_def(p, coords) -> np.ndarray:
+    """O1 conversion of rows in any of the coordinate systems of mass_cart_def to PxPyPzE."""
+    p = _rows(p, 4)
+    out = np.empty_like(p)
+    _load().orc_to_pxpypze_def(_ptr(p), p.shape[0], COORDS[coords], _ptr(out))
+    return out
 
 
 def to_cartesian_def(p) -> np.ndarray:

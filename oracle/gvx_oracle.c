@@ -554,9 +554,23 @@ void orc_lorentz_apply_def(const double *L16, int64_t l_stride, const double *v,
   }
 }
 
-/* A Cartesian leg as PxPyPzE in binary128: coords 0 gives (px, py, pz, E) as stored, coords 1
- * gives (px, py, pz, m) and E = sqrt(px^2 + py^2 + pz^2 + m^2) (the stored m enters through m^2). */
+/* A leg as PxPyPzE in binary128 (Sec. 3.1: any 4-D coordinate system): coords 0 gives
+ * (px, py, pz, E) as stored; 1 gives (px, py, pz, m) with E = sqrt(px^2 + py^2 + pz^2 + m^2) (the
+ * stored m enters through m^2); 2 gives (pt, eta, phi, E) with px = pt cos(phi), py = pt sin(phi),
+ * pz = pt sinh(eta) and E as stored; 3 gives (pt, eta, phi, m) through leg_to_cartesian_q. */
 static void cart_leg_q(const double *x, int coords, qreal out[4]) {
+  if (coords == 3) {
+    leg_to_cartesian_q(x, out);
+    return;
+  }
+  if (coords == 2) {
+    qreal pt = x[0], eta = x[1], phi = x[2];
+    out[0] = pt * Q_COS(phi);
+    out[1] = pt * Q_SIN(phi);
+    out[2] = pt * Q_SINH(eta);
+    out[3] = x[3];
+    return;
+  }
   out[0] = x[0];
   out[1] = x[1];
   out[2] = x[2];
@@ -568,10 +582,10 @@ static void cart_leg_q(const double *x, int coords, qreal out[4]) {
   }
 }
 
-/* Invariant mass of pairs given in a Cartesian coordinate system (Sec. 3.1: the kernels are
- * templated on the 4-D system; Sec. 4.1 Fig. 1 adds the pair and takes mass()): coords 0 =
- * PxPyPzE, 1 = PxPyPzM.  m[i] = mass(a[i] + b[i]) with mass() as in lv_mass_q (a negative
- * E^2 - |p|^2 gives -sqrt of its magnitude, GenVector's convention for spacelike vectors). */
+/* Invariant mass of pairs given in any of the coordinate systems of cart_leg_q (Sec. 3.1: the
+ * kernels are templated on the 4-D system; Sec. 4.1 Fig. 1 adds the pair and takes mass()):
+ * m[i] = mass(a[i] + b[i]) with mass() as in lv_mass_q (a negative E^2 - |p|^2 gives -sqrt of its
+ * magnitude, GenVector's convention for spacelike vectors). */
 void orc_mass_cart_def(const double *a, const double *b, int64_t n, int coords, double *m) {
   for (int64_t i = 0; i < n; i++) {
     qreal va[4], vb[4], w[4];
@@ -588,6 +602,15 @@ void orc_to_cartesian_def(const double *p, int64_t n, double *out) {
   for (int64_t i = 0; i < n; i++) {
     qreal v[4];
     leg_to_cartesian_q(p + 4 * i, v);
+    for (int c = 0; c < 4; c++) out[4 * i + c] = (double)v[c];
+  }
+}
+
+/* Any coordinate system of cart_leg_q -> PxPyPzE, in binary128, rounded to double once. */
+void orc_to_pxpypze_def(const double *p, int64_t n, int coords, double *out) {
+  for (int64_t i = 0; i < n; i++) {
+    qreal v[4];
+    cart_leg_q(p + 4 * i, coords, v);
     for (int c = 0; c < 4; c++) out[4 * i + c] = (double)v[c];
   }
 }

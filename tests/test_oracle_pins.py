@@ -657,3 +657,67 @@ def test_mass_cart_rotation_invariance(orc):
     neg = am.copy()
     neg[:, 3] *= -1
     assert np.array_equal(orc.mass_cart_def(am, b, "pxpypzm"), orc.mass_cart_def(neg, b, "pxpypzm"))
+
+
+def _mp_ptetaphie_leg(mp, x):
+    pt, eta, phi, E = (mp.mpf(float(t)) for t in x)
+    return [pt * mp.cos(phi), pt * mp.sin(phi), pt * mp.sinh(eta), E]
+
+
+def test_ptetaphie_conversion_and_mass_brute_force(orc):
+    """PtEtaPhiE legs (E stored) against 50-digit brute force: the conversion to PxPyPzE component
+    by component (one rounding) and the pair mass of the converted sum, on random and on
+    near-collinear pairs; the PtEtaPhiM conversion through the same entry agrees with
+    to_cartesian_def bit for bit."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    g = syn.rng(190)
+    p = syn.ptetaphim(g, 300)
+    cart = orc.to_cartesian_def(p)
+    legs = p.copy()
+    legs[:, 3] = cart[:, 3]  # on-shell energies of the PtEtaPhiM draws
+    out = orc.to_pxpypze_def(legs, "ptetaphie")
+    for i in range(0, 300, 7):
+        ref = _mp_ptetaphie_leg(mp, legs[i])
+        for c in range(4):
+            assert abs(out[i, c] - float(ref[c])) <= 2.0 ** -53 * abs(float(ref[c])) + 1e-300
+    assert np.array_equal(orc.to_pxpypze_def(p, "ptetaphim"), cart)
+    a, b = legs[:150], legs[150:].copy()
+    b[:40, 1] = a[:40, 1] + 1e-7  # near-collinear
+    b[:40, 2] = a[:40, 2]
+    m = orc.mass_cart_def(a, b, "ptetaphie")
+    for i in range(0, 150, 3):
+        va, vb = _mp_ptetaphie_leg(mp, a[i]), _mp_ptetaphie_leg(mp, b[i])
+        w = [va[k] + vb[k] for k in range(4)]
+        m2 = w[3] ** 2 - (w[0] ** 2 + w[1] ** 2 + w[2] ** 2)
+        ref = mp.sqrt(m2) if m2 >= 0 else -mp.sqrt(-m2)
+        assert abs(m[i] - float(ref)) <= 1e-15 * abs(float(ref)) + 1e-300, i
+
+
+def test_ptetaphie_mass_closed_forms(orc):
+    """Back-to-back legs of equal pt and opposite eta (p1 + p2 = 0 up to the rounding of pi) have
+    m = E1 + E2; equal legs have m = 2 sqrt(E^2 - pt^2 cosh^2 eta); a common rotation in phi and
+    a common sign flip of eta leave every mass unchanged; on-shell PtEtaPhiE legs give the
+    PtEtaPhiM pair mass where the pair is well conditioned."""
+    g = syn.rng(191)
+    pt, eta, phi = g.uniform(1, 100, 50), g.uniform(-3, 3, 50), g.uniform(-3, 3, 50)
+    E1, E2 = pt * np.cosh(eta) * 1.5, pt * np.cosh(eta) * 2.0
+    a = np.stack([pt, eta, phi, E1], axis=1)
+    b = np.stack([pt, -eta, np.where(phi > 0, phi - np.pi, phi + np.pi), E2], axis=1)
+    m = orc.mass_cart_def(a, b, "ptetaphie")
+    assert np.all(np.abs(m - (E1 + E2)) <= 1e-14 * (E1 + E2))
+    m_eq = orc.mass_cart_def(a, a, "ptetaphie")
+    want = 2 * pt * np.cosh(eta) * np.sqrt(1.5 ** 2 - 1)
+    assert np.all(np.abs(m_eq - want) <= 1e-14 * want)
+    p = syn.ptetaphim(g, 400)
+    legs = p.copy()
+    legs[:, 3] = orc.to_cartesian_def(p)[:, 3]
+    a, b = legs[:200], legs[200:]
+    m = orc.mass_cart_def(a, b, "ptetaphie")
+    ar, br = a.copy(), b.copy()
+    ar[:, 2] = np.mod(a[:, 2] + 0.7 + np.pi, 2 * np.pi) - np.pi
+    br[:, 2] = np.mod(b[:, 2] + 0.7 + np.pi, 2 * np.pi) - np.pi
+    ar[:, 1], br[:, 1] = -a[:, 1], -b[:, 1]
+    assert np.all(np.abs(orc.mass_cart_def(ar, br, "ptetaphie") - m) <= 1e-12 * m)
+    mm = orc.mass_def(p[:200], p[200:])
+    assert np.all(np.abs(m - mm) <= 1e-12 * mm)
