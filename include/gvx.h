@@ -68,7 +68,7 @@ typedef enum { GVX_F64 = 0, GVX_F32 = 1 } gvx_dtype;
 typedef enum { GVX_SOA = 0, GVX_AOS = 1 } gvx_layout;
 /* 4-D coordinate systems of a Lorentz-vector array (the component order of an AoS struct or of
  * the four SoA arrays). */
-typedef enum { GVX_PTETAPHIM = 0, GVX_PXPYPZE = 1, GVX_PXPYPZM = 2 } gvx_coords;
+typedef enum { GVX_PTETAPHIM = 0, GVX_PXPYPZE = 1, GVX_PXPYPZM = 2, GVX_PTETAPHIE = 3 } gvx_coords;
 
 typedef struct {
   void *c[4];     /* see "Layout of a Lorentz-vector array" above */
@@ -122,9 +122,9 @@ gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, g
                      int64_t n, int32_t dtype, void *stream);
 
 /*
- * Pair masses of Cartesian legs: m[i] = mass(a[i] + b[i]) for coords GVX_PXPYPZE (components
- * px, py, pz, E) or GVX_PXPYPZM (px, py, pz, m; E = sqrt(|p|^2 + m^2)) -- the invariant mass of
- * Sec. 4.1 on the other 4-D coordinate systems of Sec. 3.1.  A spacelike sum gives -sqrt of
+ * Pair masses of legs in the other 4-D coordinate systems of Sec. 3.1 (the invariant mass of
+ * Sec. 4.1): m[i] = mass(a[i] + b[i]) for coords GVX_PXPYPZE (components px, py, pz, E),
+ * GVX_PXPYPZM (px, py, pz, m; E = sqrt(|p|^2 + m^2)) or GVX_PTETAPHIE (pt, eta, phi, E).  A spacelike sum gives -sqrt of
  * |E^2 - |P|^2| (GenVector's convention).  PxPyPzE: the definition evaluated exactly in
  * fixed-point integers (every component truncated to 2^-83 of the pair's largest), within 2^-44
  * relative; PxPyPzM: p1 x p2, p1.p2, |p_i|^2 and m_i^2 in fixed point at each leg's own scale and
@@ -133,11 +133,27 @@ gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, g
  * two within 2x of its largest component), or outside the fixed-point range, take a
  * cancellation-free FP64 form (an FMA-exact cross product and E^2 - |p|^2): within 1e-12
  * relative for legs with E^2 >= |p|^2.  FP32 legs go through the same evaluations and are rounded
- * once.  Layouts and alignment as gvx_invariant_mass; coords GVX_PTETAPHIM is
- * gvx_invariant_mass itself.
+ * once.  PtEtaPhiE: both legs converted to PxPyPzE as gvx_to_pxpypze does, then the exact
+ * fixed-point mass of the converted legs (the FP64 form outside its domain); since E_i^2 - |p_i|^2
+ * is not a stored number the error is stated normwise: |m|m| - m_ref|m_ref|| <= 2^-40 (M1 + M2)^2
+ * with M_i = max(|E_i|, pt_i cosh(eta_i)) (FP32: 2^-19).  Layouts and alignment as
+ * gvx_invariant_mass; coords GVX_PTETAPHIM is gvx_invariant_mass itself.
  */
 gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n,
                                    int32_t coords, int32_t dtype, void *stream);
+
+/*
+ * Conversion to PxPyPzE (Sec. 3.1: every 4-D coordinate system maps to the Cartesian one), so that
+ * gvx_boost and gvx_lorentz_apply take vectors given in any of them: out[i] = (px, py, pz, E) of
+ * v[i] for coords GVX_PTETAPHIM (px = pt cos phi, py = pt sin phi, pz = pt sinh eta,
+ * E = sqrt((pt cosh eta)^2 + m^2)), GVX_PTETAPHIE (the same momentum, E as stored) or GVX_PXPYPZM
+ * (E = sqrt(|p|^2 + m^2)).  FP64: float-float with table-driven functions, each component within
+ * 2^-43 max(|E|, |p|) of the exact conversion; pt < 0, |eta| >= 16, |phi| > pi, zero scales and
+ * non-finite values take FP64 formulas.  FP32: CUDA's float functions.  Layouts as gvx_boost;
+ * coords GVX_PXPYPZE is refused (GVX_ERR_ARG): there is nothing to convert.
+ */
+gvx_status gvx_to_pxpypze(const gvx_lv *v, gvx_lv *out, int64_t n, int32_t coords, int32_t dtype,
+                          void *stream);
 
 /*
  * A general 4-D Lorentz transformation (Sec. 4.1: 4x4 matrices applied to every vector of an

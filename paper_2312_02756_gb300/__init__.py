@@ -24,7 +24,8 @@ from ._lib import AOS, F32, F64, SOA, GvxError, LV
 __all__ = [
     "invariant_mass", "boost", "event_pair_masses", "EventPairMassesGraph",
     "autotune_event_pair_masses", "device_status", "check_device_status", "GvxError",
-    "load_library", "library_path", "version",
+    "load_library", "library_path", "version", "event_pair_masses_bwd", "event_pair_select",
+    "invariant_mass_cart", "lorentz_apply", "to_pxpypze",
 ]
 
 
@@ -140,13 +141,14 @@ def invariant_mass(a: torch.Tensor, b: torch.Tensor, layout_a=None, layout_b=Non
 
 # ---------------------------------------------------------------------------------------- boost
 
-_COORDS = {"pxpypze": 1, "pxpypzm": 2}
+_COORDS = {"ptetaphim": 0, "pxpypze": 1, "pxpypzm": 2, "ptetaphie": 3}
 
 
 def invariant_mass_cart(a: torch.Tensor, b: torch.Tensor, coords: str = "pxpypze",
                         layout_a=None, layout_b=None) -> torch.Tensor:
-    """Pair masses of Cartesian legs (gvx_invariant_mass_cart): coords 'pxpypze' (E stored) or
-    'pxpypzm' (m stored), FP64 or FP32, SoA or AoS like invariant_mass."""
+    """Pair masses of legs in another coordinate system (gvx_invariant_mass_cart): coords
+    'pxpypze' (E stored), 'pxpypzm' (m stored) or 'ptetaphie' (pt, eta, phi, E), FP64 or FP32,
+    SoA or AoS like invariant_mass."""
     _require_cuda(a, b)
     la, lb = _layout_of(a, 4, layout_a), _layout_of(b, 4, layout_b)
     if a.dtype != b.dtype:
@@ -160,6 +162,19 @@ def invariant_mass_cart(a: torch.Tensor, b: torch.Tensor, coords: str = "pxpypze
         _COORDS[coords], _dtype_code(a), _stream())
     _lib.check(st, "gvx_invariant_mass_cart")
     return m
+
+
+def to_pxpypze(v: torch.Tensor, coords: str, layout=None) -> torch.Tensor:
+    """Vectors in coords 'ptetaphim', 'ptetaphie' or 'pxpypzm' converted to PxPyPzE
+    (gvx_to_pxpypze), same shape and layout; the input of boost and lorentz_apply."""
+    _require_cuda(v)
+    lv = _layout_of(v, 4, layout)
+    n = _count(v, lv)
+    out = torch.empty_like(v)
+    st = load_library().gvx_to_pxpypze(ctypes.byref(_lv(v, lv, 4)), ctypes.byref(_lv(out, lv, 4)),
+                                       n, _COORDS[coords], _dtype_code(v), _stream())
+    _lib.check(st, "gvx_to_pxpypze")
+    return out
 
 
 def lorentz_apply(L: torch.Tensor, v: torch.Tensor, layout=None) -> torch.Tensor:

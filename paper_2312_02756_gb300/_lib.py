@@ -18,7 +18,7 @@ STATUS_NAMES = {
 }
 F64, F32 = 0, 1
 SOA, AOS = 0, 1
-PTETAPHIM, PXPYPZE, PXPYPZM = 0, 1, 2
+PTETAPHIM, PXPYPZE, PXPYPZM, PTETAPHIE = 0, 1, 2, 3
 
 # Every symbol include/gvx.h declares (the CPU tests check the library exports all of them).
 EXPORTS = (
@@ -32,7 +32,7 @@ EXPORTS = (
     "gvx_graph_launch", "gvx_graph_destroy", "gvx_device_status",
     "gvx_testing_skip_first_tile", "gvx_event_pair_masses_noalloc",
     "gvx_event_pair_masses_bwd", "gvx_event_pair_select",
-    "gvx_invariant_mass_cart", "gvx_lorentz_apply",
+    "gvx_invariant_mass_cart", "gvx_lorentz_apply", "gvx_to_pxpypze",
 )
 
 
@@ -88,6 +88,7 @@ def _sigs(lib):
         "gvx_event_pair_masses_bwd": ([LVP, P, P, I64, I64, P, I64, LVP, LVP, P], S),
         "gvx_invariant_mass_cart": ([LVP, LVP, P, I64, I32, I32, P], S),
         "gvx_lorentz_apply": ([P, I64, LVP, LVP, I64, I32, P], S),
+        "gvx_to_pxpypze": ([LVP, LVP, I64, I32, I32, P], S),
         "gvx_event_pair_select": ([LVP, P, I64, I64, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, I32, ctypes.c_double, P, P,
                                    P, P], S),

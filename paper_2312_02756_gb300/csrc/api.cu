@@ -218,7 +218,7 @@ gvx_status gvx_invariant_mass(const gvx_lv *a, const gvx_lv *b, void *m, int64_t
 gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n,
                                    int32_t coords, int32_t dtype, void *stream) {
   if (coords == GVX_PTETAPHIM) return gvx_invariant_mass(a, b, m, n, dtype, stream);
-  if (coords != GVX_PXPYPZE && coords != GVX_PXPYPZM) return GVX_ERR_ARG;
+  if (coords != GVX_PXPYPZE && coords != GVX_PXPYPZM && coords != GVX_PTETAPHIE) return GVX_ERR_ARG;
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
   if (n == 0) return GVX_OK;
@@ -228,6 +228,18 @@ gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, in
   if ((uintptr_t)m % scalar_size(dtype)) return GVX_ERR_ALIGN;
   return from_cuda(gvx::launch_mass_cart(gvx::as_in(*a), gvx::as_in(*b), m, n, coords, dtype,
                                          (cudaStream_t)stream));
+}
+
+gvx_status gvx_to_pxpypze(const gvx_lv *v, gvx_lv *out, int64_t n, int32_t coords, int32_t dtype,
+                          void *stream) {
+  if (coords != GVX_PTETAPHIM && coords != GVX_PTETAPHIE && coords != GVX_PXPYPZM) return GVX_ERR_ARG;
+  if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
+  if (n < 0) return GVX_ERR_SIZE;
+  if (n == 0) return GVX_OK;
+  GVX_TRY(check_lv(v, dtype, 4));
+  GVX_TRY(check_lv(out, dtype, 4));
+  return from_cuda(gvx::launch_to_pxpypze(gvx::as_in(*v), gvx::as_out(*out), n, coords, dtype,
+                                          (cudaStream_t)stream));
 }
 
 gvx_status gvx_lorentz_apply(const void *L, int64_t l_stride, const gvx_lv *v, gvx_lv *out,

@@ -7,6 +7,10 @@
 // their domain take the cancellation-free FP64 form of cart_mass.cuh (an FMA-exact cross product
 // and E^2 - |p|^2), on the FP64 pipe for both storage precisions.
 //
+// gvx_to_pxpypze: PtEtaPhiM, PtEtaPhiE or PxPyPzM vectors to PxPyPzE (convert_ff.cuh in FP64, the
+// float functions in FP32); PtEtaPhiE pair masses convert both legs the same way and take the
+// exact fixed-point mass of the converted legs.
+//
 // gvx_lorentz_apply: out = L v for a row-major 4x4 matrix L, shared or one per vector.  One
 // shared FP64 matrix takes the float-float row sums of apply_ff.cuh; a matrix per vector (whose
 // own 128 bytes make the launch memory-bound) and FP32 take four FMA chains per vector in the
@@ -14,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "apply_ff.cuh"
+#include "convert_ff.cuh"
 #include "cart_fixed.cuh"
 #include "cart_mass.cuh"
 #include "common.cuh"
@@ -94,34 +99,122 @@ __global__ void __launch_bounds__(256, 4) lorentz_apply_kernel(const T *__restri
       }
       st4<T, LO>(out, i, r);
     }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const V4<T> x = ld4<T, LV>(v, i);
+      T l[16];
+      if (SHARED) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) l[k] = l0[k];
+      } else if constexpr (sizeof(T) == 8) {  // 16-byte loads of the vector's own matrix
+        const double2 *q = reinterpret_cast<const double2 *>(L) + 8 * i;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const double2 t = __ldcs(q + k);
+          l[2 * k] = t.x;
+          l[2 * k + 1] = t.y;
+        }
+      } else {
+        const float4 *q = reinterpret_cast<const float4 *>(L) + 4 * i;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const float4 t = __ldcs(q + k);
+          l[4 * k] = t.x;
+          l[4 * k + 1] = t.y;
+          l[4 * k + 2] = t.z;
+          l[4 * k + 3] = t.w;
+        }
+      }
+      st4<T, LO>(out, i, apply_fma(l, x));
+    }
+  }
+}
+
+// One leg to PxPyPzE in FP64 (the float-float path, FP64 outside its domain); coords as in
+// gvx_coords.
+__device__ __forceinline__ void to_cart_f64(const V4<double> &x, int coords, const ffm::TabRef &T,
+                                            double *o) {
+  if (coords == GVX_PXPYPZM) {
+    const double xv[4] = {x.x, x.y, x.z, x.w};
+    if (!ffm::pxpypzm_to_cart(xv, o)) {
+      o[0] = x.x;
+      o[1] = x.y;
+      o[2] = x.z;
+      o[3] = sqrt(fma(x.x, x.x, fma(x.y, x.y, fma(x.z, x.z, x.w * x.w))));
+    }
     return;
   }
+  const bool e_stored = coords == GVX_PTETAPHIE;
+  if (!ffm::ptetaphi_to_cart(x.x, x.y, x.z, x.w, e_stored, T, o)) {
+    double sn, cs;
+    sincos(x.z, &sn, &cs);
+    o[0] = x.x * cs;
+    o[1] = x.x * sn;
+    o[2] = x.x * sinh(x.y);
+    o[3] = e_stored ? x.w : hypot(x.x * cosh(x.y), x.w);
+  }
+}
+
+// The same in FP32 with CUDA's float functions.
+__device__ __forceinline__ void to_cart_f32(const V4<float> &x, int coords, float *o) {
+  if (coords == GVX_PXPYPZM) {
+    o[0] = x.x;
+    o[1] = x.y;
+    o[2] = x.z;
+    o[3] = norm4df(x.x, x.y, x.z, x.w);
+    return;
+  }
+  float sn, cs;
+  sincosf(x.z, &sn, &cs);
+  o[0] = x.x * cs;
+  o[1] = x.x * sn;
+  o[2] = x.x * sinhf(x.y);
+  o[3] = coords == GVX_PTETAPHIE ? x.w : hypotf(x.x * coshf(x.y), x.w);
+}
+
+template <typename T, int LV, int LO, int COORDS>
+__global__ void __launch_bounds__(256) to_pxpypze_kernel(Lv v, LvOut out, int64_t n) {
+  __shared__ ffm::gvx_f4 s_exp[sizeof(T) == 8 ? GVX_EXP_N : 1];
+  __shared__ ffm::gvx_f4 s_trig[sizeof(T) == 8 ? GVX_TRIG_N + 1 : 1];
+  ffm::TabRef T_{nullptr, nullptr};
+  if constexpr (sizeof(T) == 8 && COORDS != GVX_PXPYPZM) T_ = ffm::stage_tables(s_exp, s_trig);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const V4<T> x = ld4<T, LV>(v, i);
-    T l[16];
-    if (SHARED) {
-#pragma unroll
-      for (int k = 0; k < 16; k++) l[k] = l0[k];
-    } else if constexpr (sizeof(T) == 8) {  // 16-byte loads of the vector's own matrix
-      const double2 *q = reinterpret_cast<const double2 *>(L) + 8 * i;
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const double2 t = __ldcs(q + k);
-        l[2 * k] = t.x;
-        l[2 * k + 1] = t.y;
-      }
+    T o[4];
+    if constexpr (sizeof(T) == 8) {
+      to_cart_f64(x, COORDS, T_, o);
     } else {
-      const float4 *q = reinterpret_cast<const float4 *>(L) + 4 * i;
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const float4 t = __ldcs(q + k);
-        l[4 * k] = t.x;
-        l[4 * k + 1] = t.y;
-        l[4 * k + 2] = t.z;
-        l[4 * k + 3] = t.w;
-      }
+      to_cart_f32(x, COORDS, o);
     }
-    st4<T, LO>(out, i, apply_fma(l, x));
+    st4<T, LO>(out, i, V4<T>{o[0], o[1], o[2], o[3]});
+  }
+}
+
+// Pair masses of PtEtaPhiE legs: both legs converted as above, then the exact fixed-point mass
+// of the converted legs (cart_fixed.cuh), the FP64 form outside its domain.
+template <typename T, int LA, int LB>
+__global__ void __launch_bounds__(256) mass_ptetaphie_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
+  __shared__ ffm::gvx_f4 s_exp[sizeof(T) == 8 ? GVX_EXP_N : 1];
+  __shared__ ffm::gvx_f4 s_trig[sizeof(T) == 8 ? GVX_TRIG_N + 1 : 1];
+  ffm::TabRef T_{nullptr, nullptr};
+  if constexpr (sizeof(T) == 8) T_ = ffm::stage_tables(s_exp, s_trig);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const V4<T> x = ld4<T, LA>(a, i), y = ld4<T, LB>(b, i);
+    T ca[4], cb[4], r;
+    if constexpr (sizeof(T) == 8) {
+      to_cart_f64(x, GVX_PTETAPHIE, T_, ca);
+      to_cart_f64(y, GVX_PTETAPHIE, T_, cb);
+    } else {
+      to_cart_f32(x, GVX_PTETAPHIE, ca);
+      to_cart_f32(y, GVX_PTETAPHIE, cb);
+    }
+    if (!cfix::mass_pxpypze(ca, cb, &r)) {
+      const double pa[4] = {ca[0], ca[1], ca[2], ca[3]}, pb[4] = {cb[0], cb[1], cb[2], cb[3]};
+      r = (T)cart::mass(pa, pb, 0);
+    }
+    st_s(m + i, r);
   }
 }
 
@@ -163,10 +256,64 @@ cudaError_t launch_apply_t(const T *L, const Lv &v, const LvOut &out, int64_t n,
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_ptetaphie_t(const Lv &a, const Lv &b, T *m, int64_t n, cudaStream_t s) {
+  const int threads = 256;
+  if (a.layout == GVX_SOA && b.layout == GVX_SOA) {
+    constexpr auto k = mass_ptetaphie_kernel<T, GVX_SOA, GVX_SOA>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  } else if (a.layout == GVX_SOA) {
+    constexpr auto k = mass_ptetaphie_kernel<T, GVX_SOA, GVX_AOS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  } else if (b.layout == GVX_SOA) {
+    constexpr auto k = mass_ptetaphie_kernel<T, GVX_AOS, GVX_SOA>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  } else {
+    constexpr auto k = mass_ptetaphie_kernel<T, GVX_AOS, GVX_AOS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int COORDS>
+cudaError_t launch_convert_t(const Lv &v, const LvOut &out, int64_t n, cudaStream_t s) {
+  const int threads = 256;
+  if (v.layout == GVX_SOA && out.layout == GVX_SOA) {
+    constexpr auto k = to_pxpypze_kernel<T, GVX_SOA, GVX_SOA, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, out, n);
+  } else if (v.layout == GVX_SOA) {
+    constexpr auto k = to_pxpypze_kernel<T, GVX_SOA, GVX_AOS, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, out, n);
+  } else if (out.layout == GVX_SOA) {
+    constexpr auto k = to_pxpypze_kernel<T, GVX_AOS, GVX_SOA, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, out, n);
+  } else {
+    constexpr auto k = to_pxpypze_kernel<T, GVX_AOS, GVX_AOS, COORDS>;
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(v, out, n);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_convert_c(const Lv &v, const LvOut &out, int64_t n, int coords, cudaStream_t s) {
+  if (coords == GVX_PTETAPHIM) return launch_convert_t<T, GVX_PTETAPHIM>(v, out, n, s);
+  if (coords == GVX_PTETAPHIE) return launch_convert_t<T, GVX_PTETAPHIE>(v, out, n, s);
+  return launch_convert_t<T, GVX_PXPYPZM>(v, out, n, s);
+}
+
 }  // namespace
+
+cudaError_t launch_to_pxpypze(const Lv &v, const LvOut &out, int64_t n, int coords, int dtype,
+                              cudaStream_t s) {
+  return dtype == GVX_F64 ? launch_convert_c<double>(v, out, n, coords, s)
+                          : launch_convert_c<float>(v, out, n, coords, s);
+}
 
 cudaError_t launch_mass_cart(const Lv &a, const Lv &b, void *m, int64_t n, int coords, int dtype,
                              cudaStream_t s) {
+  if (coords == GVX_PTETAPHIE)
+    return dtype == GVX_F64 ? launch_ptetaphie_t<double>(a, b, (double *)m, n, s)
+                            : launch_ptetaphie_t<float>(a, b, (float *)m, n, s);
   if (dtype == GVX_F64)
     return coords == GVX_PXPYPZE ? launch_cart_t<double, 0>(a, b, (double *)m, n, s)
                                  : launch_cart_t<double, 1>(a, b, (double *)m, n, s);

@@ -38,6 +38,8 @@ cudaError_t launch_boost_bwd(const Lv &v, const Lv &beta, int64_t beta_stride, c
                              const LvOut &gv, const LvOut &gbeta, int64_t n, int dtype,
                              void *ws, cudaStream_t s);
 size_t event_pairs_workspace(int64_t n_events);
+cudaError_t launch_to_pxpypze(const Lv &v, const LvOut &out, int64_t n, int coords, int dtype,
+                              cudaStream_t s);
 cudaError_t launch_mass_cart(const Lv &a, const Lv &b, void *m, int64_t n, int coords, int dtype,
                              cudaStream_t s);
 cudaError_t launch_lorentz_apply(const void *L, int64_t l_stride, const Lv &v, const LvOut &out,

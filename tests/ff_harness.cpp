@@ -9,6 +9,7 @@
 #include "../paper_2312_02756_gb300/csrc/cart_mass.cuh"
 #include "../paper_2312_02756_gb300/csrc/cart_fixed.cuh"
 #include "../paper_2312_02756_gb300/csrc/apply_ff.cuh"
+#include "../paper_2312_02756_gb300/csrc/convert_ff.cuh"
 
 using namespace gvx::ffm;
 
@@ -156,6 +157,20 @@ int64_t ffh_apply(const double *L, const double *v, int64_t n, double *out, uint
   int64_t c = 0;
   for (int64_t i = 0; i < n; i++) {
     ok[i] = apply_ff(M.l, M.r, v + 4 * i, out + 4 * i);
+    c += ok[i];
+  }
+  return c;
+}
+
+// The float-float conversion to PxPyPzE: coords 0 PtEtaPhiM, 2 PxPyPzM, 3 PtEtaPhiE (the library's
+// gvx_coords codes); p, out (n, 4); ok[i] = inside the fast path.
+int64_t ffh_convert(const double *p, int64_t n, int coords, double *out, uint8_t *ok) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = p + 4 * i;
+    double *o = out + 4 * i;
+    ok[i] = coords == 2 ? pxpypzm_to_cart(x, o)
+                        : ptetaphi_to_cart(x[0], x[1], x[2], x[3], coords == 3, tables(), o);
     c += ok[i];
   }
   return c;

@@ -506,3 +506,48 @@ def test_fixed_point_pxpypzm_mass_edges(ffh, orc):
     ref = orc.mass_cart_def(a[ok], b[ok], "pxpypzm")
     assert np.all(np.abs(m[ok] - ref) <= 2.0 ** -43 * ref)
     assert m[2] == 5.0
+
+
+def _convert(ffh, p, code):
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    out, ok = np.full(p.shape, np.nan), np.zeros(len(p), np.uint8)
+    ffh.ffh_convert(_p(p), ctypes.c_int64(len(p)), code, _p(out), _p(ok))
+    return out, ok.astype(bool)
+
+
+def conversion_scale(p, coords):
+    """max(|E|, |p|) of each row, from the stored values (the conversion's error unit)."""
+    if coords == "pxpypzm":
+        pm = np.sqrt(np.sum(p[:, :3] ** 2, axis=1))
+        return np.maximum(pm, np.sqrt(pm ** 2 + p[:, 3] ** 2))
+    pm = np.abs(p[:, 0]) * np.cosh(p[:, 1])
+    E = np.abs(p[:, 3]) if coords == "ptetaphie" else np.sqrt(pm ** 2 + p[:, 3] ** 2)
+    return np.maximum(pm, E)
+
+
+def test_ff_conversion_to_pxpypze(ffh, orc):
+    """The float-float conversion of PtEtaPhiM, PtEtaPhiE and PxPyPzM rows to PxPyPzE against the
+    binary128 conversion: every component within 2^-44 max(|E|, |p|), on the collider-like draws
+    (light/heavy mix, |eta| up to 4, on-shell and off-shell energies) and on rows at the edges of
+    the domain (negative pt, |eta| = 16, |phi| slightly beyond pi, NaN: refused)."""
+    g = syn.rng(192)
+    p = syn.ptetaphim_light_mix(g, 20000)
+    e_on = orc.to_cartesian_def(p)[:, 3]
+    pe = p.copy()
+    pe[:, 3] = e_on * g.uniform(0.999, 1.5, len(p))
+    c = syn.pxpypze(g, 20000)
+    c[:, 3] = g.uniform(0, 10, len(c))
+    for rows, coords, code in ((p, "ptetaphim", 0), (pe, "ptetaphie", 3), (c, "pxpypzm", 2)):
+        out, ok = _convert(ffh, rows, code)
+        assert ok.all(), coords
+        ref = orc.to_pxpypze_def(rows, coords)
+        err = np.max(np.abs(out - ref), axis=1) / conversion_scale(rows, coords)
+        assert err.max() <= 2.0 ** -44, (coords, np.log2(err.max()))
+    edge = np.array([[0.0, 1.0, 0.5, 2.0], [-1.0, 1.0, 0.5, 2.0], [1.0, 16.0, 0.5, 2.0],
+                     [1.0, 1.0, 3.1415927, 2.0], [1.0, np.nan, 0.5, 2.0], [1.0, 15.9, -np.pi, 0.0]])
+    out, ok = _convert(ffh, edge, 0)
+    assert ok.tolist() == [True, False, False, False, False, True]  # pt = 0 with m > 0 is fine
+    ref = orc.to_pxpypze_def(edge[ok], "ptetaphim")
+    assert np.all(np.abs(out[ok] - ref) <= 2.0 ** -44 * conversion_scale(edge[ok], "ptetaphim")[:, None])
+    _, ok = _convert(ffh, edge, 3)
+    assert not ok[0]  # E stored: a zero pt leaves no scale

@@ -188,3 +188,96 @@ def test_device_fast_paths_match_host_build(orc, tmp_path):
     hout, hok = np.empty_like(v), np.empty(n, np.uint8)
     assert ffh.ffh_apply(P(L), P(v), ctypes.c_int64(n), P(hout), P(hok)) == n
     assert np.array_equal(out, hout)
+
+
+def _conv_inputs(seed, n):
+    """PtEtaPhiM (light/heavy mix), PtEtaPhiE (energies from on-shell to 1.5x) and PxPyPzM rows."""
+    g = syn.rng(seed)
+    p = syn.ptetaphim_light_mix(g, n)
+    pe = p.copy()
+    pe[:, 3] = orc_energy(p) * g.uniform(0.999, 1.5, n)
+    c = syn.pxpypze(g, n)
+    c[:, 3] = g.uniform(0, 10, n)
+    return {"ptetaphim": p, "ptetaphie": pe, "pxpypzm": c}
+
+
+def orc_energy(p):
+    import oracle
+    return oracle.to_cartesian_def(p)[:, 3]
+
+
+def _scale(p, coords):
+    if coords == "pxpypzm":
+        pm = np.sqrt(np.sum(p[:, :3] ** 2, axis=1))
+        return np.sqrt(pm ** 2 + p[:, 3] ** 2)
+    pm = np.abs(p[:, 0]) * np.cosh(p[:, 1])
+    E = np.abs(p[:, 3]) if coords == "ptetaphie" else np.sqrt(pm ** 2 + p[:, 3] ** 2)
+    return np.maximum(pm, E)
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+def test_to_pxpypze(orc, layout):
+    """Conversion of PtEtaPhiM, PtEtaPhiE and PxPyPzM vectors to PxPyPzE against the binary128
+    conversion: FP64 within 2^-43 max(|E|, |p|) per component, FP32 (CUDA's float functions, on
+    the float inputs) within 2^-20 of it."""
+    import paper_2312_02756_gb300 as gvx
+    torch = torch_cuda()
+    for coords, p in _conv_inputs(93, 50_001).items():
+        ref = orc.to_pxpypze_def(p, coords)
+        out = host(gvx.to_pxpypze(dev(p, layout), coords, layout=layout), layout)
+        err = np.max(np.abs(out - ref), axis=1) / _scale(p, coords)
+        print("FP64 %s -> PxPyPzE: %s" % (coords, summary(err)))
+        assert err.max() <= 2.0 ** -43, coords
+        p32 = syn.to_f32(p).astype(np.float64)
+        ref32 = orc.to_pxpypze_def(p32, coords)
+        out32 = host(gvx.to_pxpypze(dev(p32, layout, torch.float32), coords, layout=layout), layout)
+        err32 = np.max(np.abs(out32.astype(np.float64) - ref32), axis=1) / _scale(p32, coords)
+        assert err32.max() <= 2.0 ** -20, coords
+
+
+def test_to_pxpypze_edges_and_boost(orc):
+    """Rows outside the float-float domain (negative pt, |eta| >= 16, pt = 0 with E stored) take
+    the FP64 formulas; a PtEtaPhiM array converted and then boosted matches the binary128
+    conversion and boost within 1e-12 gamma (E + |beta| |p|) per component (the conversion's
+    error times the boost's amplification, plus the boost's own)."""
+    import paper_2312_02756_gb300 as gvx
+    torch = torch_cuda()
+    edge = np.array([[-2.0, 1.0, 0.5, 2.0], [1.0, 17.0, 0.5, 2.0], [0.0, 1.0, 0.5, 3.0],
+                     [5.0, -16.5, -3.0, 1e-3], [1.0, 0.0, 0.0, 0.0]])
+    for coords in ("ptetaphim", "ptetaphie"):
+        out = gvx.to_pxpypze(dev(edge), coords).cpu().numpy()
+        ref = orc.to_pxpypze_def(edge, coords)
+        assert np.all(np.abs(out - ref) <= 2.0 ** -43 * _scale(edge, coords)[:, None] + 1e-300)
+    g = syn.rng(94)
+    p = syn.ptetaphim(g, 20_000)
+    beta = syn.velocities(g, 20_000)
+    v = gvx.to_pxpypze(dev(p), "ptetaphim")
+    got = gvx.boost(v, torch.as_tensor(beta).cuda()).cpu().numpy()
+    vin = orc.to_pxpypze_def(p, "ptetaphim")
+    ref = orc.boost_def(vin, beta)
+    bn = np.linalg.norm(beta, axis=1)
+    scale = (vin[:, 3] + bn * np.linalg.norm(vin[:, :3], axis=1)) / np.sqrt(1 - bn * bn)
+    assert np.all(np.max(np.abs(got - ref), axis=1) <= 1e-12 * scale)
+
+
+def test_ptetaphie_mass(orc):
+    """PtEtaPhiE pair masses (both legs converted, then the exact fixed-point mass): within
+    2^-40 (M1 + M2)^2 in m|m| of the binary128 definition (M_i = max(|E_i|, pt_i cosh eta_i)),
+    FP64, AoS and SoA, random and near-collinear pairs; FP32 within 2^-19 (M1 + M2)^2."""
+    import paper_2312_02756_gb300 as gvx
+    torch = torch_cuda()
+    p = _conv_inputs(95, 40_000)["ptetaphie"]
+    a, b = p[:20_000], p[20_000:].copy()
+    b[:5000, 1] = a[:5000, 1] + 1e-6
+    b[:5000, 2] = a[:5000, 2]
+    ref = orc.mass_cart_def(a, b, "ptetaphie")
+    M = _scale(a, "ptetaphie") + _scale(b, "ptetaphie")
+    for la, lb in (("aos", "aos"), ("soa", "soa")):
+        m = _mass(a, b, "ptetaphie", la, lb)
+        err = np.abs(m * np.abs(m) - ref * np.abs(ref)) / M ** 2
+        print("FP64 ptetaphie mass, normwise in m|m|: %s" % summary(err))
+        assert err.max() <= 2.0 ** -40
+    a32, b32 = syn.to_f32(a).astype(np.float64), syn.to_f32(b).astype(np.float64)
+    ref32 = orc.mass_cart_def(a32, b32, "ptetaphie")
+    m32 = _mass(a32, b32, "ptetaphie", dtype=torch.float32).astype(np.float64)
+    assert np.max(np.abs(m32 * np.abs(m32) - ref32 * np.abs(ref32)) / M ** 2) <= 2.0 ** -19
