@@ -372,22 +372,40 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
         b[3] = torch.as_tensor(gm.uniform(0.0, 10.0, N_FULL)).cuda()
         t_cm = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass_cart(
             r(la), r(lb), P(m.data_ptr()), N_FULL, 2, 0, s)), stream, steps, warmup)
-        L = torch.as_tensor(np.array([[1.2, 0.1, 0.0, 0.5], [0.1, 1.1, 0.2, 0.0],
-                                      [0.0, 0.2, 1.3, 0.4], [0.5, 0.0, 0.4, 1.5]])).cuda()
+        # PtEtaPhiE legs (on-shell energies of the PtEtaPhiM draws): pair masses, and the
+        # conversion of one array to PxPyPzE
+        gp = syn.rng(7)
+        pe_a, pe_b = syn.ptetaphim(gp, N_FULL), syn.ptetaphim(gp, N_FULL)
+        for x in (pe_a, pe_b):
+            x[:, 3] = np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
+        a.copy_(torch.as_tensor(pe_a.T.copy()))
+        b.copy_(torch.as_tensor(pe_b.T.copy()))
+        del pe_a, pe_b
+        t_ce = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass_cart(
+            r(la), r(lb), P(m.data_ptr()), N_FULL, 3, 0, s)), stream, steps, warmup)
         o = torch.empty_like(a)
         lo = Step._lv(o, 0, 4)
-        t_l = time_loop(torch, lambda: _lib.check(lib.gvx_lorentz_apply(
-            P(L.data_ptr()), 0, r(la), r(lo), N_FULL, 0, s)), stream, steps, warmup)
+        t_cv = time_loop(torch, lambda: _lib.check(lib.gvx_to_pxpypze(
+            r(la), r(lo), N_FULL, 3, 0, s)), stream, steps, warmup)
+        L = torch.as_tensor(np.array([[1.2, 0.1, 0.0, 0.5], [0.1, 1.1, 0.2, 0.0],
+                                      [0.0, 0.2, 1.3, 0.4], [0.5, 0.0, 0.4, 1.5]])).cuda()
+        t_l = time_loop(torch, lambda: _lib.check(lib.gvx_lorentz_apply(  # on the converted vectors
+            P(L.data_ptr()), 0, r(lo), r(la), N_FULL, 0, s)), stream, steps, warmup)
         del a, b, m, o, L
         torch.cuda.empty_cache()
         res["coords"] = {
-            "workload": "FP64, 2^26 elements, SoA: pair masses of PxPyPzE legs and of PxPyPzM "
-                        "legs (masses in [0, 10]); a shared 4x4 Lorentz transformation of "
-                        "PxPyPzE vectors",
+            "workload": "FP64, 2^26 elements, SoA: pair masses of PxPyPzE legs, of PxPyPzM "
+                        "legs (masses in [0, 10]) and of PtEtaPhiE legs (on-shell); the "
+                        "PtEtaPhiE -> PxPyPzE conversion; a shared 4x4 Lorentz transformation "
+                        "of PxPyPzE vectors",
             "mass_pxpypze_ms": t_c, "mass_pxpypze_pairs_per_s": N_FULL / (t_c * 1e-3),
             "mass_pxpypze_GBps": 72 * N_FULL / (t_c * 1e-3) / 1e9,
             "mass_pxpypzm_ms": t_cm, "mass_pxpypzm_pairs_per_s": N_FULL / (t_cm * 1e-3),
             "mass_pxpypzm_GBps": 72 * N_FULL / (t_cm * 1e-3) / 1e9,
+            "mass_ptetaphie_ms": t_ce, "mass_ptetaphie_pairs_per_s": N_FULL / (t_ce * 1e-3),
+            "mass_ptetaphie_GBps": 72 * N_FULL / (t_ce * 1e-3) / 1e9,
+            "to_pxpypze_ms": t_cv, "to_pxpypze_vectors_per_s": N_FULL / (t_cv * 1e-3),
+            "to_pxpypze_GBps": 64 * N_FULL / (t_cv * 1e-3) / 1e9,
             "lorentz_apply_ms": t_l, "lorentz_apply_vectors_per_s": N_FULL / (t_l * 1e-3),
             "lorentz_apply_GBps": 64 * N_FULL / (t_l * 1e-3) / 1e9,
         }
