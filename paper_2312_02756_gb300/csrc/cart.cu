@@ -179,8 +179,12 @@ __global__ void __launch_bounds__(256) to_pxpypze_kernel(Lv v, LvOut out, int64_
   ffm::TabRef T_{nullptr, nullptr};
   if constexpr (sizeof(T) == 8 && COORDS != GVX_PXPYPZM) T_ = ffm::stage_tables(s_exp, s_trig);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const V4<T> x = ld4<T, LV>(v, i);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  V4<T> xn = {0, 0, 0, 0};
+  if (i < n) xn = ld4<T, LV>(v, i);
+  for (; i < n; i += stride) {
+    const V4<T> x = xn;  // the next vector's loads go out before this one's arithmetic
+    if (i + stride < n) xn = ld4<T, LV>(v, i + stride);
     T o[4];
     if constexpr (sizeof(T) == 8) {
       to_cart_f64(x, COORDS, T_, o);

@@ -202,3 +202,28 @@ def test_event_pairs_bounded_wait_times_out():
     assert dt < 30
     po, pm, _ = _run(p, off)
     assert po[-1] == _n_pairs(off)
+
+
+def test_sharded_shares_reassemble_the_packed_output(orc):
+    """Two shards of an event array, each run through event_pair_masses_sharded on this GPU (no
+    process group: each share is computed as its rank would, with the base of the shard before it
+    given by the same exclusive scan), reassemble the single-call pair offsets and pair masses
+    exactly."""
+    import paper_2312_02756_gb300 as gvx
+    from paper_2312_02756_gb300 import sharding
+    torch = torch_cuda()
+    g = syn.rng(302)
+    off = syn.jagged_offsets(g, 3000)
+    p = syn.ptetaphim(g, int(off[-1]))
+    po_all, pm_all, _ = _run(p, off)
+    base = 0
+    for r in range(2):
+        e_lo, e_hi, p_lo, p_hi = sharding.shard_events(off, r, 2)
+        local = off[e_lo:e_hi + 1] - off[e_lo]
+        po, pm, sums, b, grand = sharding.event_pair_masses_sharded(
+            dev(p[p_lo:p_hi]), torch.as_tensor(local).cuda())
+        assert b == 0 and grand == len(pm)  # a single process: its own share only
+        po = po.cpu().numpy() + base
+        assert np.array_equal(po, po_all[e_lo:e_hi + 1])
+        assert np.array_equal(pm.cpu().numpy(), pm_all[po[0]:po[-1]])
+        base += len(pm)
