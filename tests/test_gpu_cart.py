@@ -281,3 +281,25 @@ def test_ptetaphie_mass(orc):
     ref32 = orc.mass_cart_def(a32, b32, "ptetaphie")
     m32 = _mass(a32, b32, "ptetaphie", dtype=torch.float32).astype(np.float64)
     assert np.max(np.abs(m32 * np.abs(m32) - ref32 * np.abs(ref32)) / M ** 2) <= 2.0 ** -19
+
+
+@pytest.mark.parametrize("coords", ["pxpypze", "pxpypzm", "ptetaphie"])
+def test_cart_mass_nan_propagates_and_mixed_layouts(orc, coords):
+    """A NaN in any component of either leg gives a NaN mass (the fast paths refuse the pair and
+    the FP64 form propagates it), in FP64 and FP32; SoA against AoS legs give the same bits."""
+    import torch
+    g = syn.rng(96)
+    if coords == "ptetaphie":
+        a, b = _conv_inputs(97, 2 * 4096)["ptetaphie"][:4096], _conv_inputs(97, 2 * 4096)["ptetaphie"][4096:]
+    else:
+        a, b = _legs(98, 4096, coords)
+    rows = g.choice(4096, 64, replace=False)
+    for t, r in enumerate(rows):
+        (a if t % 2 else b)[r, t % 4] = np.nan
+    for dtype in (None, torch.float32):
+        m = _mass(a, b, coords, "soa", "aos", dtype=dtype)
+        assert np.all(np.isnan(m[rows]))
+        others = np.setdiff1d(np.arange(4096), rows)
+        assert np.all(np.isfinite(m[others]))
+        m2 = _mass(a, b, coords, "aos", "soa", dtype=dtype)
+        assert np.array_equal(np.isnan(m2), np.isnan(m)) and np.array_equal(m2[others], m[others])
