@@ -144,6 +144,13 @@ def invariant_mass(a: torch.Tensor, b: torch.Tensor, layout_a=None, layout_b=Non
 _COORDS = {"ptetaphim": 0, "pxpypze": 1, "pxpypzm": 2, "ptetaphie": 3}
 
 
+def _coords_code(coords: str) -> int:
+    try:
+        return _COORDS[coords]
+    except KeyError:
+        raise ValueError("coords must be one of %s, got %r" % (sorted(_COORDS), coords)) from None
+
+
 def invariant_mass_cart(a: torch.Tensor, b: torch.Tensor, coords: str = "pxpypze",
                         layout_a=None, layout_b=None) -> torch.Tensor:
     """Pair masses of legs in another coordinate system (gvx_invariant_mass_cart): coords
@@ -159,7 +166,7 @@ def invariant_mass_cart(a: torch.Tensor, b: torch.Tensor, coords: str = "pxpypze
     m = torch.empty(n, dtype=a.dtype, device=a.device)
     st = load_library().gvx_invariant_mass_cart(
         ctypes.byref(_lv(a, la, 4)), ctypes.byref(_lv(b, lb, 4)), ctypes.c_void_p(m.data_ptr()), n,
-        _COORDS[coords], _dtype_code(a), _stream())
+        _coords_code(coords), _dtype_code(a), _stream())
     _lib.check(st, "gvx_invariant_mass_cart")
     return m
 
@@ -172,7 +179,7 @@ def to_pxpypze(v: torch.Tensor, coords: str, layout=None) -> torch.Tensor:
     n = _count(v, lv)
     out = torch.empty_like(v)
     st = load_library().gvx_to_pxpypze(ctypes.byref(_lv(v, lv, 4)), ctypes.byref(_lv(out, lv, 4)),
-                                       n, _COORDS[coords], _dtype_code(v), _stream())
+                                       n, _coords_code(coords), _dtype_code(v), _stream())
     _lib.check(st, "gvx_to_pxpypze")
     return out
 

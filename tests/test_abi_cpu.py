@@ -107,3 +107,43 @@ def test_no_cpu_fallback_in_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"(import\s+oracle|from\s+oracle|liboracle|gvx_oracle)", src), f
+
+
+def test_coordinate_and_transformation_validation(lib):
+    """gvx_invariant_mass_cart, gvx_to_pxpypze and gvx_lorentz_apply reject bad coordinate codes,
+    dtypes, sizes, null and misaligned pointers on the host (status codes of include/gvx.h)."""
+    good = _lv(0, (64, 128, 192, 256))
+    r = ctypes.byref
+    ARG, SIZE, DTYPE, NULL, ALIGN = 11, 2, 3, 1, 5
+    # pair masses in other coordinate systems: coords 1 (PxPyPzE), 2 (PxPyPzM), 3 (PtEtaPhiE)
+    for coords in (1, 2, 3):
+        assert lib.gvx_invariant_mass_cart(r(good), r(good), 512, 0, coords, 0, None) == 0
+        assert lib.gvx_invariant_mass_cart(r(good), r(good), 512, -1, coords, 0, None) == SIZE
+        assert lib.gvx_invariant_mass_cart(r(good), r(good), None, 10, coords, 0, None) == NULL
+        assert lib.gvx_invariant_mass_cart(r(good), r(good), 516, 10, coords, 0, None) == ALIGN
+        assert lib.gvx_invariant_mass_cart(r(good), r(good), 512, 10, coords, 9, None) == DTYPE
+    assert lib.gvx_invariant_mass_cart(r(good), r(good), 512, 10, 4, 0, None) == ARG
+    assert lib.gvx_invariant_mass_cart(r(good), r(good), 512, 10, -1, 0, None) == ARG
+    # conversion: PtEtaPhiM (0), PxPyPzM (2), PtEtaPhiE (3); PxPyPzE (1) has nothing to convert
+    for coords in (0, 2, 3):
+        assert lib.gvx_to_pxpypze(r(good), r(good), 0, coords, 0, None) == 0
+        assert lib.gvx_to_pxpypze(r(good), r(good), -3, coords, 0, None) == SIZE
+        assert lib.gvx_to_pxpypze(None, r(good), 10, coords, 0, None) == NULL
+        assert lib.gvx_to_pxpypze(r(good), r(_lv(0)), 10, coords, 0, None) == NULL
+        assert lib.gvx_to_pxpypze(r(good), r(good), 10, coords, 5, None) == DTYPE
+    assert lib.gvx_to_pxpypze(r(good), r(good), 10, 1, 0, None) == ARG
+    assert lib.gvx_to_pxpypze(r(good), r(good), 10, 7, 0, None) == ARG
+    # general transformation: l_stride 0 or 1, L aligned to a scalar (shared) or 16 bytes
+    assert lib.gvx_lorentz_apply(ctypes.c_void_p(64), 2, r(good), r(good), 10, 0, None) == ARG
+    assert lib.gvx_lorentz_apply(None, 0, r(good), r(good), 10, 0, None) == NULL
+    assert lib.gvx_lorentz_apply(ctypes.c_void_p(72), 1, r(good), r(good), 10, 0, None) == ALIGN
+    assert lib.gvx_lorentz_apply(ctypes.c_void_p(68), 0, r(good), r(good), 10, 0, None) == ALIGN
+    assert lib.gvx_lorentz_apply(ctypes.c_void_p(64), 0, r(good), r(good), -1, 0, None) == SIZE
+
+
+def test_python_coordinate_names():
+    """The Python bindings name the coordinate systems; an unknown name is a ValueError."""
+    import paper_2312_02756_gb300 as gvx
+    assert gvx._coords_code("ptetaphie") == 3 and gvx._coords_code("pxpypze") == 1
+    with pytest.raises(ValueError):
+        gvx._coords_code("xyzt")
