@@ -551,3 +551,36 @@ def test_ff_conversion_to_pxpypze(ffh, orc):
     assert np.all(np.abs(out[ok] - ref) <= 2.0 ** -44 * conversion_scale(edge[ok], "ptetaphim")[:, None])
     _, ok = _convert(ffh, edge, 3)
     assert not ok[0]  # E stored: a zero pt leaves no scale
+
+
+def test_fixed_point_masses_adversarial_property(ffh, orc):
+    """Randomised adversarial legs for the fixed-point PxPyPzE and PxPyPzM masses (hypothesis):
+    components with random signs, exact zeros and exponents spread over 2^-60 .. 2^60 of each
+    other, second legs nearly collinear and nearly massless.  Wherever the fast path takes a pair
+    it is within its bound of the binary128 definition (2^-44 and 2^-43 relative)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    comp = st.tuples(st.sampled_from([-1.0, 0.0, 1.0]), st.floats(1.0, 2.0), st.integers(-60, 60))
+
+    @hyp.settings(max_examples=300, deadline=None, derandomize=True)
+    @hyp.given(st.lists(comp, min_size=4, max_size=4), st.floats(1e-12, 1e-3),
+               st.floats(-1e-6, 1e-6), st.sampled_from([0, 1]))
+    def check(c, mfrac, eps, coords):
+        a = np.array([s * m * 2.0 ** e for s, m, e in c])
+        p = a[:3]
+        pn = np.sqrt(np.sum(p * p))
+        if coords == 0:
+            a[3] = abs(a[3]) + pn  # timelike or on the light cone
+        b = a.copy()
+        b[:3] = p * (1.0 + eps)
+        b[3] = (np.sqrt(np.sum(b[:3] ** 2) + (mfrac * max(pn, 1e-300)) ** 2) if coords == 0
+                else mfrac * max(pn, abs(a[3]), 1e-300))
+        A, B = a[None, :], b[None, :]
+        m, ok, _, _ = _cart_fixed(ffh, A, B, coords)
+        if ok[0]:
+            ref = orc.mass_cart_def(A, B, ("pxpypze", "pxpypzm")[coords])[0]
+            tol = 2.0 ** -44 if coords == 0 else 2.0 ** -43
+            assert abs(m[0] - ref) <= tol * abs(ref), (a, b, m[0], ref)
+
+    check()
