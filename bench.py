@@ -383,6 +383,13 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
         del pe_a, pe_b
         t_ce = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass_cart(
             r(la), r(lb), P(m.data_ptr()), N_FULL, 3, 0, s)), stream, steps, warmup)
+        # FP32 copies of the PtEtaPhiE legs: the same pair masses in single precision
+        a32, b32 = a.float(), b.float()
+        m32 = torch.empty(N_FULL, dtype=torch.float32, device="cuda")
+        la32, lb32 = Step._lv(a32, 0, 4), Step._lv(b32, 0, 4)
+        t_ce32 = time_loop(torch, lambda: _lib.check(lib.gvx_invariant_mass_cart(
+            r(la32), r(lb32), P(m32.data_ptr()), N_FULL, 3, 1, s)), stream, steps, warmup)
+        del a32, b32, m32
         o = torch.empty_like(a)
         lo = Step._lv(o, 0, 4)
         t_cv = time_loop(torch, lambda: _lib.check(lib.gvx_to_pxpypze(
@@ -395,7 +402,7 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
         torch.cuda.empty_cache()
         res["coords"] = {
             "workload": "FP64, 2^26 elements, SoA: pair masses of PxPyPzE legs, of PxPyPzM "
-                        "legs (masses in [0, 10]) and of PtEtaPhiE legs (on-shell); the "
+                        "legs (masses in [0, 10]) and of PtEtaPhiE legs (on-shell; also in FP32); the "
                         "PtEtaPhiE -> PxPyPzE conversion; a shared 4x4 Lorentz transformation "
                         "of PxPyPzE vectors",
             "mass_pxpypze_ms": t_c, "mass_pxpypze_pairs_per_s": N_FULL / (t_c * 1e-3),
@@ -404,6 +411,8 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
             "mass_pxpypzm_GBps": 72 * N_FULL / (t_cm * 1e-3) / 1e9,
             "mass_ptetaphie_ms": t_ce, "mass_ptetaphie_pairs_per_s": N_FULL / (t_ce * 1e-3),
             "mass_ptetaphie_GBps": 72 * N_FULL / (t_ce * 1e-3) / 1e9,
+            "mass_ptetaphie_f32_ms": t_ce32,
+            "mass_ptetaphie_f32_GBps": 36 * N_FULL / (t_ce32 * 1e-3) / 1e9,
             "to_pxpypze_ms": t_cv, "to_pxpypze_vectors_per_s": N_FULL / (t_cv * 1e-3),
             "to_pxpypze_GBps": 64 * N_FULL / (t_cv * 1e-3) / 1e9,
             "lorentz_apply_ms": t_l, "lorentz_apply_vectors_per_s": N_FULL / (t_l * 1e-3),
