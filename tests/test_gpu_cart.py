@@ -303,3 +303,44 @@ def test_cart_mass_nan_propagates_and_mixed_layouts(orc, coords):
         assert np.all(np.isfinite(m[others]))
         m2 = _mass(a, b, coords, "aos", "soa", dtype=dtype)
         assert np.array_equal(np.isnan(m2), np.isnan(m)) and np.array_equal(m2[others], m[others])
+
+
+def test_coordinates_workload_full_size_sampled(orc):
+    """The benchmark's coordinate-system workload at its full size (2^26 FP64 elements, SoA, the
+    same seeded inputs as bench.py's coords form): 2^14 sampled outputs of every kernel -- the
+    PxPyPzE, PxPyPzM and PtEtaPhiE pair masses, the conversion and the shared-matrix
+    transformation -- against the oracle within each kernel's bound."""
+    import paper_2312_02756_gb300 as gvx
+    torch = torch_cuda()
+    n = 1 << 26
+    idx = np.sort(syn.rng(187).choice(n, 1 << 14, replace=False))
+    g = syn.rng(5)
+    a, b = syn.pxpypze(g, n), syn.pxpypze(g, n)
+    m = gvx.invariant_mass_cart(dev(a, "soa"), dev(b, "soa"), "pxpypze", "soa", "soa").cpu().numpy()
+    ref = orc.mass_cart_def(a[idx], b[idx], "pxpypze")
+    assert np.max(np.abs(m[idx] - ref) / np.abs(ref)) <= 2.0 ** -44
+    gm = syn.rng(6)
+    a[:, 3], b[:, 3] = gm.uniform(0.0, 10.0, n), gm.uniform(0.0, 10.0, n)
+    m = gvx.invariant_mass_cart(dev(a, "soa"), dev(b, "soa"), "pxpypzm", "soa", "soa").cpu().numpy()
+    ref = orc.mass_cart_def(a[idx], b[idx], "pxpypzm")
+    assert np.max(np.abs(m[idx] - ref) / np.abs(ref)) <= 2.0 ** -43
+    del a, b, m
+    torch.cuda.empty_cache()
+    gp = syn.rng(7)
+    pa, pb = syn.ptetaphim(gp, n), syn.ptetaphim(gp, n)
+    for x in (pa, pb):
+        x[:, 3] = np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
+    m = gvx.invariant_mass_cart(dev(pa, "soa"), dev(pb, "soa"), "ptetaphie", "soa", "soa").cpu().numpy()
+    ref = orc.mass_cart_def(pa[idx], pb[idx], "ptetaphie")
+    M = _scale(pa[idx], "ptetaphie") + _scale(pb[idx], "ptetaphie")
+    assert np.max(np.abs(m[idx] * np.abs(m[idx]) - ref * np.abs(ref)) / M ** 2) <= 2.0 ** -40
+    vd = gvx.to_pxpypze(dev(pa, "soa"), "ptetaphie", layout="soa")
+    v = host(vd, "soa")
+    ref = orc.to_pxpypze_def(pa[idx], "ptetaphie")
+    assert np.max(np.max(np.abs(v[idx] - ref), axis=1) / _scale(pa[idx], "ptetaphie")) <= 2.0 ** -43
+    L = np.array([[1.2, 0.1, 0.0, 0.5], [0.1, 1.1, 0.2, 0.0], [0.0, 0.2, 1.3, 0.4], [0.5, 0.0, 0.4, 1.5]])
+    w = host(gvx.lorentz_apply(torch.as_tensor(L).cuda(), vd, layout="soa"), "soa")
+    ref = orc.lorentz_apply_def(L, v[idx])
+    assert np.all(np.abs(w[idx] - ref) <= _apply_bound(L, v[idx], True))
+    del pa, pb, m, v, vd, w
+    torch.cuda.empty_cache()
