@@ -72,11 +72,9 @@ GVX_HD bool boost_ff(const BetaFF &B, double bx, double by, double bz, double px
 // k' = dk/dgamma = gamma (gamma + 2)/(gamma + 1)^2 (so k' - 1 = -(s w)^2):
 //   grad_beta = A beta + B p + f grad_p,
 //   A = gamma^3 [gb (t + (k' - 1) bp) + gE t],   B = k gb + gamma gE,   f = k t + w E.
-// bp, t, gb and tg are FP64 (the sums that can cancel: the boost's condition number multiplies
-// only their rounding), and so is gamma tg; A, B, f, the boost of grad_out and the combinations
-// with beta, p and grad_p are float-float on the scaled inputs, every product of a combination
-// at one scale (2^(sv + sq) for grad_beta, 2^sq for grad_v), and return to double by integer
-// operations: 9 FP64 operations per vector, the FP64 pipe being the scarce one.
+// bp, t, gb and tg are FP64 (the sums that can cancel); A, B, f and the boost of grad_out are
+// formed in ff from the scaled inputs and return to double by integer operations; the
+// combinations with beta, p and grad_p are FP64 multiply-adds: 21 FP64 operations per vector.
 
 struct BetaBwdFF {
   ff gf, w, k, kpm1, g3;  // gamma, 1/(1 + s), gamma w, k' - 1, gamma^3
@@ -127,19 +125,18 @@ GVX_HD bool boost_bwd_ff(const BetaBwdFF &B, double bx, double by, double bz, co
   const ff En = from_double_ranged(p[3], sv);
   const ff TG = from_double_ranged(tg, sq), GB = from_double_ranged(gb, sq);
   const ff GE = from_double_ranged(q[3], sq);
-  const ff F = add(mul(B.k, T), mul(B.w, En));     // f, scale 2^sv
-  const ff FQ = add(mul(B.k, TG), mul(B.w, GE));   // f of grad_out, scale 2^sq
-  const ff A = mul(B.g3, add(mul(GB, add(T, mul(B.kpm1, BP))), mul(GE, T)));  // scale 2^(sv + sq)
-  const ff BQ = add(mul(B.k, GB), mul(B.gf, GE));  // scale 2^sq
-  const double bv[3] = {bx, by, bz};
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    const ff bc = from_double_ranged(bv[c], 0);  // |beta_c| < 1
-    const ff pc = from_double_ranged(p[c], sv), qc = from_double_ranged(q[c], sq);
-    gv[c] = to_double_int(renorm(add(mul(FQ, bc), qc)), sq);
-    gbeta[c] = to_double_int(renorm(add(add(mul(A, bc), mul(BQ, pc)), mul(F, qc))), sv + sq);
-  }
+  const double f = to_double_int(add(mul(B.k, T), mul(B.w, En)), sv);
+  const double fq = to_double_int(add(mul(B.k, TG), mul(B.w, GE)), sq);
+  const ff A = mul(B.g3, add(mul(GB, add(T, mul(B.kpm1, BP))), mul(GE, T)));
+  const double a = to_double_int(renorm(A), sv + sq);
+  const double bq = to_double_int(add(mul(B.k, GB), mul(B.gf, GE)), sq);
+  gv[0] = fma(fq, bx, q[0]);
+  gv[1] = fma(fq, by, q[1]);
+  gv[2] = fma(fq, bz, q[2]);
   gv[3] = B.g * tg;
+  gbeta[0] = fma(a, bx, fma(bq, p[0], f * q[0]));
+  gbeta[1] = fma(a, by, fma(bq, p[1], f * q[1]));
+  gbeta[2] = fma(a, bz, fma(bq, p[2], f * q[2]));
   return true;
 }
 
