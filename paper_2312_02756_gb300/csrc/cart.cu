@@ -8,8 +8,9 @@
 // and E^2 - |p|^2), on the FP64 pipe for both storage precisions.
 //
 // gvx_to_pxpypze: PtEtaPhiM, PtEtaPhiE or PxPyPzM vectors to PxPyPzE (convert_ff.cuh in FP64, the
-// float functions in FP32); PtEtaPhiE pair masses convert both legs the same way and take the
-// exact fixed-point mass of the converted legs.
+// float functions in FP32).  PtEtaPhiE pair masses: in FP64 the float-float identity of
+// ptetaphie_ff.cuh; otherwise both legs converted the same way and the exact fixed-point mass of
+// the converted legs.
 //
 // gvx_lorentz_apply: out = L v for a row-major 4x4 matrix L, shared or one per vector.  One
 // shared FP64 matrix takes the float-float row sums of apply_ff.cuh; a matrix per vector (whose
@@ -19,6 +20,7 @@
 
 #include "apply_ff.cuh"
 #include "convert_ff.cuh"
+#include "ptetaphie_ff.cuh"
 #include "cart_fixed.cuh"
 #include "cart_mass.cuh"
 #include "common.cuh"
@@ -195,8 +197,9 @@ __global__ void __launch_bounds__(256) to_pxpypze_kernel(Lv v, LvOut out, int64_
   }
 }
 
-// Pair masses of PtEtaPhiE legs: both legs converted as above, then the exact fixed-point mass
-// of the converted legs (cart_fixed.cuh), the FP64 form outside its domain.
+// Pair masses of PtEtaPhiE legs.  FP64: the float-float identity of ptetaphie_ff.cuh; outside its
+// domain (and in FP32) both legs converted as above, then the exact fixed-point mass of the
+// converted legs (cart_fixed.cuh), the FP64 form outside that one's domain.
 template <typename T, int LA, int LB>
 __global__ void __launch_bounds__(256) mass_ptetaphie_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
   __shared__ ffm::gvx_f4 s_exp[sizeof(T) == 8 ? GVX_EXP_N : 1];
@@ -208,6 +211,11 @@ __global__ void __launch_bounds__(256) mass_ptetaphie_kernel(Lv a, Lv b, T *__re
     const V4<T> x = ld4<T, LA>(a, i), y = ld4<T, LB>(b, i);
     T ca[4], cb[4], r;
     if constexpr (sizeof(T) == 8) {
+      double rf;
+      if (ffm::pair_mass_e_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T_, &rf)) {
+        st_s(m + i, rf);  // the float-float identity (ptetaphie_ff.cuh)
+        continue;
+      }
       to_cart_f64(x, GVX_PTETAPHIE, T_, ca);
       to_cart_f64(y, GVX_PTETAPHIE, T_, cb);
     } else {

@@ -10,6 +10,7 @@
 #include "../paper_2312_02756_gb300/csrc/cart_fixed.cuh"
 #include "../paper_2312_02756_gb300/csrc/apply_ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/convert_ff.cuh"
+#include "../paper_2312_02756_gb300/csrc/ptetaphie_ff.cuh"
 
 using namespace gvx::ffm;
 
@@ -171,6 +172,19 @@ int64_t ffh_convert(const double *p, int64_t n, int coords, double *out, uint8_t
     double *o = out + 4 * i;
     ok[i] = coords == 2 ? pxpypzm_to_cart(x, o)
                         : ptetaphi_to_cart(x[0], x[1], x[2], x[3], coords == 3, tables(), o);
+    c += ok[i];
+  }
+  return c;
+}
+
+// The float-float PtEtaPhiE pair mass: a, b (n, 4) rows (pt, eta, phi, E); ok[i] = fast path.
+int64_t ffh_mass_e(const double *a, const double *b, int64_t n, double *m, uint8_t *ok) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = a + 4 * i, *y = b + 4 * i;
+    double out = NAN;
+    ok[i] = pair_mass_e_ff(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], tables(), &out);
+    m[i] = out;
     c += ok[i];
   }
   return c;
