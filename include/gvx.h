@@ -133,10 +133,12 @@ gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, g
  * two within 2x of its largest component), or outside the fixed-point range, take a
  * cancellation-free FP64 form (an FMA-exact cross product and E^2 - |p|^2): within 1e-12
  * relative for legs with E^2 >= |p|^2.  FP32 legs go through the same evaluations and are rounded
- * once.  PtEtaPhiE: both legs converted to PxPyPzE as gvx_to_pxpypze does, then the exact
- * fixed-point mass of the converted legs (the FP64 form outside its domain); since E_i^2 - |p_i|^2
- * is not a stored number the error is stated normwise: |m|m| - m_ref|m_ref|| <= 2^-40 (M1 + M2)^2
- * with M_i = max(|E_i|, pt_i cosh(eta_i)) (FP32: 2^-19).  Layouts and alignment as
+ * once.  PtEtaPhiE: in FP64 the PtEtaPhiM identity with q_i = E_i^2 - (pt_i cosh eta_i)^2 in
+ * float-float; outside its domain (negative E, m^2 below 2^-80 of the scale, spacelike sums) and
+ * in FP32, both legs converted to PxPyPzE as gvx_to_pxpypze does and the exact fixed-point mass of
+ * the converted legs (the FP64 form outside that one's domain).  Since E_i^2 - |p_i|^2 is not a
+ * stored number the error is stated normwise: |m|m| - m_ref|m_ref|| <= 2^-40 (M1 + M2)^2 with
+ * M_i = max(|E_i|, pt_i cosh(eta_i)) (FP32: 2^-19).  Layouts and alignment as
  * gvx_invariant_mass; coords GVX_PTETAPHIM is gvx_invariant_mass itself.
  */
 gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n,
