@@ -7,8 +7,13 @@
  *   - ApplyBoost (Sec. 4.1): a Lorentz boost, held in the paper as a 4x4 matrix, applied to
  *     every vector of a PxPyPzE array.
  *   - The jagged per-event form (all pair masses and the summed 4-vector of each event) serves
- *     the RDataFrame-style analyses named as the next target in Sec. 6.
- *   - The *_bwd entry points are the adjoints (vector-Jacobian products) of the above.
+ *     the RDataFrame-style analyses named as the next target in Sec. 6, and so does the fused
+ *     per-event selection, pair-mass histogram and best candidate.
+ *   - The other 4-D coordinate systems of Sec. 3.1 as inputs: pair masses of PxPyPzE, PxPyPzM
+ *     and PtEtaPhiE legs, and the conversion of PtEtaPhiM, PtEtaPhiE and PxPyPzM vectors to
+ *     PxPyPzE (the input of the boost); a general 4x4 Lorentz transformation (Sec. 4.1).
+ *   - The *_bwd entry points are the adjoints (vector-Jacobian products) of the mass, the boost
+ *     and the jagged form.
  *
  * Conventions shared by every entry point
  *   Memory:  every pointer is caller-owned memory that the GPU can address: device memory
