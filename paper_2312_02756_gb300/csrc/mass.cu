@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "mass_ff.cuh"
+#include "mass_ff2.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
@@ -55,8 +56,8 @@ __global__ void __launch_bounds__(256) mass_f64_kernel(Lv a, Lv b, double *__res
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     V4<double> x = ld4<double, LA>(a, i);
     V4<double> y = ld4<double, LB>(b, i);
-    double out;
-    if (!ffm::pair_mass_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T, &out))
+    double out;  // the two legs on paired FP32 instructions (mass_ff2.cuh): the same bits
+    if (!ffm::pair_mass_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T, &out))
       out = sqrt(pair_terms(make_leg(x), make_leg(y)).m2);
     st_s(m + i, out);
   }

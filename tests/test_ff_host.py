@@ -613,3 +613,30 @@ def test_ff_ptetaphie_mass_against_oracle(ffh, orc):
     m2, ok2 = np.empty(4), np.zeros(4, np.uint8)
     ffh.ffh_mass_e(_p(neg), _p(np.ascontiguousarray(b[:4])), ctypes.c_int64(4), _p(m2), _p(ok2))
     assert not ok2.any()
+
+
+def test_leg_paired_pair_mass_is_bit_identical(ffh):
+    """The pair mass with its two legs on paired FP32 operations (the FP64 kernel's path) gives the
+    scalar pair_mass_ff's bits, and takes the same pairs, on the collider-like draws, the
+    light/heavy mix, near-collinear pairs, azimuthal wrap-around, negative and zero eta and tiny
+    masses."""
+    g = syn.rng(194)
+    n = 40000
+    a = syn.ptetaphim_light_mix(g, n)
+    b = syn.ptetaphim_light_mix(g, n)
+    k = n // 4
+    b[:k, 1] = a[:k, 1] + g.uniform(-1e-7, 1e-7, k)
+    b[:k, 2] = a[:k, 2] + g.uniform(-1e-7, 1e-7, k)
+    b[k:2 * k, 2] = np.where(a[k:2 * k, 2] > 0, a[k:2 * k, 2] - 3.1, a[k:2 * k, 2] + 3.1)
+    b[2 * k:2 * k + 500, 3] = 0.0
+    a[2 * k + 500:2 * k + 1000, 3] = a[2 * k + 500:2 * k + 1000, 0] * 2.0 ** -29
+    a[2 * k + 1000:2 * k + 1500, 1] = 0.0
+    b[2 * k + 1000:2 * k + 1250, 1] = -a[2 * k + 1000:2 * k + 1250, 1]
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    m1, ok1 = _mass(ffh, a, b)
+    assert ok1.mean() > 0.99
+    m3, ok3 = np.empty(n), np.zeros(n, np.uint8)
+    ffh.ffh_mass_lp(_p(a), _p(b), ctypes.c_int64(n), _p(m3), _p(ok3))
+    ok3 = ok3.astype(bool)
+    assert np.array_equal(ok3, ok1)
+    assert np.array_equal(m1[ok1].view(np.uint64), m3[ok1].view(np.uint64))
