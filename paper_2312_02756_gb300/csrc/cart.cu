@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(256) mass_ptetaphie_kernel(Lv a, Lv b, T *__re
     T ca[4], cb[4], r;
     if constexpr (sizeof(T) == 8) {
       double rf;
-      if (ffm::pair_mass_e_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T_, &rf)) {
-        st_s(m + i, rf);  // the float-float identity (ptetaphie_ff.cuh)
+      if (ffm::pair_mass_e_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T_, &rf)) {
+        st_s(m + i, rf);  // the float-float identity, legs paired (ptetaphie_ff.cuh)
         continue;
       }
       to_cart_f64(x, GVX_PTETAPHIE, T_, ca);

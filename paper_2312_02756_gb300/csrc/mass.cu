@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "mass_ff.cuh"
 #include "mass_ff2.cuh"
+#include "mass_grad_ff2.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
@@ -98,8 +99,8 @@ cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaSt
   return cudaGetLastError();
 }
 
-// FP64 adjoint: float-float evaluation (mass_ff.cuh, pair_mass_grad_ff) with the FP64 formulas
-// kept for lanes outside its domain.
+// FP64 adjoint: float-float evaluation (mass_ff.cuh, pair_mass_grad_ff; the two legs on paired
+// FP32 instructions, mass_grad_ff2.cuh) with the FP64 formulas kept for lanes outside its domain.
 template <int LA, int LB, int LGA, int LGB>
 __global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ gm,
                                                            LvOut ga, LvOut gb, int64_t n) {
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const 
     double g = ld_s(gm + i);
     double o[8];
     V4<double> g1, g2;
-    if (ffm::pair_mass_grad_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
+    if (ffm::pair_mass_grad_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
       g1 = {o[0], o[1], o[2], o[3]};
       g2 = {o[4], o[5], o[6], o[7]};
     } else {

@@ -14,6 +14,7 @@
 #pragma once
 
 #include "mass_ff.cuh"
+#include "mass_ff2.cuh"
 
 namespace gvx {
 namespace ffm {
@@ -37,6 +38,33 @@ GVX_HD bool pair_mass_e_ff(double pt1, double eta1, double phi1, double E1, doub
   const LegFF a = make_leg_e_ff(pt1, eta1, E1, s, T);
   const LegFF b = make_leg_e_ff(pt2, eta2, E2, s, T);
   return finish_mass(pair_m2_ff(a, b, eta1, eta2, phi1, phi2, T, &ok), s, ok, out);
+}
+
+// add of ff.cuh per lane (accurate under cancellation)
+GVX_HD ff2 add(const ff2 &x, const ff2 &y) {
+  ff2 s = two_sum2(x.hi, y.hi);
+  const ff2 t = two_sum2(x.lo, y.lo);
+  s = fast_two_sum2(s.hi, add2(s.lo, t.hi));
+  return fast_two_sum2(s.hi, add2(s.lo, t.lo));
+}
+
+// pair_mass_e_ff with both legs (make_leg_e_ff) in one sequence of paired FP32 operations
+// (mass_ff2.cuh; lane x leg 1, lane y leg 2): the same bits, the same domain.
+GVX_HD bool pair_mass_e_ff_lp(double pt1, double eta1, double phi1, double e1, double pt2,
+                              double eta2, double phi2, double e2, const TabRef &T, double *out) {
+  if ((dhi(e1) | dhi(e2)) >> 31) return false;  // a negative (or -0) energy
+  int s;
+  if (!mass_ff_domain(pt1, eta1, phi1, e1, pt2, eta2, phi2, e2, &s)) return false;
+  const ff2 pt = pack(from_double_ranged(pt1, s), from_double_ranged(pt2, s));
+  const ff2 E2 = sqr(pack(from_double_ranged(e1, s), from_double_ranged(e2, s)));
+  const ff2 eta = pack(from_double_ranged(eta1, 0), from_double_ranged(eta2, 0));
+  const ff2 P = mul(pt, cosh_t(eta, T));
+  const ff2 q = add(E2, neg(sqr(P)));
+  const LegFF a{lane_x(pt), lane_x(P), lane_x(q), lane_x(E2)};
+  const LegFF b{lane_y(pt), lane_y(P), lane_y(q), lane_y(E2)};
+  bool ok = true;
+  const ff m2s = pair_m2_ff(a, b, eta1, eta2, phi1, phi2, T, &ok);
+  return finish_mass(m2s, s, ok, out);
 }
 
 }  // namespace ffm

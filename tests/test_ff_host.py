@@ -172,6 +172,14 @@ def test_ff_pair_mass_gradient_against_oracle(ffh, orc):
         assert ok.mean() > 0.99, k
         assert scaled_grad_err(ga[ok], ra[ok], a[ok]).max() <= 1e-12, k
         assert scaled_grad_err(gb[ok], rb[ok], b[ok]).max() <= 1e-12, k
+        # the kernel's path, both legs prepared on paired FP32 operations: the same bits
+        ga2, gb2 = np.empty_like(a), np.empty_like(b)
+        ok2 = np.empty(len(a), np.uint8)
+        ffh.ffh_mass_grad_lp(_p(a), _p(b), _p(gm), ctypes.c_int64(len(a)), _p(ga2), _p(gb2),
+                             _p(ok2))
+        assert np.array_equal(ok2.astype(bool), ok), k
+        assert np.array_equal(ga2[ok].view(np.uint64), ga[ok].view(np.uint64)), k
+        assert np.array_equal(gb2[ok].view(np.uint64), gb[ok].view(np.uint64)), k
 
 
 def test_ff_boost_coefficients(ffh):
@@ -613,6 +621,14 @@ def test_ff_ptetaphie_mass_against_oracle(ffh, orc):
     m2, ok2 = np.empty(4), np.zeros(4, np.uint8)
     ffh.ffh_mass_e(_p(neg), _p(np.ascontiguousarray(b[:4])), ctypes.c_int64(4), _p(m2), _p(ok2))
     assert not ok2.any()
+    # the kernel's path, both legs on paired FP32 operations: the same pairs, the same bits
+    # (spacelike and negative-energy pairs included: both refuse them)
+    a2, b2 = np.concatenate([a, neg]), np.concatenate([b, b[:4]])
+    m3, ok3 = np.empty(len(a2)), np.zeros(len(a2), np.uint8)
+    ffh.ffh_mass_e_lp(_p(a2), _p(b2), ctypes.c_int64(len(a2)), _p(m3), _p(ok3))
+    ok3 = ok3.astype(bool)
+    assert np.array_equal(ok3, np.concatenate([ok, np.zeros(4, bool)]))
+    assert np.array_equal(m3[:len(a)][ok].view(np.uint64), m[ok].view(np.uint64))
 
 
 def test_leg_paired_pair_mass_is_bit_identical(ffh):
