@@ -19,6 +19,7 @@
 #pragma once
 
 #include "ff.cuh"
+#include "mass_ff2.cuh"
 
 namespace gvx {
 namespace cfix {
@@ -273,18 +274,19 @@ GVX_HD bool mass_pxpypzm_scaled(const T *a, const T *b, ff *m, int *e_out) {
                                 mul_shift64(A[0], B[2]), d[0].neg != d[6].neg);
   const ff cz = cross_component(mul_shift64(A[0], B[1]), d[0].neg != d[5].neg,
                                 mul_shift64(A[1], B[0]), d[1].neg != d[4].neg);
-  // the rest in ff on the scaled components
-  ff x[4], y[4];
+  // the rest in ff on the scaled components; the per-leg quantities |p_i|^2, m_i^2 and E_i^2
+  // of both legs on paired FP32 operations (mass_ff2.cuh: lane x leg 1, lane y leg 2, each lane
+  // the scalar operations' bits)
+  ff2 v[4];
 #pragma unroll
-  for (int k = 0; k < 4; k++) {
-    x[k] = scaled_ff(a[k], s1);
-    y[k] = scaled_ff(b[k], s2);
-  }
-  const ff P1 = add_same(add_same(sqr(x[0]), sqr(x[1])), sqr(x[2]));
-  const ff P2 = add_same(add_same(sqr(y[0]), sqr(y[1])), sqr(y[2]));
-  const ff q1 = sqr(x[3]), q2 = sqr(y[3]);
-  const ff dot = add(add(mul(x[0], y[0]), mul(x[1], y[1])), mul(x[2], y[2]));
-  const ff E1E2 = ffm::sqrt(mul(add_same(P1, q1), add_same(P2, q2)));  // scale 2^(s1 + s2)
+  for (int k = 0; k < 4; k++) v[k] = pack(scaled_ff(a[k], s1), scaled_ff(b[k], s2));
+  const ff2 PP = add_same(add_same(sqr(v[0]), sqr(v[1])), sqr(v[2]));
+  const ff2 qq = sqr(v[3]);
+  const ff2 EE = add_same(PP, qq);
+  const ff P1 = lane_x(PP), P2 = lane_y(PP), q1 = lane_x(qq), q2 = lane_y(qq);
+  const ff dot = add(add(mul(lane_x(v[0]), lane_y(v[0])), mul(lane_x(v[1]), lane_y(v[1]))),
+                     mul(lane_x(v[2]), lane_y(v[2])));
+  const ff E1E2 = ffm::sqrt(mul(lane_x(EE), lane_y(EE)));  // scale 2^(s1 + s2)
   ff T2;
   if (dot.hi > 0.0f) {
     const ff c2 = add_same(add_same(sqr(cx), sqr(cy)), sqr(cz));
