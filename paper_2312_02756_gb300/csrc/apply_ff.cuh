@@ -10,7 +10,9 @@
 //     count as 0);
 //   * the four products of a row are formed by TwoProduct with the cross terms of the low parts,
 //     their high parts added by TwoSum, and the low parts and the TwoSum errors collected in
-//     one float;
+//     one float; rows 0 and 1, and rows 2 and 3, run together on paired FP32 instructions
+//     (ff2.cuh: each lane the scalar operations' bits), the matrix kept with those rows
+//     interleaved so that one 16-byte load gives both rows' entries of a column;
 //   * the result, hi + lo scaled by 2^(r_i + s), is rounded to double by one FP64 add (each
 //     float moved into a double exactly by integer operations).
 // Error of each component: below 2^-42 sum_j |L_ij v_j| + 2^-70 max_j |L_ij| max_j |v_j| (the
@@ -22,6 +24,7 @@
 #pragma once
 
 #include "ff.cuh"
+#include "ff2.cuh"
 
 namespace gvx {
 namespace ffm {
@@ -66,25 +69,38 @@ GVX_HD double f2d_rebias(float f, uint32_t k) {
   return hilo2d((((u & 0x7fffffffu) >> 3) + k) | (u & 0x80000000u), u << 29);
 }
 
-// sum_j l[j] x[j] for ff l, x: the high parts' products by TwoProduct and TwoSum, everything
-// else collected in one float.  Returned unnormalized (the caller rounds hi + lo once).
-GVX_HD ff dot4_ff(const ff *l, const ff *x) {
-  ff p = two_prod(l[0].hi, x[0].hi);
-  float s = p.hi;
-  float e = ffma(l[0].lo, x[0].hi, ffma(l[0].hi, x[0].lo, p.lo));
+// The scaled matrix with its rows paired: lp[4 p + j] holds column j of rows 2p (lane x) and
+// 2p + 1 (lane y).
+GVX_HD void pair_rows(const LorentzFF &M, ff2 *lp) {
+#pragma unroll
+  for (int p = 0; p < 2; p++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) lp[4 * p + j] = pack(M.l[8 * p + j], M.l[8 * p + 4 + j]);
+}
+
+// sum_j l[j] x[j] of two rows at once (lanes), for ff x: the high parts' products by TwoProduct
+// and TwoSum, everything else collected in one float per lane.  Returned unnormalized (the
+// caller rounds hi + lo once).
+GVX_HD ff2 dot4_ff2(const ff2 *l, const ff *x) {
+  f2 xh = bc2(x[0].hi), xl = bc2(x[0].lo);
+  ff2 p = two_prod2(l[0].hi, xh);
+  f2 s = p.hi;
+  f2 e = fma2(l[0].lo, xh, fma2(l[0].hi, xl, p.lo));
 #pragma unroll
   for (int j = 1; j < 4; j++) {
-    p = two_prod(l[j].hi, x[j].hi);
-    const ff t = two_sum(s, p.hi);
+    xh = bc2(x[j].hi);
+    xl = bc2(x[j].lo);
+    p = two_prod2(l[j].hi, xh);
+    const ff2 t = two_sum2(s, p.hi);
     s = t.hi;
-    e = fadd(e, fadd(t.lo, ffma(l[j].lo, x[j].hi, ffma(l[j].hi, x[j].lo, p.lo))));
+    e = add2(e, add2(t.lo, fma2(l[j].lo, xh, fma2(l[j].hi, xl, p.lo))));
   }
   return {s, e};
 }
 
-// out = L v for one vector, with the scaled ff matrix l (row-major) and its row scale exponents
-// r from lorentz_ff; false (out untouched) outside the domain.
-GVX_HD bool apply_ff(const ff *l, const int *r, const double *v, double *out) {
+// out = L v for one vector, with the row-paired scaled matrix lp (pair_rows) and the row scale
+// exponents r of lorentz_ff; false (out untouched) outside the domain.
+GVX_HD bool apply_ff(const ff2 *lp, const int *r, const double *v, double *out) {
   int emax = 0;
 #pragma unroll
   for (int j = 0; j < 4; j++) {
@@ -97,10 +113,12 @@ GVX_HD bool apply_ff(const ff *l, const int *r, const double *v, double *out) {
 #pragma unroll
   for (int j = 0; j < 4; j++) x[j] = from_double_ranged(v[j], s);
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const ff y = dot4_ff(l + 4 * i, x);
-    const uint32_t k = (uint32_t)(896 + r[i] + s) << 20;  // float -> double exponent rebias
-    out[i] = f2d_rebias(y.hi, k) + f2d_rebias(y.lo, k);
+  for (int p = 0; p < 2; p++) {
+    const ff2 y = dot4_ff2(lp + 4 * p, x);
+    const uint32_t k0 = (uint32_t)(896 + r[2 * p] + s) << 20;  // float -> double exponent rebias
+    const uint32_t k1 = (uint32_t)(896 + r[2 * p + 1] + s) << 20;
+    out[2 * p] = f2d_rebias(y.hi.x, k0) + f2d_rebias(y.lo.x, k0);
+    out[2 * p + 1] = f2d_rebias(y.hi.y, k1) + f2d_rebias(y.lo.y, k1);
   }
   return true;
 }

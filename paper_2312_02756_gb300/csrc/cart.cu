@@ -64,21 +64,21 @@ template <typename T, int LV, int LO, bool SHARED>
 __global__ void __launch_bounds__(256, 4) lorentz_apply_kernel(const T *__restrict__ L, Lv v, LvOut out,
                                                             int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  T l0[16];
-  if (SHARED) {
-#pragma unroll
-    for (int k = 0; k < 16; k++) l0[k] = L[k];
-  }
   if constexpr (SHARED && sizeof(T) == 8) {
     // one matrix for every vector: the float-float row sums of apply_ff.cuh (the scaled matrix
     // in shared memory, read by broadcast), FP64 FMA chains for a matrix or a vector outside
-    // their domain
-    __shared__ ffm::ff s_l[16];
+    // their domain (the raw matrix also in shared memory, read only there, so that it holds no
+    // registers)
+    __shared__ ffm::ff2 s_l[8];  // rows paired (pair_rows): one 16-byte load per column
+    __shared__ double s_raw[16];
     __shared__ int s_r[4];
     __shared__ int s_ok;
+    if (threadIdx.x < 16) s_raw[threadIdx.x] = L[threadIdx.x];
     if (threadIdx.x == 0) {
+      double l0[16];
+      for (int k = 0; k < 16; k++) l0[k] = L[k];
       const ffm::LorentzFF M = ffm::lorentz_ff(l0);
-      for (int k = 0; k < 16; k++) s_l[k] = M.l[k];
+      ffm::pair_rows(M, s_l);
       for (int k = 0; k < 4; k++) s_r[k] = M.r[k];
       s_ok = M.ok;
     }
@@ -97,11 +97,16 @@ __global__ void __launch_bounds__(256, 4) lorentz_apply_kernel(const T *__restri
       if (ok && ffm::apply_ff(s_l, s_r, xv, o)) {
         r = {o[0], o[1], o[2], o[3]};
       } else {
-        r = apply_fma(l0, x);
+        r = apply_fma(s_raw, x);
       }
       st4<T, LO>(out, i, r);
     }
   } else {
+    T l0[16];
+    if (SHARED) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) l0[k] = L[k];
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
       const V4<T> x = ld4<T, LV>(v, i);
       T l[16];

@@ -157,9 +157,11 @@ int64_t ffh_mass_cart_fixed(const double *a, const double *b, int64_t n, int coo
 int64_t ffh_apply(const double *L, const double *v, int64_t n, double *out, uint8_t *ok) {
   const LorentzFF M = lorentz_ff(L);
   if (!M.ok) return -1;
+  ff2 lp[8];
+  pair_rows(M, lp);
   int64_t c = 0;
   for (int64_t i = 0; i < n; i++) {
-    ok[i] = apply_ff(M.l, M.r, v + 4 * i, out + 4 * i);
+    ok[i] = apply_ff(lp, M.r, v + 4 * i, out + 4 * i);
     c += ok[i];
   }
   return c;
