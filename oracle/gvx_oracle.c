@@ -633,13 +633,27 @@ void orc_lv_mass_def(const double *v, int64_t n, double *m) {
  *   P_1 P_2 - p_1.p_2 = pt_1 pt_2 (cosh(d_eta) - cos(d_phi))
  *                     = 2 pt_1 pt_2 (sinh^2(d_eta/2) + sin^2(d_phi/2)).
  * Every term is >= 0 for pt >= 0, so the relative error is a few ulps. */
+/* sin(d_phi / 2) up to sign, with d_phi = phi1 - phi2.  sin^2(d_phi/2) has period 2 pi, so for
+ * |d_phi| > pi (both azimuths within [-pi, pi]) the half-angle is taken as
+ * pi - |d_phi|/2 = ((pi - |phi1|) + (pi - |phi2|)) / 2: each bracket is an exact difference in
+ * double (|phi| >= pi/2 there) and their sum has no cancellation, whereas phi1 - phi2 itself is
+ * rounded to ~4e-16 absolute, which is a large relative error when |d_phi| is within ~1e-6 of
+ * 2 pi. */
+static double half_dphi_sin_fp64(double phi1, double phi2) {
+  const double pid = 3.141592653589793116, pilo = 1.2246467991473531772e-16; /* pi = pid + pilo */
+  double d = phi1 - phi2;
+  if (fabs(d) > pid && fabs(phi1) <= pid && fabs(phi2) <= pid)
+    return sin(0.5 * ((pid - fabs(phi1)) + (pid - fabs(phi2)) + 2.0 * pilo));
+  return sin(0.5 * d);
+}
+
 static double pair_mass_fp64(const double *a, const double *b) {
   double pt1 = a[0], eta1 = a[1], phi1 = a[2], m1 = a[3];
   double pt2 = b[0], eta2 = b[1], phi2 = b[2], m2 = b[3];
   double P1 = pt1 * cosh(eta1), P2 = pt2 * cosh(eta2);
   double mm1 = m1 * m1, mm2 = m2 * m2;
   double E1 = sqrt(P1 * P1 + mm1), E2 = sqrt(P2 * P2 + mm2);
-  double se = sinh(0.5 * (eta1 - eta2)), sp = sin(0.5 * (phi1 - phi2));
+  double se = sinh(0.5 * (eta1 - eta2)), sp = half_dphi_sin_fp64(phi1, phi2);
   double t_mass = 2.0 * (mm1 * P2 * P2 + mm2 * P1 * P1 + mm1 * mm2) / (E1 * E2 + P1 * P2);
   double t_ang = 4.0 * pt1 * pt2 * (se * se + sp * sp);
   double denom = E1 * E2 + P1 * P2;

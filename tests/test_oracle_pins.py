@@ -121,6 +121,26 @@ def test_mass_definition_vs_identity(orc):
     # binary128 (information, but also a check that the adversarial set is adversarial)
     naive = np.abs(orc.mass_naive_fp64(a, b) / m1 - 1)
     assert naive.max() > 1e-9
+    # azimuths on either side of +-pi, 2 pi - |d_phi| down to 1e-8 (massless legs at equal eta,
+    # where the azimuthal term is the whole mass): O2's half-angle from exact brackets; the
+    # rounded phi1 - phi2 (~4e-16 absolute) would be off by up to ~1e-8 relative here.  Compared
+    # where O1 itself keeps 1e-14 (m >= 1e-9 (E1 + E2)).
+    g = syn.rng(106)
+    n = 4000
+    a, b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    a[:, 1] = g.uniform(-1, 1, n)
+    b[:, 1] = a[:, 1]
+    gap = 10 ** g.uniform(-8, -1, n)
+    a[:, 2] = np.pi - gap * g.random(n)
+    b[:, 2] = -np.pi + gap * g.random(n)
+    a[::2, 3] = 0.0
+    b[::2, 3] = 0.0
+    m1 = orc.mass_def(a, b)
+    e = lambda x: np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
+    cond = m1 >= 1e-9 * (e(a) + e(b))
+    assert cond.mean() > 0.9
+    rel = np.abs(orc.mass_fp64(a, b)[cond] / m1[cond] - 1)
+    assert rel.max() <= 1e-14
 
 
 def test_mass_threads_agree(orc):
