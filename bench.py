@@ -334,7 +334,7 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
             la, lb, lga, lgb = (Step._lv(t, 0, 4) for t in (a, b, ga, gb))
             fwd = lambda: _lib.check(lib.gvx_invariant_mass(r(la), r(lb), P(m.data_ptr()), n, code, s))
             bwd = lambda: _lib.check(lib.gvx_invariant_mass_bwd(
-                r(la), r(lb), P(gm.data_ptr()), r(lga), r(lgb), n, code, s))
+                r(la), r(lb), P(m.data_ptr()), P(gm.data_ptr()), r(lga), r(lgb), n, code, s))
             t_f = time_loop(torch, fwd, stream, steps, warmup)
             t_fb = time_loop(torch, lambda: (fwd(), bwd()), stream, steps, warmup)
             del a, b, gm, m, ga, gb

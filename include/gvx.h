@@ -106,10 +106,14 @@ gvx_status gvx_invariant_mass(const gvx_lv *a, const gvx_lv *b, void *m, int64_t
  * Adjoint of gvx_invariant_mass: grad_a[i] = grad_m[i] * dm[i]/d(pt, eta, phi, m) of leg a, and
  * likewise grad_b.  grad_a and grad_b are written (not accumulated) in their own layouts.  Where
  * m[i] = 0 the gradient is 0 (m is not differentiable there).
+ *   m_saved: NULL, or the n masses gvx_invariant_mass returned for the same a and b (device,
+ *            `dtype`, aligned to its size).  When given, "m[i] = 0" means m_saved[i] = 0, so
+ *            that the adjoint's zeros coincide with the forward's; the caller keeps it alive
+ *            until the call has run.
  */
-gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *grad_m,
-                                  gvx_lv *grad_a, gvx_lv *grad_b, int64_t n, int32_t dtype,
-                                  void *stream);
+gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *m_saved,
+                                  const void *grad_m, gvx_lv *grad_a, gvx_lv *grad_b, int64_t n,
+                                  int32_t dtype, void *stream);
 
 /*
  * Lorentz boost (Sec. 4.1 ApplyBoost): out[i] = L(beta_i) v[i] for PxPyPzE vectors, with

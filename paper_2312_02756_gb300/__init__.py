@@ -107,20 +107,21 @@ class _InvariantMass(torch.autograd.Function):
         st = lib.gvx_invariant_mass(ctypes.byref(_lv(a, la, 4)), ctypes.byref(_lv(b, lb, 4)),
                                     ctypes.c_void_p(m.data_ptr()), n, _dtype_code(a), _stream())
         _lib.check(st, "gvx_invariant_mass")
-        ctx.save_for_backward(a, b)
+        ctx.save_for_backward(a, b, m)
         ctx.la, ctx.lb = la, lb
         return m
 
     @staticmethod
     def backward(ctx, gm):
         lib = load_library()
-        a, b = ctx.saved_tensors
+        a, b, m = ctx.saved_tensors
         gm = gm.contiguous().to(a.dtype)
         ga, gb = torch.empty_like(a), torch.empty_like(b)
         n = _count(a, ctx.la)
         st = lib.gvx_invariant_mass_bwd(
             ctypes.byref(_lv(a, ctx.la, 4)), ctypes.byref(_lv(b, ctx.lb, 4)),
-            ctypes.c_void_p(gm.data_ptr()), ctypes.byref(_lv(ga, ctx.la, 4)),
+            ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(gm.data_ptr()),
+            ctypes.byref(_lv(ga, ctx.la, 4)),
             ctypes.byref(_lv(gb, ctx.lb, 4)), n, _dtype_code(a), _stream())
         _lib.check(st, "gvx_invariant_mass_bwd")
         return ga, gb, None, None

@@ -65,7 +65,7 @@ def _sigs(lib):
         "gvx_status_string": ([I32], ctypes.c_char_p),
         "gvx_last_cuda_error": ([], I32),
         "gvx_invariant_mass": ([LVP, LVP, P, I64, I32, P], S),
-        "gvx_invariant_mass_bwd": ([LVP, LVP, P, LVP, LVP, I64, I32, P], S),
+        "gvx_invariant_mass_bwd": ([LVP, LVP, P, P, LVP, LVP, I64, I32, P], S),
         "gvx_boost": ([LVP, LVP, I64, LVP, I64, I32, P], S),
         "gvx_boost_bwd_workspace": ([I64, I64, I32], SZ),
         "gvx_boost_bwd": ([LVP, LVP, I64, LVP, LVP, LVP, I64, I32, P, SZ, P], S),

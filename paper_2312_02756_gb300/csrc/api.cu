@@ -256,9 +256,9 @@ gvx_status gvx_lorentz_apply(const void *L, int64_t l_stride, const gvx_lv *v, g
                                              dtype, (cudaStream_t)stream));
 }
 
-gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *grad_m,
-                                  gvx_lv *grad_a, gvx_lv *grad_b, int64_t n, int32_t dtype,
-                                  void *stream) {
+gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *m_saved,
+                                  const void *grad_m, gvx_lv *grad_a, gvx_lv *grad_b, int64_t n,
+                                  int32_t dtype, void *stream) {
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
   if (n == 0) return GVX_OK;
@@ -268,7 +268,8 @@ gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *
   GVX_TRY(check_lv(grad_b, dtype, 4));
   if (!grad_m) return GVX_ERR_NULL;
   if ((uintptr_t)grad_m % scalar_size(dtype)) return GVX_ERR_ALIGN;
-  return from_cuda(gvx::launch_mass_bwd(gvx::as_in(*a), gvx::as_in(*b), grad_m,
+  if (m_saved && (uintptr_t)m_saved % scalar_size(dtype)) return GVX_ERR_ALIGN;
+  return from_cuda(gvx::launch_mass_bwd(gvx::as_in(*a), gvx::as_in(*b), m_saved, grad_m,
                                         gvx::as_out(*grad_a), gvx::as_out(*grad_b), n, dtype,
                                         (cudaStream_t)stream));
 }

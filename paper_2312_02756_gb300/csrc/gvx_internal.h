@@ -29,8 +29,8 @@ int32_t *device_status_word();
 
 cudaError_t launch_mass(const Lv &a, const Lv &b, void *m, int64_t n, int dtype,
                         cudaStream_t s);
-cudaError_t launch_mass_bwd(const Lv &a, const Lv &b, const void *gm, const LvOut &ga,
-                            const LvOut &gb, int64_t n, int dtype, cudaStream_t s);
+cudaError_t launch_mass_bwd(const Lv &a, const Lv &b, const void *ms, const void *gm,
+                            const LvOut &ga, const LvOut &gb, int64_t n, int dtype, cudaStream_t s);
 cudaError_t launch_boost(const Lv &v, const Lv &beta, int64_t beta_stride, const LvOut &out,
                          int64_t n, int dtype, cudaStream_t s);
 size_t boost_bwd_workspace(int64_t n, int64_t beta_stride, int dtype);

@@ -10,12 +10,12 @@
 //      and go on);  write pair_offsets;
 //   3. stage the tile's particles in shared memory in sub-batches of at most kCP particles:
 //      per-particle terms once per particle (one thread each, which also finds its event's
-//      scale) -- the float-float leg (pt, P = pt cosh(eta), m^2, E^2, scaled by the event's
-//      power of two) and the Cartesian components for the sums -- then, after one barrier, the
-//      event sums (one thread per event, FP64) and the pair masses (one thread per pair over the
-//      flattened pair range of the sub-batch, coalesced stores) with the same float-float pair
-//      arithmetic as the elementwise FP64 kernel (mass_ff.cuh), falling back to FP64 for pairs
-//      outside its domain;
+//      scale) -- the float-float light-cone terms of the leg (pt, Y = E + P, D = m^2 / Y, scaled
+//      by the event's power of two, bit for bit a lane of the elementwise FP64 kernel's legs) and
+//      the Cartesian components for the sums -- then, after one barrier, the event sums (one
+//      thread per event, FP64) and the pair masses (one thread per pair over the flattened pair
+//      range of the sub-batch, coalesced stores) with the elementwise kernel's pair arithmetic
+//      (mass_lc.cuh: lc_pair_m2), falling back to FP64 for pairs outside its domain;
 //   4. an event with more than kCP particles is handled alone, straight from global memory.
 // Tile descriptors are 64-bit words: 2 flag bits (aggregate / inclusive prefix) + 62-bit value.
 #include <cuda_runtime.h>
@@ -25,19 +25,18 @@
 #include <limits.h>
 
 #include "common.cuh"
-#include "mass_ff.cuh"
+#include "mass_lc.cuh"
 #include "pair_index.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
 namespace {
 
-// particles staged in shared memory per sub-batch: with the 32 KB of tables, four CTAs of 256
-// threads (capped at 64 registers) fit an SM; 384 particles and three CTAs measured 4% slower
+// particles staged in shared memory per sub-batch
 constexpr int kCP = 224;
-// per particle: eta, phi, px, py, pz, E (doubles), pt, P, q, E2 (float pairs), leg exponent and
-// scale (ints)
-constexpr size_t kDynSmem = (size_t)kCP * (6 * sizeof(double) + 4 * sizeof(float2) + 2 * sizeof(int));
+// per particle: eta, phi, px, py, pz, E (doubles), pt, Y, D (float pairs), the particle's
+// largest high word of pt and |m|, and its event's scale field or kNoFast (ints)
+constexpr size_t kDynSmem = (size_t)kCP * (6 * sizeof(double) + 3 * sizeof(float2) + 2 * sizeof(int));
 constexpr int kNoFast = INT_MIN;  // scale marker of a particle outside the float-float domain
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
@@ -128,18 +127,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
   extern __shared__ double s_dyn[];
   double *s_eta = s_dyn, *s_phi = s_eta + kCP, *s_px = s_phi + kCP, *s_py = s_px + kCP;
   double *s_pz = s_py + kCP, *s_E = s_pz + kCP;
-  ffm::ff *s_pt = reinterpret_cast<ffm::ff *>(s_E + kCP), *s_P = s_pt + kCP, *s_q = s_P + kCP;
-  ffm::ff *s_E2 = s_q + kCP;
-  int *s_sc = reinterpret_cast<int *>(s_E2 + kCP), *s_fs = s_sc + kCP;
-  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
-  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
+  ffm::ff *s_pt = reinterpret_cast<ffm::ff *>(s_E + kCP), *s_Y = s_pt + kCP, *s_D = s_Y + kCP;
+  int *s_sc = reinterpret_cast<int *>(s_D + kCP), *s_fs = s_sc + kCP;
   __shared__ int64_t s_off[TE + 1];
   __shared__ int64_t s_pp[TE + 1];
   __shared__ int64_t s_warp[NT / 32];
   __shared__ double s_red[4 * (NT / 32)];
   __shared__ int64_t s_base;
   __shared__ int64_t s_tile;
-  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
+  const ffm::LcTab T{ffm::kHypTab, ffm::kSinTab};
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(A.counter, 1u);
@@ -223,19 +219,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
         continue;
       }
       const int np = (int)(s_off[sbe] - pb);
-      // (a) raw particles; pt and m parked in the px/py slots, the leg exponent in s_sc
+      // (a) raw particles; pt and m parked in the px/py slots, the larger high word of pt and
+      // |m| in s_sc
       for (int k = threadIdx.x; k < np; k += NT) {
         V4<double> v = ld4<double, LP>(A.p, pb + k);
         s_eta[k] = v.y;
         s_phi[k] = v.z;
         s_px[k] = v.x;
         s_py[k] = v.w;
-        s_sc[k] = ffm::leg_exponent(v.x, v.w);
+        s_sc[k] = (int)ffm::umax32(ffm::dhi(v.x), ffm::dhi(v.w) & 0x7fffffffu);
       }
       __syncthreads();
-      // (b) one thread per particle: its event's scale (the largest leg exponent over the event,
-      // from s_sc), whether the fast path takes it (the final scale goes to s_fs, so s_sc stays
-      // intact for the other particles of the event), and its per-particle terms
+      // (b) one thread per particle: its event's scale (the largest high word over the event,
+      // from s_sc), whether the fast path takes it (the event's scale field goes to s_fs, so s_sc
+      // stays intact for the other particles of the event), and its per-particle terms
       for (int k = threadIdx.x; k < np; k += NT) {
         int lo = sb, hi = sbe - 1;  // the particle's event: the last e with s_off[e] <= pb + k
         while (lo < hi) {
@@ -243,35 +240,38 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
           if (s_off[mid] <= pb + k) lo = mid;
           else hi = mid - 1;
         }
-        int emax = 0;
+        uint32_t wmax = 0;
         for (int t = (int)(s_off[lo] - pb); t < (int)(s_off[lo + 1] - pb); t++)
-          emax = s_sc[t] > emax ? s_sc[t] : emax;
+          wmax = ffm::umax32((uint32_t)s_sc[t], wmax);
         const double pt = s_px[k], eta = s_eta[k], phi = s_phi[k], m = s_py[k];
-        int sc = ffm::scale_exponent_ok(emax) && ffm::leg_in_domain(pt, eta, phi, m, emax)
-                     ? emax - 1023
+        // the domain of the elementwise fast path (mass_lc.cuh), at the event's scale
+        const uint32_t ew = wmax & 0x7ff00000u;
+        const uint32_t hp = ffm::dhi(pt), hm = ffm::dhi(m) & 0x7fffffffu;
+        const uint32_t he = ffm::dhi(eta) & 0x7fffffffu, hf = ffm::dhi(phi) & 0x7fffffffu;
+        int sc = wmax - (200u << 20) < (1700u << 20) &&
+                         ffm::umin32(hp - 0x100000u, hm - 0x100000u) >= ew - (41u << 20) &&
+                         he < 0x40200000u && hf < 0x400C0000u
+                     ? (int)ew
                      : kNoFast;
-        bool ok = true;
         if (sc != kNoFast) {
-          ffm::LegFF l;
-          l.pt = ffm::from_double_ranged(pt, sc);
-          l.q = ffm::sqr(ffm::from_double_ranged(m, sc));
-          ffm::ff sn, cs;
-          const ffm::ff eta_f = ffm::from_double_ranged(eta, 0);
-          const ffm::ff sh = ffm::sinh_t(eta_f, T);
-          ffm::sincos_t(phi, T, &sn, &cs, &ok);
-          l.P = ffm::mul(l.pt, ffm::cosh_t(eta_f, T));  // as make_leg_ff: bitwise the same leg
-          l.E2 = ffm::add_same(ffm::sqr(l.P), l.q);
-          s_pt[k] = l.pt;
-          s_P[k] = l.P;
-          s_q[k] = l.q;
-          s_E2[k] = l.E2;
-          s_px[k] = ffm::to_double(ffm::renorm(ffm::mul(l.pt, cs)), sc);
-          s_py[k] = ffm::to_double(ffm::renorm(ffm::mul(l.pt, sn)), sc);
-          s_pz[k] = ffm::to_double(ffm::renorm(ffm::mul(l.pt, sh)), sc);
-          s_E[k] = ffm::to_double(ffm::sqrt(l.E2), sc);
-        }
-        if (sc == kNoFast || !ok) {  // FP64 evaluation
-          sc = kNoFast;
+          const uint32_t rb = ew - (127u << 20);
+          const ffm::ff ptf = ffm::cvt1(ffm::cvt_parts(hp, ffm::dlo(pt), rb));
+          const ffm::ff mmf = ffm::cvt1(ffm::cvt_parts(hm, ffm::dlo(m), rb));
+          const ffm::ff xe = ffm::cvt1(ffm::cvt_parts(ffm::umax32(he, 0x3E100000u), ffm::dlo(eta),
+                                                      ffm::kRebaseOne));
+          ffm::ff sh, sn, cs;
+          const ffm::LcLeg<ffm::ff> L = ffm::lc_leg(ptf, mmf, xe, T.hyp, &sh);
+          ffm::sincos_lc(ffm::cvt1(ffm::cvt_parts(hf, ffm::dlo(phi), ffm::kRebaseOne)), T.sin, &sn, &cs);
+          s_pt[k] = ptf;
+          s_Y[k] = L.Y;
+          s_D[k] = L.D;
+          const int e2 = (int)(ew >> 20) - 1023;
+          const double sphi = (ffm::dhi(phi) >> 31) ? -1.0 : 1.0, seta = (ffm::dhi(eta) >> 31) ? -1.0 : 1.0;
+          s_px[k] = ffm::to_double(ffm::lc_mul(ptf, cs), e2);
+          s_py[k] = sphi * ffm::to_double(ffm::lc_mul(ptf, sn), e2);
+          s_pz[k] = seta * ffm::to_double(ffm::lc_mul(ptf, sh), e2);
+          s_E[k] = ffm::to_double(L.E, e2);
+        } else {  // FP64 evaluation
           double sphi, cphi;
           sincos(phi, &sphi, &cphi);
           s_px[k] = pt * cphi;
@@ -310,11 +310,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
         bool done = false;
         const int sc = s_fs[ia];
         if (sc != kNoFast && s_fs[ib] != kNoFast) {
-          bool ok = true;
-          ffm::LegFF a{s_pt[ia], s_P[ia], s_q[ia], s_E2[ia]};
-          ffm::LegFF b{s_pt[ib], s_P[ib], s_q[ib], s_E2[ib]};
-          ffm::ff m2 = ffm::pair_m2_ff(a, b, s_eta[ia], s_eta[ib], s_phi[ia], s_phi[ib], T, &ok);
-          done = ffm::finish_mass(m2, sc, ok, &mass);
+          ffm::ff m2s;
+          if (ffm::lc_pair_m2(s_pt[ia], s_pt[ib], s_Y[ia], s_Y[ib], s_D[ia], s_D[ib], s_eta[ia],
+                              s_eta[ib], s_phi[ia], s_phi[ib], T, &m2s)) {
+            mass = ffm::lc_mass_out(m2s, (uint32_t)sc);
+            done = true;
+          }
         }
         if (!done) {
           Leg<double> a = make_leg(ld4<double, LP>(A.p, pb + ia));

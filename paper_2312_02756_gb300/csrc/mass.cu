@@ -8,15 +8,18 @@
 // with P_i = pt_i cosh(eta_i) = |p_i| and E_i = sqrt(P_i^2 + m_i^2): a relative error of a few
 // ulps whatever the cancellation in the plain form.
 //
-// FP64 forward: the identity is evaluated in float-float on the FP32 pipe (mass_ff.cuh) -- a
-// GB300 SM retires ~80x more FP32 than FP64 operations -- with the FP64 evaluation kept for the
-// rare lanes outside the float-float domain (huge |eta|, extreme scale ratios).
+// FP64 forward: float-float on the FP32 pipe -- a GB300 SM retires ~64x more FP32 than FP64
+// operations -- through the light-cone form of the same mass (mass_lc.cuh): with D = E - P and
+// Y = E + P per leg, m^2 = (D1 + D2)(Y1 + Y2) + 4 pt1 pt2 (sinh^2(d_eta/2) + sin^2(d_phi/2)),
+// again all terms non-negative.  The FP64 evaluation is kept for the rare lanes outside the
+// float-float domain (|eta| >= 8, extreme scale ratios, |d_phi| near 2 pi).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 #include "mass_ff.cuh"
 #include "mass_ff2.cuh"
 #include "mass_grad_ff2.cuh"
+#include "mass_lc.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
@@ -48,29 +51,46 @@ __global__ void __launch_bounds__(256) mass_kernel(Lv a, Lv b, T *__restrict__ m
   }
 }
 
+// One FP64 pair: the light-cone float-float fast path (mass_lc.cuh), the FP64 formulas for a
+// lane outside its domain.
+__device__ __forceinline__ double pair_mass_f64(const V4<double> &x, const V4<double> &y,
+                                                const ffm::LcTab &T) {
+  double out;
+  if (!ffm::pair_mass_lc(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T, &out))
+    out = sqrt(pair_terms(make_leg(x), make_leg(y)).m2);
+  return out;
+}
+
+// FP64 forward: grid-stride, one pair per thread and step; 64 registers, so four CTAs of 256
+// threads share an SM.  For a leg in SoA layout (four separate arrays), lanes 0..7 of each warp
+// first ask L2 to prefetch the warp's next 32 elements of each array (one 128-byte line per
+// lane), so that the next step's eight loads find them in L2 rather than in HBM.
 template <int LA, int LB>
-__global__ void __launch_bounds__(256) mass_f64_kernel(Lv a, Lv b, double *__restrict__ m, int64_t n) {
-  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
-  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
-  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
+__global__ void __launch_bounds__(256, 4) mass_f64_kernel(Lv a, Lv b, double *__restrict__ m, int64_t n) {
+  const ffm::LcTab T{ffm::kHypTab, ffm::kSinTab};
+  const int lane = threadIdx.x & 31;
+  const int leg = (lane >> 2) & 1;  // lanes 0-3: leg a's arrays, 4-7: leg b's
+  const bool soa = leg ? LB == GVX_SOA : LA == GVX_SOA;
+  const char *pbase = (const char *)(leg ? b : a).c[lane & 3] + 128 * ((lane >> 3) & 1);
+  const bool prefetch = soa && lane < 16;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    V4<double> x = ld4<double, LA>(a, i);
-    V4<double> y = ld4<double, LB>(b, i);
-    double out;  // the two legs on paired FP32 instructions (mass_ff2.cuh): the same bits
-    if (!ffm::pair_mass_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T, &out))
-      out = sqrt(pair_terms(make_leg(x), make_leg(y)).m2);
-    st_s(m + i, out);
+    const int64_t next = i - lane + stride;  // the warp's first element of the next step
+    if (prefetch && next + 32 <= n) asm volatile("prefetch.global.L2 [%0];" ::"l"(pbase + 8 * next));
+    st_s(m + i, pair_mass_f64(ld4<double, LA>(a, i), ld4<double, LB>(b, i), T));
   }
 }
 
+// Where the forward's saved mass ms[i] is 0 the gradient is 0 (the convention of the adjoint),
+// so that forward and adjoint agree even where a recomputed mass would round away from 0.
 template <typename T, int LA, int LB, int LGA, int LGB>
-__global__ void __launch_bounds__(256) mass_bwd_kernel(Lv a, Lv b, const T *__restrict__ gm,
-                                                       LvOut ga, LvOut gb, int64_t n) {
+__global__ void __launch_bounds__(256) mass_bwd_kernel(Lv a, Lv b, const T *__restrict__ ms,
+                                                       const T *__restrict__ gm, LvOut ga, LvOut gb,
+                                                       int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    V4<T> g1, g2;
-    pair_mass_grad(ld4<T, LA>(a, i), ld4<T, LB>(b, i), ld_s(gm + i), g1, g2);
+    V4<T> g1 = {0, 0, 0, 0}, g2 = {0, 0, 0, 0};
+    if (!ms || ld_s(ms + i) != (T)0) pair_mass_grad(ld4<T, LA>(a, i), ld4<T, LB>(b, i), ld_s(gm + i), g1, g2);
     st4<T, LGA>(ga, i, g1);
     st4<T, LGB>(gb, i, g2);
   }
@@ -78,12 +98,9 @@ __global__ void __launch_bounds__(256) mass_bwd_kernel(Lv a, Lv b, const T *__re
 
 template <int LA, int LB>
 void launch_mass_f64_l(const Lv &a, const Lv &b, double *m, int64_t n, cudaStream_t s) {
-  static int occ[64];
   const int threads = 256;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  unsigned grid = balanced_grid(mass_f64_kernel<LA, LB>, threads, 0, n, &occ[dev & 63]);
-  mass_f64_kernel<LA, LB><<<grid, threads, 0, s>>>(a, b, m, n);
+  mass_f64_kernel<LA, LB><<<balanced_grid_of<mass_f64_kernel<LA, LB>>(threads, 0, n), threads, 0, s>>>(
+      a, b, m, n);
 }
 
 cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaStream_t s) {
@@ -102,7 +119,8 @@ cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaSt
 // FP64 adjoint: float-float evaluation (mass_ff.cuh, pair_mass_grad_ff; the two legs on paired
 // FP32 instructions, mass_grad_ff2.cuh) with the FP64 formulas kept for lanes outside its domain.
 template <int LA, int LB, int LGA, int LGB>
-__global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ gm,
+__global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ ms,
+                                                           const double *__restrict__ gm,
                                                            LvOut ga, LvOut gb, int64_t n) {
   __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
   __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
@@ -114,7 +132,10 @@ __global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const 
     double g = ld_s(gm + i);
     double o[8];
     V4<double> g1, g2;
-    if (ffm::pair_mass_grad_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
+    if (ms && ld_s(ms + i) == 0.0) {
+      g1 = {0, 0, 0, 0};
+      g2 = {0, 0, 0, 0};
+    } else if (ffm::pair_mass_grad_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
       g1 = {o[0], o[1], o[2], o[3]};
       g2 = {o[4], o[5], o[6], o[7]};
     } else {
@@ -145,43 +166,43 @@ cudaError_t launch_mass_t(const Lv &a, const Lv &b, void *m, int64_t n, cudaStre
 }
 
 template <typename T, int LA, int LB, int LGA, int LGB>
-void launch_bwd_one(int threads, const Lv &a, const Lv &b, const T *gm,
+void launch_bwd_one(int threads, const Lv &a, const Lv &b, const T *ms, const T *gm,
                     const LvOut &ga, const LvOut &gb, int64_t n, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
     constexpr auto k = mass_bwd_f64_kernel<LA, LB, LGA, LGB>;
-    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, gm, ga, gb, n);
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, ms, gm, ga, gb, n);
   } else {
     constexpr auto k = mass_bwd_kernel<T, LA, LB, LGA, LGB>;
-    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, gm, ga, gb, n);
+    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, ms, gm, ga, gb, n);
   }
 }
 
 template <typename T, int LA, int LB>
-void launch_bwd_out(int threads, const Lv &a, const Lv &b, const T *gm,
+void launch_bwd_out(int threads, const Lv &a, const Lv &b, const T *ms, const T *gm,
                     const LvOut &ga, const LvOut &gb, int64_t n, cudaStream_t s) {
   if (ga.layout == GVX_SOA && gb.layout == GVX_SOA)
-    launch_bwd_one<T, LA, LB, GVX_SOA, GVX_SOA>(threads, a, b, gm, ga, gb, n, s);
+    launch_bwd_one<T, LA, LB, GVX_SOA, GVX_SOA>(threads, a, b, ms, gm, ga, gb, n, s);
   else if (ga.layout == GVX_SOA)
-    launch_bwd_one<T, LA, LB, GVX_SOA, GVX_AOS>(threads, a, b, gm, ga, gb, n, s);
+    launch_bwd_one<T, LA, LB, GVX_SOA, GVX_AOS>(threads, a, b, ms, gm, ga, gb, n, s);
   else if (gb.layout == GVX_SOA)
-    launch_bwd_one<T, LA, LB, GVX_AOS, GVX_SOA>(threads, a, b, gm, ga, gb, n, s);
+    launch_bwd_one<T, LA, LB, GVX_AOS, GVX_SOA>(threads, a, b, ms, gm, ga, gb, n, s);
   else
-    launch_bwd_one<T, LA, LB, GVX_AOS, GVX_AOS>(threads, a, b, gm, ga, gb, n, s);
+    launch_bwd_one<T, LA, LB, GVX_AOS, GVX_AOS>(threads, a, b, ms, gm, ga, gb, n, s);
 }
 
 template <typename T>
-cudaError_t launch_mass_bwd_t(const Lv &a, const Lv &b, const void *gm, const LvOut &ga,
-                              const LvOut &gb, int64_t n, cudaStream_t s) {
+cudaError_t launch_mass_bwd_t(const Lv &a, const Lv &b, const void *ms, const void *gm,
+                              const LvOut &ga, const LvOut &gb, int64_t n, cudaStream_t s) {
   const int threads = 256;
-  const T *g = (const T *)gm;
+  const T *g = (const T *)gm, *msv = (const T *)ms;
   if (a.layout == GVX_SOA && b.layout == GVX_SOA)
-    launch_bwd_out<T, GVX_SOA, GVX_SOA>(threads, a, b, g, ga, gb, n, s);
+    launch_bwd_out<T, GVX_SOA, GVX_SOA>(threads, a, b, msv, g, ga, gb, n, s);
   else if (a.layout == GVX_SOA)
-    launch_bwd_out<T, GVX_SOA, GVX_AOS>(threads, a, b, g, ga, gb, n, s);
+    launch_bwd_out<T, GVX_SOA, GVX_AOS>(threads, a, b, msv, g, ga, gb, n, s);
   else if (b.layout == GVX_SOA)
-    launch_bwd_out<T, GVX_AOS, GVX_SOA>(threads, a, b, g, ga, gb, n, s);
+    launch_bwd_out<T, GVX_AOS, GVX_SOA>(threads, a, b, msv, g, ga, gb, n, s);
   else
-    launch_bwd_out<T, GVX_AOS, GVX_AOS>(threads, a, b, g, ga, gb, n, s);
+    launch_bwd_out<T, GVX_AOS, GVX_AOS>(threads, a, b, msv, g, ga, gb, n, s);
   return cudaGetLastError();
 }
 
@@ -191,10 +212,10 @@ cudaError_t launch_mass(const Lv &a, const Lv &b, void *m, int64_t n, int dtype,
   return dtype == GVX_F64 ? launch_mass_f64(a, b, m, n, s) : launch_mass_t<float>(a, b, m, n, s);
 }
 
-cudaError_t launch_mass_bwd(const Lv &a, const Lv &b, const void *gm, const LvOut &ga,
-                            const LvOut &gb, int64_t n, int dtype, cudaStream_t s) {
-  return dtype == GVX_F64 ? launch_mass_bwd_t<double>(a, b, gm, ga, gb, n, s)
-                          : launch_mass_bwd_t<float>(a, b, gm, ga, gb, n, s);
+cudaError_t launch_mass_bwd(const Lv &a, const Lv &b, const void *ms, const void *gm,
+                            const LvOut &ga, const LvOut &gb, int64_t n, int dtype, cudaStream_t s) {
+  return dtype == GVX_F64 ? launch_mass_bwd_t<double>(a, b, ms, gm, ga, gb, n, s)
+                          : launch_mass_bwd_t<float>(a, b, ms, gm, ga, gb, n, s);
 }
 
 }  // namespace gvx

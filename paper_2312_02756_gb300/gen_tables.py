@@ -10,6 +10,12 @@ split into a float pair hi + lo:
 
 and the Cody-Waite splits of c and d (c0 with 9 significant bits, so n c0 is exact for
 |n| < 2^15; d0 with 13 bits, exact for j <= 2^11), 1/c, 1/d and pi as a float pair.
+
+Two tables at a power-of-two step h = 2^-8 serve the light-cone pair mass (mass_lc.cuh), whose
+argument reduction x = n h + r is then exact in float arithmetic:
+
+  kHypTab[n] = {cosh.hi, cosh.lo, sinh.hi, sinh.lo} of n h, n = 0 .. 2048 (x <= 8);
+  kSinTab[j] = {sin.hi, sin.lo, cos.hi, cos.lo} of j h, j = 0 .. 896 (x <= 3.5).
 """
 from __future__ import annotations
 
@@ -21,6 +27,9 @@ from decimal import Decimal, getcontext
 getcontext().prec = 60
 EXP_N = 1024
 TRIG_STEPS = 2048  # d = pi / TRIG_STEPS; the table covers [0, pi/2]
+LC_STEP_LOG2 = 8   # the light-cone tables' step is 2^-8
+HYP_N = 2048       # kHypTab covers [0, 8]
+SIN_N = 896        # kSinTab covers [0, 3.5]
 
 
 def _atan_inv(k: int) -> Decimal:
@@ -128,6 +137,23 @@ def generate() -> str:
     for j in range(TRIG_STEPS // 2 + 1):
         s, co = _sin_cos(j * d)
         a, b = _split(s)
+        e, f = _split(co)
+        out.append("  {%s, %s, %s, %s}," % (_lit(a), _lit(b), _lit(e), _lit(f)))
+    out.append("};")
+    step = Decimal(1) / (1 << LC_STEP_LOG2)
+    out.append("#define GVX_HYP_N %d" % HYP_N)
+    out.append("#define GVX_SIN_N %d" % SIN_N)
+    out.append("GVX_TABLE const gvx_f4 kHypTab[%d] = {" % (HYP_N + 1))
+    for n in range(HYP_N + 1):
+        ep, em = _exp(n * step), _exp(-n * step)
+        a, b = _split((ep + em) / 2)
+        e, f = _split((ep - em) / 2)
+        out.append("  {%s, %s, %s, %s}," % (_lit(a), _lit(b), _lit(e), _lit(f)))
+    out.append("};")
+    out.append("GVX_TABLE const gvx_f4 kSinTab[%d] = {" % (SIN_N + 1))
+    for j in range(SIN_N + 1):
+        s_, co = _sin_cos(j * step)
+        a, b = _split(s_)
         e, f = _split(co)
         out.append("  {%s, %s, %s, %s}," % (_lit(a), _lit(b), _lit(e), _lit(f)))
     out.append("};")

@@ -13,6 +13,7 @@
 #include "../paper_2312_02756_gb300/csrc/ptetaphie_ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_ff2.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_grad_ff2.cuh"
+#include "../paper_2312_02756_gb300/csrc/mass_lc.cuh"
 
 using namespace gvx::ffm;
 
@@ -28,6 +29,53 @@ int64_t ffh_mass(const double *a, const double *b, int64_t n, double *m, uint8_t
     bool f = pair_mass_ff(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], tables(), &out);
     ok[i] = f;
     m[i] = out;
+    c += f;
+  }
+  return c;
+}
+
+// The light-cone fast path of the FP64 mass kernel (mass_lc.cuh).
+int64_t ffh_mass_lc(const double *a, const double *b, int64_t n, double *m, uint8_t *ok) {
+  int64_t c = 0;
+  const LcTab T{kHypTab, kSinTab};
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = a + 4 * i, *y = b + 4 * i;
+    double out = NAN;
+    bool f = pair_mass_lc(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], T, &out);
+    ok[i] = f;
+    m[i] = out;
+    c += f;
+  }
+  return c;
+}
+
+// The jagged kernel's route for the same pairs: each particle's light-cone terms computed alone
+// (scalar) at the scale of the larger high word of (pt, |m|) over both legs and `extra` (an
+// event's other particles), then the shared pair step.  ok[i] = 0 where either route declines.
+int64_t ffh_mass_lc_event(const double *a, const double *b, const double *extra, int64_t n,
+                          double *m, uint8_t *ok) {
+  int64_t c = 0;
+  const LcTab T{kHypTab, kSinTab};
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = a + 4 * i, *y = b + 4 * i;
+    uint32_t w = umax32(umax32(dhi(x[0]), dhi(x[3]) & 0x7fffffffu), umax32(dhi(y[0]), dhi(y[3]) & 0x7fffffffu));
+    w = umax32(w, umax32(dhi(extra[i]), 0u));
+    const uint32_t ew = w & 0x7ff00000u, rb = ew - (127u << 20);
+    ff pt[2], Y[2], D[2];
+    for (int l = 0; l < 2; l++) {
+      const double *v = l ? y : x;
+      const ff ptf = cvt1(cvt_parts(dhi(v[0]), dlo(v[0]), rb));
+      const ff mmf = cvt1(cvt_parts(dhi(v[3]) & 0x7fffffffu, dlo(v[3]), rb));
+      const ff xe = cvt1(cvt_parts(umax32(dhi(v[1]) & 0x7fffffffu, 0x3E100000u), dlo(v[1]), kRebaseOne));
+      const LcLeg<ff> L = lc_leg(ptf, mmf, xe, T.hyp);
+      pt[l] = ptf;
+      Y[l] = L.Y;
+      D[l] = L.D;
+    }
+    ff m2s;
+    bool f = lc_pair_m2(pt[0], pt[1], Y[0], Y[1], D[0], D[1], x[1], y[1], x[2], y[2], T, &m2s);
+    ok[i] = f;
+    m[i] = f ? lc_mass_out(m2s, ew) : NAN;
     c += f;
   }
   return c;

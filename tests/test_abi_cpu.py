@@ -58,7 +58,8 @@ def test_mass_validation(lib):
     assert lib.gvx_invariant_mass(r(good), r(good), 516, 10, 0, None) == 5   # misaligned out
     assert lib.gvx_invariant_mass(r(_lv(1, (48, 0, 0, 0))), r(good), 512, 10, 0, None) == 5
     assert lib.gvx_invariant_mass(r(_lv(2, (64, 0, 0, 0))), r(good), 512, 10, 0, None) == 4
-    assert lib.gvx_invariant_mass_bwd(r(good), r(good), 512, r(good), None, 10, 0, None) == 1
+    assert lib.gvx_invariant_mass_bwd(r(good), r(good), None, 512, r(good), None, 10, 0, None) == 1
+    assert lib.gvx_invariant_mass_bwd(r(good), r(good), 4, 512, r(good), r(good), 10, 0, None) == 5
 
 
 def test_boost_validation(lib):

@@ -106,6 +106,62 @@ def test_ff_pair_mass_against_oracle(ffh, orc):
             assert ok.mean() > 0.998, k  # the fast path covers the collider-like workloads
 
 
+def _mass_lc(lib, a, b):
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    m, ok = np.empty(len(a)), np.empty(len(a), np.uint8)
+    lib.ffh_mass_lc(_p(a), _p(b), ctypes.c_int64(len(a)), _p(m), _p(ok))
+    return m, ok.astype(bool)
+
+
+def test_lc_pair_mass_against_oracle(ffh, orc):
+    """The light-cone fast path of the FP64 mass kernel (mass_lc.cuh), built for the host with the
+    hardware approximations' worst-case error modelled: pure relative error against O1 wherever
+    O1 is accurate (m >= 1e-9 (E1 + E2)) and against O2, on every value it accepts; it accepts all
+    but a few of the collider-like pairs."""
+    from test_oracle_pins import _adversarial_pairs
+    from helpers import edge_pairs
+    n = 100_000
+    cases = [(syn.ptetaphim(syn.rng(0), n), syn.ptetaphim(syn.rng(7), n)),
+             _adversarial_pairs(50_000, 104),
+             (syn.ptetaphim_light_mix(syn.rng(2), n), syn.ptetaphim_light_mix(syn.rng(3), n)),
+             edge_pairs()]
+    e = lambda x: np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
+    for k, (a, b) in enumerate(cases):
+        m, ok = _mass_lc(ffh, a, b)
+        o1, o2 = orc.mass_def(a, b, nthreads=8), orc.mass_fp64(a, b, nthreads=8)
+        cond = ok & (o1 >= 1e-9 * (e(a) + e(b)))
+        assert np.all(np.abs(m - o1)[cond] <= 2.5e-13 * o1[cond]), k
+        pos = ok & (o2 > 0)
+        assert np.all(np.abs(m - o2)[pos] <= 2.5e-13 * o2[pos]), k
+        assert np.all(m[ok & (o2 == 0)] == 0), k
+        if k < 3:
+            assert ok.mean() > 0.9999, k
+
+
+def test_lc_pair_mass_tiny_and_degenerate_legs(ffh, orc):
+    """Scale ratios at and beyond the fast path's 2^-40 rule, zero and denormal components, and
+    |d_phi| in and out of the band around 2 pi that the fast path leaves to FP64: whatever it
+    accepts is within its bound."""
+    g = syn.rng(12)
+    n = 20_000
+    a, b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    shrink = np.ldexp(1.0, -g.integers(0, 80, n))
+    a[:, 0] *= np.where(g.random(n) < 0.3, shrink, 1.0)
+    a[:, 3] *= np.where(g.random(n) < 0.3, shrink, 1.0)
+    b[:, 3] = np.where(g.random(n) < 0.2, 0.0, b[:, 3])
+    a[:, 0] = np.where(g.random(n) < 0.05, 0.0, a[:, 0])
+    b[:, 0] = np.where(g.random(n) < 0.02, 5e-324, b[:, 0])
+    w = g.random(n) < 0.2  # opposite azimuths near +-pi
+    a[w, 2] = np.pi - 10 ** g.uniform(-12, 0, w.sum())
+    b[w, 2] = -np.pi + 10 ** g.uniform(-12, 0, w.sum())
+    m, ok = _mass_lc(ffh, a, b)
+    o2 = orc.mass_fp64(a, b, nthreads=8)
+    pos = ok & (o2 > 0)
+    assert np.all(np.abs(m - o2)[pos] <= 2.5e-13 * o2[pos])
+    assert np.all(m[ok & (o2 == 0)] == 0)
+    assert 0.5 < ok.mean() < 1.0  # both branches are exercised
+
+
 def test_ff_unchecked_conversion_and_tiny_legs(ffh):
     """pt and m (and the boost's inputs) enter the ff paths through the unchecked conversion:
     bitwise the checked one on every value that one accepts, a signed zero for zeros, denormals

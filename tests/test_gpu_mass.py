@@ -1,7 +1,10 @@
-"""GPU parity of gvx_invariant_mass against the binary128 definition oracle (O1).
+"""GPU parity of gvx_invariant_mass against the oracle.
 
-FP64: every element within 1e-12 relative (plus an absolute floor of 1e-16 (E1 + E2), far below
-1e-12 m unless the pair is exactly degenerate, where the definition itself rounds to +-1e-17 E).
+FP64, against O2 (the oracle's cancellation-free FP64 identity, pinned to O1 at 1e-14 relative):
+every element within 1e-12 relative.  Against O1 (the definition in binary128): every element
+within 1e-12 relative wherever O1 is itself that accurate -- the definition cancels
+log10(E^2/m^2) of binary128's 34 digits, so that holds for m >= 1e-9 (E1 + E2); below that O1
+returns a rounding of a near-zero mass, and the kernel must lie within 1e-16 (E1 + E2) of it.
 FP32: the error per output against O1 on the exact upcast of the FP32 inputs is measured and held
 to the bound derived from the arithmetic (all terms non-negative: a few ulps).
 """
@@ -16,6 +19,7 @@ pytestmark = pytest.mark.gpu
 N0 = 65_536  # the small FP64 workload: 65,536 pairs
 N_FULL = 1 << 26
 TOL_F32 = 2.0e-6  # ~34 ulp of FP32; measured max is reported by the test
+O1_COND = 1e-9    # O1 keeps 1e-12 relative accuracy for m >= O1_COND (E1 + E2)
 
 
 def _energy_scale(a, b):
@@ -23,27 +27,43 @@ def _energy_scale(a, b):
     return e(a) + e(b)
 
 
-def _check_f64(got, ref, a, b):
-    bound = TOL_F64 * np.abs(ref) + 1e-16 * _energy_scale(a, b)
-    bad = np.abs(got - ref) > bound
-    assert not bad.any(), (np.flatnonzero(bad)[:5], got[bad][:5], ref[bad][:5])
+def _check_f64(got, a, b, o1=None, o2=None, label=""):
+    """Returns the max relative errors (vs O1 where it is accurate, vs O2 everywhere)."""
+    scale = _energy_scale(a, b)
+    out = []
+    if o1 is not None:
+        cond = o1 >= O1_COND * scale
+        rel = np.abs(got - o1)[cond] / o1[cond]
+        bad = np.flatnonzero(cond)[rel > TOL_F64]
+        assert bad.size == 0, (label, "O1", bad[:5], got[bad][:5], o1[bad][:5])
+        near0 = ~cond
+        assert np.all(np.abs(got - o1)[near0] <= 1e-16 * scale[near0]), (label, "O1 near 0")
+        out.append(rel.max() if rel.size else 0.0)
+    if o2 is not None:
+        pos = o2 > 0
+        rel = np.abs(got - o2)[pos] / o2[pos]
+        bad = np.flatnonzero(pos)[rel > TOL_F64]
+        assert bad.size == 0, (label, "O2", bad[:5], got[bad][:5], o2[bad][:5])
+        assert np.all(np.abs(got[~pos]) <= 1e-16 * scale[~pos]), (label, "O2 zero")
+        out.append(rel.max() if rel.size else 0.0)
+    print("FP64 mass %s: max rel err %s" % (label, " / ".join("%.3e" % e for e in out)))
+    return out
 
 
 @pytest.fixture(scope="module")
 def cfg0(orc):
     g = syn.rng(0)
     a, b = syn.ptetaphim(g, N0), syn.ptetaphim(g, N0)
-    return a, b, orc.mass_def(a, b, nthreads=8)
+    return a, b, orc.mass_def(a, b, nthreads=8), orc.mass_fp64(a, b, nthreads=8)
 
 
 @pytest.mark.parametrize("la,lb", [("soa", "soa"), ("aos", "aos"), ("soa", "aos"), ("aos", "soa")])
 def test_mass_f64_small_workload(cfg0, la, lb):
     torch_cuda()
     import paper_2312_02756_gb300 as gvx
-    a, b, ref = cfg0
+    a, b, o1, o2 = cfg0
     m = gvx.invariant_mass(dev(a, la), dev(b, lb), la, lb).cpu().numpy()
-    _check_f64(m, ref, a, b)
-    print("FP64 mass vs O1 (%s/%s): %s" % (la, lb, summary(rel_err(m, ref))))
+    _check_f64(m, a, b, o1, o2, "65,536 pairs %s/%s vs O1 / O2" % (la, lb))
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 255, 256, 257, 4097, 77_777])
@@ -55,46 +75,51 @@ def test_mass_f64_ragged_sizes(orc, n):
     for layout in ("soa", "aos"):
         m = gvx.invariant_mass(dev(a, layout), dev(b, layout), layout, layout).cpu().numpy()
         assert m.shape == (n,)
-        _check_f64(m, orc.mass_def(a, b, nthreads=8), a, b)
+        _check_f64(m, a, b, orc.mass_def(a, b, nthreads=8), orc.mass_fp64(a, b),
+                   "n=%d %s" % (n, layout))
 
 
 def test_mass_f64_edge_cases(orc):
     torch = torch_cuda()
     import paper_2312_02756_gb300 as gvx
     a, b = edge_pairs()
-    ref = orc.mass_def(a, b)
     for layout in ("soa", "aos"):
         m = gvx.invariant_mass(dev(a, layout), dev(b, layout), layout, layout).cpu().numpy()
-        _check_f64(m, ref, a, b)
-    # adversarial near-collinear light pairs: the plain FP64 form loses up to 1e-8 here
+        _check_f64(m, a, b, orc.mass_def(a, b), orc.mass_fp64(a, b), "edge pairs " + layout)
+    # adversarial near-collinear light pairs (the plain FP64 form loses up to 1e-8 here) and the
+    # light/heavy particle mix, in FP64
     from test_oracle_pins import _adversarial_pairs
-    a, b = _adversarial_pairs(50_000, 104)
-    m = gvx.invariant_mass(dev(a), dev(b)).cpu().numpy()
-    _check_f64(m, orc.mass_def(a, b, nthreads=8), a, b)
+    for label, (a, b) in (("adversarial", _adversarial_pairs(50_000, 104)),
+                          ("light mix", (syn.ptetaphim_light_mix(syn.rng(20), 50_000),
+                                         syn.ptetaphim_light_mix(syn.rng(21), 50_000)))):
+        m = gvx.invariant_mass(dev(a), dev(b)).cpu().numpy()
+        _check_f64(m, a, b, orc.mass_def(a, b, nthreads=8), orc.mass_fp64(a, b, nthreads=8), label)
     # n = 0
     e = torch.empty((0, 4), dtype=torch.float64, device="cuda")
     assert gvx.invariant_mass(e, e).shape == (0,)
 
 
-def test_mass_f64_full_size_sampled(orc):
-    """2^26 pairs in both layouts (the benchmark launch): 2^16 sampled outputs against O1,
-    and properties of all outputs."""
+def test_mass_f64_full_size(orc):
+    """2^26 pairs in both layouts (the benchmark launch): every output against O2, and 2^16
+    sampled outputs against O1."""
     torch = torch_cuda()
     import paper_2312_02756_gb300 as gvx
     g = syn.rng(1)
     a, b = syn.ptetaphim(g, N_FULL), syn.ptetaphim(g, N_FULL)
+    o2 = orc.mass_fp64(a, b, nthreads=16)
     idx = np.sort(syn.rng(101).choice(N_FULL, 1 << 16, replace=False))
-    ref = orc.mass_def(a[idx], b[idx], nthreads=8)
+    o1 = orc.mass_def(a[idx], b[idx], nthreads=16)
     for layout in ("soa", "aos"):
         da, db = dev(a, layout), dev(b, layout)
         m = gvx.invariant_mass(da, db, layout, layout)
         torch.cuda.synchronize()
         del da, db
         mh = m.cpu().numpy()
-        assert np.all(np.isfinite(mh)) and np.all(mh >= 0)
-        _check_f64(mh[idx], ref, a[idx], b[idx])
         del m
         torch.cuda.empty_cache()
+        assert np.all(np.isfinite(mh)) and np.all(mh >= 0)
+        _check_f64(mh, a, b, o2=o2, label="2^26 pairs %s, every output vs O2" % layout)
+        _check_f64(mh[idx], a[idx], b[idx], o1=o1, label="2^26 pairs %s, 2^16 samples vs O1" % layout)
 
 
 def test_mass_f32_error_per_output(orc):
