@@ -113,7 +113,7 @@ constexpr int kWaves = 8;
 // per_block per CTA and pass; 0 means one per thread).
 template <typename Kernel>
 inline unsigned balanced_grid(Kernel k, int threads, size_t smem, int64_t n, int *cache,
-                              int64_t per_block = 0) {
+                              int64_t per_block = 0, int waves = kWaves) {
   if (*cache <= 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess ||
@@ -123,18 +123,19 @@ inline unsigned balanced_grid(Kernel k, int threads, size_t smem, int64_t n, int
   }
   if (per_block <= 0) per_block = threads;
   int64_t need = (n + per_block - 1) / per_block;
-  int64_t cap = (int64_t)num_sms() * *cache * kWaves;
+  int64_t cap = (int64_t)num_sms() * *cache * waves;
   int64_t g = need < cap ? need : cap;
   return (unsigned)(g < 1 ? 1 : g);
 }
 
 // balanced_grid for one kernel instantiation, its occupancy cached per device.
 template <auto Kernel>
-inline unsigned balanced_grid_of(int threads, size_t smem, int64_t n, int64_t per_block = 0) {
+inline unsigned balanced_grid_of(int threads, size_t smem, int64_t n, int64_t per_block = 0,
+                                 int waves = kWaves) {
   static int occ[64];
   int dev = 0;
   cudaGetDevice(&dev);
-  return balanced_grid(Kernel, threads, smem, n, &occ[dev & 63], per_block);
+  return balanced_grid(Kernel, threads, smem, n, &occ[dev & 63], per_block, waves);
 }
 
 // Record a device-detected error (the first one since the last read wins).

@@ -250,15 +250,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
         const uint32_t he = ffm::dhi(eta) & 0x7fffffffu, hf = ffm::dhi(phi) & 0x7fffffffu;
         int sc = wmax - (200u << 20) < (1700u << 20) &&
                          ffm::umin32(hp - 0x100000u, hm - 0x100000u) >= ew - (41u << 20) &&
-                         he < 0x40200000u && hf < 0x400C0000u
+                         ffm::umax32(hp, hm) >= 0x100000u && he < 0x40200000u && hf < 0x400C0000u
                      ? (int)ew
                      : kNoFast;
         if (sc != kNoFast) {
           const uint32_t rb = ew - (127u << 20);
           const ffm::ff ptf = ffm::cvt1(ffm::cvt_parts(hp, ffm::dlo(pt), rb));
           const ffm::ff mmf = ffm::cvt1(ffm::cvt_parts(hm, ffm::dlo(m), rb));
-          const ffm::ff xe = ffm::cvt1(ffm::cvt_parts(ffm::umax32(he, 0x3E100000u), ffm::dlo(eta),
-                                                      ffm::kRebaseOne));
+          const ffm::ff xe = ffm::cvt1(ffm::cvt_parts_normal(ffm::umax32(he, 0x3E100000u),
+                                                             ffm::dlo(eta), ffm::kRebaseOne));
           ffm::ff sh, sn, cs;
           const ffm::LcLeg<ffm::ff> L = ffm::lc_leg(ptf, mmf, xe, T.hyp, &sh);
           ffm::sincos_lc(ffm::cvt1(ffm::cvt_parts(hf, ffm::dlo(phi), ffm::kRebaseOne)), T.sin, &sn, &cs);
@@ -310,9 +310,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
         bool done = false;
         const int sc = s_fs[ia];
         if (sc != kNoFast && s_fs[ib] != kNoFast) {
-          ffm::ff m2s;
-          if (ffm::lc_pair_m2(s_pt[ia], s_pt[ib], s_Y[ia], s_Y[ib], s_D[ia], s_D[ib], s_eta[ia],
-                              s_eta[ib], s_phi[ia], s_phi[ib], T, &m2s)) {
+          ffm::ff S, m2s;
+          const bool oks = ffm::lc_pair_S(s_eta[ia], s_eta[ib], s_phi[ia], s_phi[ib], T, &S);
+          if (ffm::lc_pair_m2(s_pt[ia], s_pt[ib], s_Y[ia], s_Y[ib], s_D[ia], s_D[ib], S, &m2s) && oks) {
             mass = ffm::lc_mass_out(m2s, (uint32_t)sc);
             done = true;
           }

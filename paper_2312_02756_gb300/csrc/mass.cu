@@ -61,17 +61,21 @@ __device__ __forceinline__ double pair_mass_f64(const V4<double> &x, const V4<do
   return out;
 }
 
-// FP64 forward: grid-stride, one pair per thread and step; 64 registers, so four CTAs of 256
-// threads share an SM.  For a leg in SoA layout (four separate arrays), lanes 0..7 of each warp
+// FP64 forward: grid-stride, one pair per thread and step; 64 registers, eight CTAs of 128
+// threads per SM, a grid of 32 times the resident CTAs (small CTAs and many waves even out the
+// SMs' progress: 2-3% faster than four CTAs of 256 and 8 waves on GB300).  For a leg in SoA layout (four separate arrays), lanes 0..7 of each warp
 // first ask L2 to prefetch the warp's next 32 elements of each array (one 128-byte line per
 // lane), so that the next step's eight loads find them in L2 rather than in HBM.
 template <int LA, int LB>
-__global__ void __launch_bounds__(256, 4) mass_f64_kernel(Lv a, Lv b, double *__restrict__ m, int64_t n) {
+__global__ void __launch_bounds__(128, 8) mass_f64_kernel(Lv a, Lv b, double *__restrict__ m, int64_t n) {
   const ffm::LcTab T{ffm::kHypTab, ffm::kSinTab};
   const int lane = threadIdx.x & 31;
   const int leg = (lane >> 2) & 1;  // lanes 0-3: leg a's arrays, 4-7: leg b's
   const bool soa = leg ? LB == GVX_SOA : LA == GVX_SOA;
-  const char *pbase = (const char *)(leg ? b : a).c[lane & 3] + 128 * ((lane >> 3) & 1);
+  // the lane's array by selects (an index into the parameters would copy them to local memory)
+  const void *pa = (lane & 2) ? ((lane & 1) ? a.c[3] : a.c[2]) : ((lane & 1) ? a.c[1] : a.c[0]);
+  const void *pb = (lane & 2) ? ((lane & 1) ? b.c[3] : b.c[2]) : ((lane & 1) ? b.c[1] : b.c[0]);
+  const char *pbase = (const char *)(leg ? pb : pa) + 128 * ((lane >> 3) & 1);
   const bool prefetch = soa && lane < 16;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -96,11 +100,13 @@ __global__ void __launch_bounds__(256) mass_bwd_kernel(Lv a, Lv b, const T *__re
   }
 }
 
+constexpr int kMassWaves = 32;
+
 template <int LA, int LB>
 void launch_mass_f64_l(const Lv &a, const Lv &b, double *m, int64_t n, cudaStream_t s) {
-  const int threads = 256;
-  mass_f64_kernel<LA, LB><<<balanced_grid_of<mass_f64_kernel<LA, LB>>(threads, 0, n), threads, 0, s>>>(
-      a, b, m, n);
+  const int threads = 128;
+  mass_f64_kernel<LA, LB><<<balanced_grid_of<mass_f64_kernel<LA, LB>>(threads, 0, n, 0, kMassWaves),
+                            threads, 0, s>>>(a, b, m, n);
 }
 
 cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaStream_t s) {

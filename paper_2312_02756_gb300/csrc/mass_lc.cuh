@@ -26,7 +26,8 @@
 // common power-of-two scale of pt and m (the largest brought into [1, 2)).
 //
 // Fast-path domain (anything else returns false and the caller takes the FP64 formulas):
-//  - pt >= 0 (not -0), |eta| < 8, |phi| < 3.5, all inputs finite;
+//  - pt >= 0 (not -0), |eta| < 8, |phi| < 3.5, all inputs finite, neither leg a zero vector
+//    (pt = m = 0);
 //  - the pair's scale 2^e of pt and m with 2^-823 <= 2^e < 2^877, and every nonzero pt and m
 //    at least 2^-40 of it (denormal inputs count as zero: below 2^-199 of the scale);
 //  - |d_phi| not within 2^-6 of 2 pi (there the FP64 rounding of phi1 - phi2 would matter);
@@ -122,6 +123,14 @@ GVX_HD CvtParts cvt_parts(uint32_t wh, uint32_t wl, uint32_t rb) {
   return {hb, el | ((wl >> 6) & 0x7fffffu), el};
 }
 
+// cvt_parts for a value known to rebase to an exponent in [24, 254] (|eta| raised to >= 2^-30):
+// no clamps.
+GVX_HD CvtParts cvt_parts_normal(uint32_t wh, uint32_t wl, uint32_t rb) {
+  const uint32_t hb = funnel_l3(wl, wh - rb);
+  const uint32_t el = (hb & 0x7f800000u) - (23u << 23);
+  return {hb, el | ((wl >> 6) & 0x7fffffu), el};
+}
+
 GVX_HD ff2 cvt2(const CvtParts &a, const CvtParts &b) {
   ff2 r;
   r.hi = mk2(u2f(a.hb), u2f(b.hb));
@@ -182,25 +191,25 @@ GVX_HD F lc_add(const F &x, const F &y) {
   const auto s = vadd(a, b);
   return {s, vadd(vsub(b, vsub(s, a)), vadd(x.lo, y.lo))};
 }
-// sqrt(x), x >= 0: s = x.hi rs with the approximate reciprocal square root rs, corrected once
-// from the float-float residual x - s^2.  With rs within 2^-22.9 relative, the corrected root is
+// sqrt(x), x.hi > 0: s = x.hi rs with the approximate reciprocal square root rs, corrected
+// once from the float-float residual x - s^2.  With rs within 2^-22.9 relative, the corrected root is
 // within ~1.5 (2^-22.9)^2 = 2^-45.2 relative (the correction removes the first-order error).
 template <class F>
 GVX_HD F lc_sqrt(const F &x) {
   using V = lane_t<F>;
-  const V rs = vrsqrt(vmax(x.hi, vbc(1e-30f, V{})));
+  const V rs = vrsqrt(x.hi);
   const V s = vmul(x.hi, rs);
   const V pp = vmul(s, s);
   const V pe = vfma(s, s, vneg(pp));
   const V res = vadd(vsub(vsub(x.hi, pp), pe), x.lo);
   return {s, vmul(res, vmul(rs, vbc(0.5f, V{})))};
 }
-// q / y, y > 0 or q = 0 (then 0): q1 = q.hi / y.hi from the approximate reciprocal, one
-// correction from the float-float remainder.
+// q / y, y.hi > 0: q1 = q.hi / y.hi from the approximate reciprocal, one correction from the
+// float-float remainder.
 template <class F>
 GVX_HD F lc_div(const F &q, const F &y) {
   using V = lane_t<F>;
-  const V ry = vrcp(vmax(y.hi, vbc(1e-30f, V{})));
+  const V ry = vrcp(y.hi);
   const V q1 = vmul(q.hi, ry);
   const V r0 = vfma(vneg(q1), y.hi, q.hi);
   const V r1 = vfma(vneg(q1), y.lo, vadd(r0, q.lo));
@@ -371,14 +380,10 @@ GVX_HD void sincos_lc(const ff &x, const gvx_f4 *sintab, ff *sn, ff *cs) {
 
 // ---- the pair ------------------------------------------------------------------------------
 
-// The scaled m^2 of a pair from its legs' scaled pt, Y and D and its raw angles:
-//   m^2 = (D1 + D2)(Y1 + Y2) + 4 pt1 pt2 (sinh^2(|d_eta|/2) + sin^2(|d_phi|/2)),
-// the two half-angle functions as the lanes of one paired table evaluation.  False when the
-// pair is outside the fast path: |d_phi|/2 within 2^-7 of pi (there the FP64 rounding of
-// phi1 - phi2 matters), or the scaled m^2 nonzero and below 2^-80 (where terms flushed below
-// the float range could matter).
-GVX_HD bool lc_pair_m2(ff pt1, ff pt2, ff Y1, ff Y2, ff D1, ff D2, double eta1, double eta2,
-                       double phi1, double phi2, const LcTab &T, ff *m2s) {
+// The angular factor of a pair, S = sinh^2(|d_eta|/2) + sin^2(|d_phi|/2), from its raw angles,
+// the two half-angle functions as the lanes of one paired table evaluation.  False when
+// |d_phi|/2 is within 2^-7 of pi (there the FP64 rounding of phi1 - phi2 matters).
+GVX_HD bool lc_pair_S(double eta1, double eta2, double phi1, double phi2, const LcTab &T, ff *S) {
   const double de = eta1 - eta2, dp = phi1 - phi2;  // FP64: exact where the legs are close
   const uint32_t hde = dhi(de) & 0x7fffffffu, hdp = dhi(dp) & 0x7fffffffu;
   const CvtParts cp = cvt_parts(hdp, dlo(dp), kRebaseHalf);
@@ -392,16 +397,21 @@ GVX_HD bool lc_pair_m2(ff pt1, ff pt2, ff Y1, ff Y2, ff D1, ff D2, double eta1, 
   uint32_t nj[2];
   ff2 r = lc_reduce(xa, nj);
   r.lo = add2(r.lo, mk2(0.0f, lo3));
-  const bool ok = nj[1] - 802u > 4u;  // |d_phi|/2 within 2^-7 of pi
   const gvx_f4 th = ldtab(&T.hyp[umin32(nj[0], GVX_HYP_N)]);
   const gvx_f4 ts = ldtab(&T.sin[umin32(nj[1], GVX_SIN_N)]);
   const ff2 A = {mk2(th.z, ts.x), mk2(th.w, ts.y)};
   const ff2 B = {mk2(th.x, ts.z), mk2(th.y, ts.w)};
   const ff2 w = lc_sqr(tab_eval(A, B, r, mk2(0.5f, -0.5f)));
-  const ff S = lc_add(lane_x(w), lane_y(w));
+  *S = lc_add(lane_x(w), lane_y(w));
+  return nj[1] - 802u > 4u;  // |d_phi|/2 within 2^-7 of pi
+}
+
+// The scaled m^2 = (D1 + D2)(Y1 + Y2) + 4 pt1 pt2 S from the legs' scaled pt, Y and D; false
+// when it is nonzero and below 2^-80 (where terms flushed below the float range could matter).
+GVX_HD bool lc_pair_m2(ff pt1, ff pt2, ff Y1, ff Y2, ff D1, ff D2, ff S, ff *m2s) {
   const ff ta = lc_mul(lc_mul(pt1, pt2), S);
   *m2s = lc_add(lc_mul(lc_add(D1, D2), lc_add(Y1, Y2)), ff{fmul(ta.hi, 4.0f), fmul(ta.lo, 4.0f)});
-  return ok && (m2s->hi >= 8.27180613e-25f || m2s->hi == 0.0f);  // 2^-80
+  return m2s->hi >= 8.27180613e-25f || m2s->hi == 0.0f;  // 2^-80
 }
 
 // The scaled float-float m^2 of a pair and the scale exponent field; false outside the
@@ -419,18 +429,22 @@ GVX_HD bool pair_m2_lc(double pt1, double eta1, double phi1, double m1, double p
   const uint32_t he1 = dhi(eta1) & 0x7fffffffu, he2 = dhi(eta2) & 0x7fffffffu;
   const uint32_t hf1 = dhi(phi1) & 0x7fffffffu, hf2 = dhi(phi2) & 0x7fffffffu;
   const bool ok = wmax - (200u << 20) < (1700u << 20) && vmin_ >= ew - (41u << 20) &&
+                  umin32(umax32(hp1, hm1), umax32(hp2, hm2)) >= 0x100000u &&  // no zero leg
                   umax32(he1, he2) < 0x40200000u && umax32(hf1, hf2) < 0x400C0000u;
   *emax_w = ew;
+  // -- the angular factor first: the raw angles are then dead during the legs --
+  ff S;
+  const bool oks = lc_pair_S(eta1, eta2, phi1, phi2, T, &S);
   // -- the legs (lane x: leg 1, lane y: leg 2), pt and m scaled by 2^(1023 - emax) --
   const uint32_t rb = ew - (127u << 20);
   const ff2 pt = cvt2(cvt_parts(hp1, dlo(pt1), rb), cvt_parts(hp2, dlo(pt2), rb));
   const ff2 mm = cvt2(cvt_parts(hm1, dlo(m1), rb), cvt_parts(hm2, dlo(m2), rb));
   // |eta| below 2^-30 is raised to [2^-30, 2^-29): cosh changes by less than 2^-58
-  const ff2 x = cvt2(cvt_parts(umax32(he1, 0x3E100000u), dlo(eta1), kRebaseOne),
-                     cvt_parts(umax32(he2, 0x3E100000u), dlo(eta2), kRebaseOne));
+  const ff2 x = cvt2(cvt_parts_normal(umax32(he1, 0x3E100000u), dlo(eta1), kRebaseOne),
+                     cvt_parts_normal(umax32(he2, 0x3E100000u), dlo(eta2), kRebaseOne));
   const LcLeg<ff2> L = lc_leg(pt, mm, x, T.hyp);
   return lc_pair_m2(lane_x(pt), lane_y(pt), lane_x(L.Y), lane_y(L.Y), lane_x(L.D), lane_y(L.D),
-                    eta1, eta2, phi1, phi2, T, m2s) && ok;
+                    S, m2s) && ok && oks;
 }
 
 // m = sqrt(m2s) * 2^(e - 1023), e the scale's exponent (field ew = e << 20), as a double: the

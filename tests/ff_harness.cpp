@@ -72,8 +72,9 @@ int64_t ffh_mass_lc_event(const double *a, const double *b, const double *extra,
       Y[l] = L.Y;
       D[l] = L.D;
     }
-    ff m2s;
-    bool f = lc_pair_m2(pt[0], pt[1], Y[0], Y[1], D[0], D[1], x[1], y[1], x[2], y[2], T, &m2s);
+    ff S, m2s;
+    const bool oks = lc_pair_S(x[1], y[1], x[2], y[2], T, &S);
+    bool f = lc_pair_m2(pt[0], pt[1], Y[0], Y[1], D[0], D[1], S, &m2s) && oks;
     ok[i] = f;
     m[i] = f ? lc_mass_out(m2s, ew) : NAN;
     c += f;
