@@ -153,6 +153,21 @@ def cpu_oracle_rate(a, b, v, beta, reps=1):
     return 3 * n / (2 * t_mass + t_boost), cores, t_mass, t_boost
 
 
+def cpu_oracle_rate_1t(a, b, v, beta, sample=1 << 22):
+    """O2 on one host thread (the paper measures its speed-ups against a single-threaded CPU run,
+    Sec. 5.2) over the first `sample` rows: outputs/s for the step's mix."""
+    import oracle
+    oracle.build()
+    a, b, v, beta = a[:sample], b[:sample], v[:sample], beta[:sample]
+    t0 = time.perf_counter()
+    oracle.mass_fp64(a, b, nthreads=1)
+    t_mass = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.boost_fp64(v, beta, nthreads=1)
+    t_boost = time.perf_counter() - t0
+    return 3 * a.shape[0] / (2 * t_mass + t_boost), t_mass, t_boost
+
+
 class Step:
     """The timed step: mass SoA, mass AoS, boost, called through the C ABI with preallocated
     outputs, one CUDA-event pair around every launch."""
@@ -576,10 +591,14 @@ def run_gvx(args):
             line["e2e"] = res
     if rank == 0 and not args.no_cpu:
         rate, cores, tm, tb = cpu_oracle_rate(a, b, v, beta)
+        r1, tm1, tb1 = cpu_oracle_rate_1t(a, b, v, beta)
         line["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "the whole 2^26 workload (mass twice, boost once) through the FP64 oracle "
-                      "tier O2 on all host cores: mass %.0f ms, boost %.0f ms" % (tm * 1e3, tb * 1e3)}
+                      "tier O2 on all host cores: mass %.0f ms, boost %.0f ms" % (tm * 1e3, tb * 1e3),
+            "single_thread": {"value": r1, "unit": UNIT, "cores": 1,
+                              "sample": "2^22 pairs and 2^22 boosts through O2 on one thread: "
+                                        "mass %.0f ms, boost %.0f ms" % (tm1 * 1e3, tb1 * 1e3)}}
     del step
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_forms:
@@ -600,8 +619,9 @@ def run_gvx(args):
 # The sources each timed kernel's device code is built from (the committed counters are valid
 # while these match; gvx_internal.h, which only declares the host-side launch functions, is left
 # out).
-_MASS_SRC = ("mass.cu", "mass_ff.cuh", "mass_ff2.cuh", "mass_grad_ff2.cuh", "ff2.cuh",
-             "ff_tables.cuh", "ff.cuh", "pair_math.cuh", "common.cuh", "../gen_tables.py")
+_MASS_SRC = ("mass.cu", "mass_lc.cuh", "mass_ff.cuh", "mass_ff2.cuh", "mass_grad_ff2.cuh",
+             "ff2.cuh", "ff_tables.cuh", "ff.cuh", "pair_math.cuh", "common.cuh",
+             "../gen_tables.py")
 KERNEL_SOURCES = {
     "mass_f64_soa": _MASS_SRC,
     "mass_f64_aos": _MASS_SRC,

@@ -284,7 +284,9 @@ gvx_status gvx_event_pair_select(const gvx_lv *particles, const int64_t *offsets
  * large (262,400 bytes); every GPU that loads the library keeps it until the process exits.
  * Arguments and results are those of gvx_event_pair_masses.  More than GVX_NOALLOC_MAX_EVENTS
  * events returns GVX_ERR_SIZE and launches nothing.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * array's device address (cudaGetSymbolAddress) and caches it per device; make that first call
+ * before any stream capture, and make no call on a device after cudaDeviceReset of it (the
+ * cached address belonged to the reset context).
  * All calls share the one array (each clears what it uses before its kernel): two calls that can
  * run at the same time on the GPU (unordered streams) race and give wrong results -- order them.
  * Nothing here calls cudaMalloc, cudaFree or an allocating library routine.

@@ -164,6 +164,8 @@ int num_sms() {
   return cache[d];
 }
 
+gvx_status status_from_cuda(cudaError_t e) { return from_cuda(e); }
+
 int32_t *device_status_word() {
   static int32_t *cache[kMaxDevices] = {nullptr};
   int d = current_device();

@@ -27,6 +27,10 @@ int num_sms();
 // Device status word (one per device, in device memory owned by the library).
 int32_t *device_status_word();
 
+// GVX_OK for cudaSuccess; otherwise GVX_ERR_CUDA, with the error recorded for
+// gvx_last_cuda_error on this host thread.
+gvx_status status_from_cuda(cudaError_t e);
+
 cudaError_t launch_mass(const Lv &a, const Lv &b, void *m, int64_t n, int dtype,
                         cudaStream_t s);
 cudaError_t launch_mass_bwd(const Lv &a, const Lv &b, const void *ms, const void *gm,

@@ -3,7 +3,8 @@
 //
 // The scratch (tile counter + look-back descriptors) lives in g_scratch below.  Host code never
 // uses the name g_scratch as an address: the device address comes from cudaGetSymbolAddress,
-// taken once per device (with that device current) by the first call on it and cached.
+// taken once per device (with that device current) by the first call on it and cached.  The
+// cached address belongs to the context it was taken in: after cudaDeviceReset it is stale.
 // Every call shares the one array; each call clears the part it uses before its kernel runs, so
 // calls that overlap on the GPU (different streams, no ordering between them) race on it.
 #include <cuda_runtime.h>
@@ -80,8 +81,7 @@ extern "C" gvx_status gvx_event_pair_masses_noalloc(const gvx_lv *particles,
   if ((uintptr_t)offsets % 8 || (uintptr_t)pair_offsets % 8) return GVX_ERR_ALIGN;
   cudaStream_t s = (cudaStream_t)stream;
   if (n_events == 0) {
-    return cudaMemsetAsync(pair_offsets, 0, sizeof(int64_t), s) == cudaSuccess ? GVX_OK
-                                                                              : GVX_ERR_CUDA;
+    return gvx::status_from_cuda(cudaMemsetAsync(pair_offsets, 0, sizeof(int64_t), s));
   }
   gvx_status st = check_lv64(event_sum);
   if (st != GVX_OK) return st;
@@ -97,5 +97,5 @@ extern "C" gvx_status gvx_event_pair_masses_noalloc(const gvx_lv *particles,
                                       n_events, n_particles, pair_offsets, pair_m, pair_capacity,
                                       gvx::as_out(*event_sum), ws, false, s);
   }
-  return e == cudaSuccess ? GVX_OK : GVX_ERR_CUDA;
+  return gvx::status_from_cuda(e);
 }

@@ -154,6 +154,34 @@ def test_boost_grad_f64_shared_velocity(orc):
     assert np.all(np.abs(gb - rb) <= TOL_F64 * np.sum(np.abs(rb_each), axis=0))
 
 
+def test_boost_grad_f64_finite_differences():
+    """Central differences of the GPU boost, h = 1e-6 relative (max(|x|, 1)), for the loss
+    sum(gout . boost(v, beta)): the gradients with respect to the 4-vector and to beta, per
+    vector within 1e-6 of the largest gradient component (FD truncation and rounding at this step
+    are far below that)."""
+    torch = torch_cuda()
+    import paper_2312_02756_gb300 as gvx
+    g = syn.rng(49)
+    n = 4096
+    v, beta = syn.pxpypze(g, n), syn.velocities(g, n, 0.99)
+    gout = syn.upstream(g, (n, 4))
+    gv, gb = _boost_grads(v, beta, gout)
+    loss = lambda vv, bb: np.sum(gvx.boost(dev(vv), dev(bb)).cpu().numpy() * gout, axis=1)
+    for x, grad, width, which in ((v, gv, 4, "v"), (beta, gb, 3, "beta")):
+        scale = np.abs(grad).max(axis=1) + 1e-300
+        for k in range(width):
+            h = 1e-6 * np.maximum(np.abs(x[:, k]), 1.0) if which == "v" else np.full(n, 1e-6)
+            hi, lo = x.copy(), x.copy()
+            hi[:, k] += h
+            lo[:, k] -= h
+            if which == "v":
+                fd = (loss(hi, beta) - loss(lo, beta)) / (hi[:, k] - lo[:, k])
+            else:
+                fd = (loss(v, hi) - loss(v, lo)) / (hi[:, k] - lo[:, k])
+            err = np.abs(fd - grad[:, k]) / scale
+            assert err.max() <= 1e-6, (which, k, err.max())
+
+
 def test_boost_grad_autograd_gradcheck():
     torch = torch_cuda()
     import paper_2312_02756_gb300 as gvx
