@@ -20,6 +20,7 @@
 #include "mass_ff2.cuh"
 #include "mass_grad_ff2.cuh"
 #include "mass_lc.cuh"
+#include "mass_lc_grad.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
@@ -28,6 +29,10 @@ namespace {
 // FP32: memory-bound, so each thread loads kUnroll pairs (strided by the grid) before it
 // computes any of them, to keep more loads in flight per SM.
 constexpr int kUnroll = 4;
+
+// Grid of the FP64 kernels: 32 times the resident CTAs (small CTAs and many waves even out the
+// SMs' progress).
+constexpr int kMassWaves = 32;
 
 template <typename T, int LA, int LB>
 __global__ void __launch_bounds__(256) mass_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
@@ -100,8 +105,6 @@ __global__ void __launch_bounds__(256) mass_bwd_kernel(Lv a, Lv b, const T *__re
   }
 }
 
-constexpr int kMassWaves = 32;
-
 template <int LA, int LB>
 void launch_mass_f64_l(const Lv &a, const Lv &b, double *m, int64_t n, cudaStream_t s) {
   const int threads = 128;
@@ -122,15 +125,14 @@ cudaError_t launch_mass_f64(const Lv &a, const Lv &b, void *m, int64_t n, cudaSt
   return cudaGetLastError();
 }
 
-// FP64 adjoint: float-float evaluation (mass_ff.cuh, pair_mass_grad_ff; the two legs on paired
-// FP32 instructions, mass_grad_ff2.cuh) with the FP64 formulas kept for lanes outside its domain.
+// FP64 adjoint: the light-cone float-float evaluation (mass_lc_grad.cuh; the two legs on paired
+// FP32 instructions, the forward's saved masses used where given) with the FP64 formulas kept for
+// lanes outside its domain.
 template <int LA, int LB, int LGA, int LGB>
-__global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ ms,
+__global__ void __launch_bounds__(128, 6) mass_bwd_f64_kernel(Lv a, Lv b, const double *__restrict__ ms,
                                                            const double *__restrict__ gm,
                                                            LvOut ga, LvOut gb, int64_t n) {
-  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
-  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
-  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
+  const ffm::LcTab T{ffm::kHypTab, ffm::kSinTab};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     V4<double> x = ld4<double, LA>(a, i);
@@ -138,12 +140,13 @@ __global__ void __launch_bounds__(256, 3) mass_bwd_f64_kernel(Lv a, Lv b, const 
     double g = ld_s(gm + i);
     double o[8];
     V4<double> g1, g2;
-    if (ms && ld_s(ms + i) == 0.0) {
-      g1 = {0, 0, 0, 0};
-      g2 = {0, 0, 0, 0};
-    } else if (ffm::pair_mass_grad_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
+    const double msv = ms ? ld_s(ms + i) : 0.0;
+    if (ffm::pair_mass_grad_lc(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, ms != nullptr, msv, T, o)) {
       g1 = {o[0], o[1], o[2], o[3]};
       g2 = {o[4], o[5], o[6], o[7]};
+    } else if (ms && msv == 0.0) {
+      g1 = {0, 0, 0, 0};
+      g2 = {0, 0, 0, 0};
     } else {
       pair_mass_grad(x, y, g, g1, g2);
     }
@@ -176,7 +179,8 @@ void launch_bwd_one(int threads, const Lv &a, const Lv &b, const T *ms, const T 
                     const LvOut &ga, const LvOut &gb, int64_t n, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
     constexpr auto k = mass_bwd_f64_kernel<LA, LB, LGA, LGB>;
-    k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, ms, gm, ga, gb, n);
+    constexpr int t64 = 128;  // the FP64 kernel's launch bounds
+    k<<<balanced_grid_of<k>(t64, 0, n, 0, kMassWaves), t64, 0, s>>>(a, b, ms, gm, ga, gb, n);
   } else {
     constexpr auto k = mass_bwd_kernel<T, LA, LB, LGA, LGB>;
     k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, ms, gm, ga, gb, n);

@@ -347,9 +347,10 @@ template <class F>
 struct LcLeg {
   F P, E, Y, D;
 };
-// With sh given, also *sh = sinh(x) (same reduction and table entry).
+// With sh (chp) given, also *sh = sinh(x) (*chp = cosh(x)), from the same reduction and entry.
 template <class F>
-GVX_HD LcLeg<F> lc_leg(const F &pt, const F &mm, const F &x, const gvx_f4 *hyp, F *sh = nullptr) {
+GVX_HD LcLeg<F> lc_leg(const F &pt, const F &mm, const F &x, const gvx_f4 *hyp, F *sh = nullptr,
+                       F *chp = nullptr) {
   using V = lane_t<F>;
   uint32_t n[2];
   const F r = lc_reduce(x, n);
@@ -358,6 +359,7 @@ GVX_HD LcLeg<F> lc_leg(const F &pt, const F &mm, const F &x, const gvx_f4 *hyp, 
   const TabPoly<V> tp = tab_poly(r, vbc(0.5f, V{}));
   const F ch = tab_comb(C, Sh, r, tp);
   if (sh) *sh = tab_comb(Sh, C, r, tp);
+  if (chp) *chp = ch;
   const F q = lc_sqr(mm);
   LcLeg<F> l;
   l.P = lc_mul(pt, ch);
@@ -450,6 +452,18 @@ GVX_HD bool pair_m2_lc(double pt1, double eta1, double phi1, double m1, double p
 // m = sqrt(m2s) * 2^(e - 1023), e the scale's exponent (field ew = e << 20), as a double: the
 // leading float placed by bits, the trailing one likewise (or 0 when it is zero, denormal or
 // below 2^-60 of the leading one), one FP64 add.  The domain keeps the exponents in range.
+// ff times 2^shift -> double: hi and lo each moved exactly to double by their bits (integer
+// operations), then one FP64 addition (one rounding of the exact sum).  eoff = (896 + shift) << 20
+// moves the float exponent field to the double one.  hi normal or 0; a denormal lo counts as 0;
+// the result must lie in the normal range of double.
+GVX_HD double lc_to_double(const ff &x, uint32_t eoff) {
+  const uint32_t hb = f2u(x.hi), lb = f2u(x.lo);
+  const uint32_t ah = hb & 0x7fffffffu, al = lb & 0x7fffffffu;
+  const double dh = hilo2d(ah >= 0x800000u ? ((ah >> 3) + eoff) | (hb & 0x80000000u) : 0u, hb << 29);
+  const double dl = hilo2d(al >= 0x800000u ? ((al >> 3) + eoff) | (lb & 0x80000000u) : 0u, lb << 29);
+  return dh + dl;
+}
+
 GVX_HD double lc_mass_out(ff m2s, uint32_t ew) {
   if (m2s.hi == 0.0f) return 0.0;
   const ff m = lc_sqrt_refined(m2s);

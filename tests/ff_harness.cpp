@@ -14,6 +14,7 @@
 #include "../paper_2312_02756_gb300/csrc/mass_ff2.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_grad_ff2.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_lc.cuh"
+#include "../paper_2312_02756_gb300/csrc/mass_lc_grad.cuh"
 
 using namespace gvx::ffm;
 
@@ -98,6 +99,32 @@ int64_t ffh_mass_grad(const double *a, const double *b, const double *gm, int64_
     c += f;
   }
   return c;
+}
+
+// The light-cone adjoint of the FP64 mass kernel (mass_lc_grad.cuh); ms = nullptr: no saved
+// masses (the forward's m is recomputed).
+int64_t ffh_mass_grad_lc(const double *a, const double *b, const double *gm, const double *ms,
+                         int64_t n, double *ga, double *gb, uint8_t *ok) {
+  int64_t c = 0;
+  const LcTab T{kHypTab, kSinTab};
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = a + 4 * i, *y = b + 4 * i;
+    double out[8];
+    bool f = pair_mass_grad_lc(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], gm[i],
+                               ms != nullptr, ms ? ms[i] : 0.0, T, out);
+    ok[i] = f;
+    for (int k = 0; k < 4; k++) {
+      ga[4 * i + k] = f ? out[k] : NAN;
+      gb[4 * i + k] = f ? out[4 + k] : NAN;
+    }
+    c += f;
+  }
+  return c;
+}
+
+// lc_to_double of the ff (hi[i], lo[i]) times 2^shift (mass_lc.cuh)
+void ffh_lc_to_double(const float *hi, const float *lo, int64_t n, int shift, double *out) {
+  for (int64_t i = 0; i < n; i++) out[i] = lc_to_double(ff{hi[i], lo[i]}, (uint32_t)(896 + shift) << 20);
 }
 
 // op: 0 cosh, 1 sinh, 2 sin_q1, 3 round trip double -> ff -> double, 4 sqrt, 5 sqr

@@ -138,6 +138,84 @@ def test_lc_pair_mass_against_oracle(ffh, orc):
             assert ok.mean() > 0.9999, k
 
 
+def test_lc_to_double_conversion(ffh):
+    """The adjoint's ff -> double conversion (mass_lc.cuh lc_to_double) against the exact sum
+    hi + lo (fractions): the correctly rounded double of hi + lo, times 2^shift, for lo of every
+    relative size and sign, power-of-two hi included; exactly hi where lo is 0 or denormal (a
+    denormal lo counts as 0); 0 for a zero hi."""
+    from fractions import Fraction
+    g = syn.rng(80)
+    n = 20000
+    e = g.integers(-100, 100, n)
+    hi = np.ldexp(g.uniform(1, 2, n), e).astype(np.float32)
+    hi[: n // 4] = np.ldexp(1.0, e[: n // 4]).astype(np.float32)       # powers of two
+    hi *= np.where(g.random(n) < 0.5, -1, 1).astype(np.float32)
+    ulp = np.spacing(np.abs(hi)).astype(np.float64)
+    lo = (g.uniform(-2, 2, n) * ulp * np.ldexp(1.0, -g.integers(0, 40, n))).astype(np.float32)
+    lo[::11] = 0.0
+    hi, lo = np.ascontiguousarray(hi), np.ascontiguousarray(lo)
+    for shift in (0, -300, 500):
+        out = np.empty(n)
+        ffh.ffh_lc_to_double(hi.ctypes.data_as(ctypes.c_void_p), lo.ctypes.data_as(ctypes.c_void_p),
+                             ctypes.c_int64(n), ctypes.c_int(shift), _p(out))
+        for h, l, o in zip(hi, lo, out):
+            lo_eff = float(l) if abs(float(l)) >= 2.0 ** -126 else 0.0
+            exact = (Fraction(float(h)) + Fraction(lo_eff)) * Fraction(2) ** shift
+            assert o == float(exact), (h, l, o)
+    tiny = np.array([0.0, -0.0], np.float32)
+    out = np.empty(2)
+    z = np.zeros(2, np.float32)
+    ffh.ffh_lc_to_double(tiny.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                         ctypes.c_int64(2), ctypes.c_int(0), _p(out))
+    assert np.all(out == 0)
+
+
+def _mass_grad_lc(lib, a, b, gm, ms=None):
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    gm = np.ascontiguousarray(gm, dtype=np.float64)
+    ga, gb, ok = np.empty_like(a), np.empty_like(b), np.empty(len(a), np.uint8)
+    msp = None if ms is None else _p(np.ascontiguousarray(ms, dtype=np.float64))
+    lib.ffh_mass_grad_lc(_p(a), _p(b), _p(gm), msp, ctypes.c_int64(len(a)), _p(ga), _p(gb),
+                         _p(ok))
+    return ga, gb, ok.astype(bool)
+
+
+def test_lc_pair_mass_gradient_against_oracle(ffh, orc):
+    """The light-cone adjoint of the FP64 mass kernel (mass_lc_grad.cuh), host build: both legs'
+    gradients against the binary128 chain rule, normwise (components weighted by max(|x|, 1))
+    within 1e-12 of the weighted reference wherever it runs, with the forward's masses recomputed
+    and with the oracle's masses given as the saved ones; zero where m = 0 or gm = 0."""
+    from test_oracle_pins import _adversarial_pairs
+    from helpers import scaled_grad_err
+    cases = [(syn.ptetaphim(syn.rng(60), 50000), syn.ptetaphim(syn.rng(61), 50000)),
+             (syn.ptetaphim_light_mix(syn.rng(62), 20000), syn.ptetaphim_light_mix(syn.rng(63), 20000)),
+             _adversarial_pairs(10000, 64)]
+    e = lambda x: np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
+    for k, (a, b) in enumerate(cases):
+        gm = syn.upstream(syn.rng(65 + k), len(a))
+        ra, rb = orc.mass_grad_def(a, b, gm, nthreads=8)
+        o1 = orc.mass_def(a, b, nthreads=8)
+        for ms in (None, o1):
+            ga, gb, ok = _mass_grad_lc(ffh, a, b, gm, ms)
+            assert ok.mean() > 0.999, k
+            # O1's gradient is exact only where m is resolved (the m = 0 pairs get 0 here)
+            sel = ok & (o1 >= 1e-9 * (e(a) + e(b)))
+            err = scaled_grad_err(np.hstack([ga, gb])[sel], np.hstack([ra, rb])[sel],
+                                  np.hstack([a, b])[sel])
+            assert err.max() <= 1e-12, (k, ms is None, err.max())
+    # gm = 0 and saved m = 0 give exact zeros
+    a, b = syn.ptetaphim(syn.rng(68), 1000), syn.ptetaphim(syn.rng(69), 1000)
+    gm = syn.upstream(syn.rng(70), 1000)
+    gm[::3] = 0.0
+    ms = orc.mass_def(a, b)
+    ms[1::3] = 0.0
+    ga, gb, ok = _mass_grad_lc(ffh, a, b, gm, ms)
+    zero = np.zeros(1000, bool)
+    zero[::3] = zero[1::3] = True
+    assert ok.all() and np.all(ga[zero] == 0) and np.all(gb[zero] == 0)
+    assert np.all(np.abs(ga[~zero]).max(axis=1) > 0)
+
+
 def test_lc_pair_mass_tiny_and_degenerate_legs(ffh, orc):
     """Scale ratios at and beyond the fast path's 2^-40 rule, zero and denormal components, and
     |d_phi| in and out of the band around 2 pi that the fast path leaves to FP64: whatever it
