@@ -72,6 +72,9 @@ def _load():
         "orc_lv_mass_def": ([P, I64, P], None),
         "orc_mass_fp64": ([P, P, I64, P, INT], None),
         "orc_boost_fp64": ([P, P, I64, I64, P, INT], None),
+        "orc_mass_grad_fp64": ([P, P, P, I64, P, P, INT], None),
+        "orc_event_pairs_fp64": ([P, P, I64, P, P, P, INT], INT),
+        "orc_event_pairs_grad_fp64": ([P, P, I64, P, P, INT, P, INT], INT),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -303,3 +306,62 @@ def boost_fp64(v, beta, nthreads: int = 1) -> np.ndarray:
     out = np.empty((n, 4))
     _load().orc_boost_fp64(_ptr(v), _ptr(b), stride, n, _ptr(out), nthreads)
     return out
+
+
+def mass_grad_fp64(a, b, gm, nthreads: int = 1):
+    """O2 adjoint of the pair mass: (ga, gb) = gm * dm/d(pt, eta, phi, m) of each leg, from the
+    O2 identity differentiated term by term, in double."""
+    a, b = _rows(a, 4), _rows(b, 4)
+    gm = np.ascontiguousarray(np.asarray(gm, dtype=np.float64)).reshape(-1)
+    if gm.shape[0] != a.shape[0] or b.shape[0] != a.shape[0]:
+        raise ValueError("a, b and gm must have the same length")
+    ga, gb = np.empty_like(a), np.empty_like(b)
+    _load().orc_mass_grad_fp64(_ptr(a), _ptr(b), _ptr(gm), a.shape[0], _ptr(ga), _ptr(gb),
+                               nthreads)
+    return ga, gb
+
+
+def _offsets(p, offsets):
+    p = _rows(p, 4) if len(p) else np.zeros((0, 4))
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    n_ev = off.shape[0] - 1
+    if n_ev < 0 or off[-1] != p.shape[0]:
+        raise ValueError("offsets must have n_events+1 entries ending at the particle count")
+    counts = np.diff(off)
+    if np.any(counts < 0):
+        raise ValueError("offsets must be non-decreasing")
+    return p, off, n_ev, int(np.sum(counts * (counts - 1) // 2))
+
+
+def event_pairs_fp64(p, offsets, nthreads: int = 1):
+    """O2 jagged pair masses, as event_pairs_def: (pair_offsets, pair_m, sums (n_ev, 4))."""
+    p, off, n_ev, n_pairs = _offsets(p, offsets)
+    pair_off = np.empty(n_ev + 1, dtype=np.int64)
+    pair_m = np.empty(max(n_pairs, 1))
+    sums = np.empty((max(n_ev, 1), 4))
+    rc = _load().orc_event_pairs_fp64(_ptr(p), _ptr(off), n_ev, _ptr(pair_off), _ptr(pair_m),
+                                      _ptr(sums), nthreads)
+    if rc != 0:
+        raise ValueError("malformed offsets")
+    return pair_off, pair_m[:n_pairs], sums[:n_ev]
+
+
+def event_pairs_grad_fp64(p, offsets, grad_pair_m, grad_sums=None, magnitudes=False,
+                          nthreads: int = 1) -> np.ndarray:
+    """O2 adjoint of the jagged pair masses and event sums, as event_pairs_grad_def; with
+    magnitudes, the per-particle sums of the contributions' magnitudes instead."""
+    p, off, n_ev, n_pairs = _offsets(p, offsets)
+    gpm = np.ascontiguousarray(np.asarray(grad_pair_m, dtype=np.float64)).reshape(-1)
+    if gpm.shape[0] != n_pairs:
+        raise ValueError("grad_pair_m must hold one value per pair")
+    gpm = gpm if n_pairs else np.zeros(1)
+    gs = None if grad_sums is None else _rows(grad_sums, 4)
+    if gs is not None and gs.shape[0] != n_ev:
+        raise ValueError("grad_sums must hold one row per event")
+    out = np.zeros((max(p.shape[0], 1), 4))
+    rc = _load().orc_event_pairs_grad_fp64(_ptr(p), _ptr(off), n_ev, _ptr(gpm),
+                                           None if gs is None else _ptr(gs), int(magnitudes),
+                                           _ptr(out), nthreads)
+    if rc != 0:
+        raise ValueError("malformed offsets")
+    return out[:p.shape[0]]

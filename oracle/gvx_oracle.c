@@ -671,6 +671,231 @@ void orc_mass_fp64(const double *a, const double *b, int64_t n, double *m, int n
   run_ranges(mass_fp64_range, &c, n, nthreads);
 }
 
+/* Adjoint of the O2 pair mass, from the same identity differentiated term by term.  With
+ * F = m^2 = m_1^2 + m_2^2 + 2 Q + 4 pt_1 pt_2 S,  Q = E_1 E_2 - P_1 P_2,
+ * S = sinh^2(d_eta/2) + sin^2(d_phi/2), dE_i/dP_i = P_i/E_i and dE_i/dm_i = m_i/E_i:
+ *   dF/dP_1 = 2 (E_2 P_1 - P_2 E_1)/E_1 = 2 (P_1^2 m_2^2 - P_2^2 m_1^2) / (E_1 (E_2 P_1 + P_2 E_1))
+ *     (the difference E_2 P_1 - P_2 E_1 multiplied by its conjugate), and likewise for leg 2;
+ *   dF/dm_i = 2 m_i (E_1 + E_2)/E_i;
+ *   dF/dpt_i = cosh(eta_i) dF/dP_i + 4 pt_o S;
+ *   dF/deta_i = pt_i sinh(eta_i) dF/dP_i +- 2 pt_1 pt_2 sinh(d_eta);
+ *   dF/dphi_i = +- 2 pt_1 pt_2 sin(d_phi)   (+ for leg 1, - for leg 2),
+ * and dm/dx = dF/dx / (2 m).  sin(d_phi) = 2 sin(d_phi/2) cos(d_phi/2) from the half-angle of
+ * half_dphi_sin_fp64 (for |d_phi| > pi its cosine changes sign).  Readings as O1's: where m = 0
+ * the gradient is zero; a massless leg has E_i = P_i, so dE_i/dP_i = 1 and dF/dP_i =
+ * 2 (E_o - P_o) = 2 m_o^2/(E_o + P_o), dF/dm_i = 0. */
+static void half_dphi_sincos_fp64(double phi1, double phi2, double *sn, double *cs) {
+  const double pid = 3.141592653589793116, pilo = 1.2246467991473531772e-16;
+  double d = phi1 - phi2;
+  if (fabs(d) > pid && fabs(phi1) <= pid && fabs(phi2) <= pid) {
+    double h = 0.5 * ((pid - fabs(phi1)) + (pid - fabs(phi2)) + 2.0 * pilo); /* pi - |d|/2 */
+    *sn = d > 0 ? sin(h) : -sin(h); /* sin(d/2) */
+    *cs = -cos(h);                 /* cos(d/2) */
+    return;
+  }
+  *sn = sin(0.5 * d);
+  *cs = cos(0.5 * d);
+}
+
+static void pair_mass_dm_fp64(const double *a, const double *b, double ga[4], double gb[4]) {
+  double pt[2] = {a[0], b[0]}, eta[2] = {a[1], b[1]}, mm[2] = {a[3], b[3]};
+  double P[2], E[2], msq[2];
+  for (int l = 0; l < 2; l++) {
+    P[l] = pt[l] * cosh(eta[l]);
+    msq[l] = mm[l] * mm[l];
+    E[l] = sqrt(P[l] * P[l] + msq[l]);
+  }
+  double m = pair_mass_fp64(a, b);
+  double *outs[2] = {ga, gb};
+  if (!(m > 0)) {
+    for (int l = 0; l < 2; l++)
+      for (int k = 0; k < 4; k++) outs[l][k] = 0;
+    return;
+  }
+  double de = eta[0] - eta[1];
+  double se = sinh(0.5 * de), sp, cp;
+  half_dphi_sincos_fp64(a[2], b[2], &sp, &cp);
+  double S = se * se + sp * sp;
+  double p12 = pt[0] * pt[1];
+  double sinh_de = sinh(de), sin_dp = 2.0 * sp * cp;
+  for (int l = 0; l < 2; l++) {
+    int o = 1 - l;
+    double dFdP, dFdm;
+    if (mm[l] == 0) {
+      dFdP = E[o] + P[o] > 0 ? 2.0 * msq[o] / (E[o] + P[o]) : 0.0;
+      dFdm = 0.0;
+    } else {
+      double den = E[l] * (E[o] * P[l] + P[o] * E[l]);
+      dFdP = den > 0 ? 2.0 * (P[l] * P[l] * msq[o] - P[o] * P[o] * msq[l]) / den : 0.0;
+      dFdm = 2.0 * mm[l] * (E[0] + E[1]) / E[l];
+    }
+    double sgn = l == 0 ? 1.0 : -1.0;
+    double dpt = cosh(eta[l]) * dFdP + 4.0 * pt[o] * S;
+    double deta = pt[l] * sinh(eta[l]) * dFdP + sgn * 2.0 * p12 * sinh_de;
+    double dphi = sgn * 2.0 * p12 * sin_dp;
+    outs[l][0] = dpt / (2.0 * m);
+    outs[l][1] = deta / (2.0 * m);
+    outs[l][2] = dphi / (2.0 * m);
+    outs[l][3] = dFdm / (2.0 * m);
+  }
+}
+
+typedef struct {
+  const double *a, *b, *gm;
+  double *ga, *gb;
+} mass_grad_fp64_ctx;
+
+static void mass_grad_fp64_range(void *p, int64_t lo, int64_t hi) {
+  mass_grad_fp64_ctx *c = (mass_grad_fp64_ctx *)p;
+  for (int64_t i = lo; i < hi; i++) {
+    double da[4], db[4];
+    pair_mass_dm_fp64(c->a + 4 * i, c->b + 4 * i, da, db);
+    for (int k = 0; k < 4; k++) {
+      c->ga[4 * i + k] = c->gm[i] * da[k];
+      c->gb[4 * i + k] = c->gm[i] * db[k];
+    }
+  }
+}
+
+/* O2 counterpart of orc_mass_grad_def. */
+void orc_mass_grad_fp64(const double *a, const double *b, const double *gm, int64_t n,
+                        double *ga, double *gb, int nthreads) {
+  mass_grad_fp64_ctx c = {a, b, gm, ga, gb};
+  run_ranges(mass_grad_fp64_range, &c, n, nthreads);
+}
+
+/* One leg as PxPyPzE in double: (pt cos phi, pt sin phi, pt sinh eta, sqrt((pt cosh eta)^2 + m^2)). */
+static void leg_to_cartesian_fp64(const double *leg, double v[4]) {
+  double pt = leg[0], eta = leg[1], phi = leg[2], mm = leg[3];
+  double P = pt * cosh(eta);
+  v[0] = pt * cos(phi);
+  v[1] = pt * sin(phi);
+  v[2] = pt * sinh(eta);
+  v[3] = sqrt(P * P + mm * mm);
+}
+
+/* J^T g for one leg: g . dv/d(pt, eta, phi, m), v = leg_to_cartesian_fp64(leg); with
+ * |J|^T |g| instead when magnitudes is set.  The derivatives of E are written with
+ * E = sqrt(P^2 + m^2): dE/dpt = P cosh(eta)/E, dE/deta = P pt sinh(eta)/E, dE/dm = m/E, and for a
+ * massless leg (E = P) cosh(eta) and pt sinh(eta), as in O1's reading. */
+static void leg_jacobian_t_fp64(const double *leg, const double g[4], int magnitudes, double out[4]) {
+  double pt = leg[0], eta = leg[1], phi = leg[2], mm = leg[3];
+  double c = cos(phi), s = sin(phi), sh = sinh(eta), ch = cosh(eta);
+  double P = pt * ch, E = sqrt(P * P + mm * mm);
+  double J[4][4] = {{c, 0, -pt * s, 0}, {s, 0, pt * c, 0}, {sh, pt * ch, 0, 0}, {0, 0, 0, 0}};
+  if (mm == 0) {
+    J[3][0] = ch;
+    J[3][1] = pt * sh;
+  } else {
+    J[3][0] = P * ch / E;
+    J[3][1] = P * pt * sh / E;
+    J[3][3] = mm / E;
+  }
+  for (int k = 0; k < 4; k++) {
+    double acc = 0;
+    for (int r = 0; r < 4; r++) acc += magnitudes ? fabs(g[r] * J[r][k]) : g[r] * J[r][k];
+    out[k] = acc;
+  }
+}
+
+typedef struct {
+  const double *p;
+  const int64_t *off, *pair_off;
+  double *pair_m, *sums;
+  const double *gpm, *gsum;
+  double *grad_p;
+  int magnitudes;
+} event_fp64_ctx;
+
+static void event_pairs_fp64_range(void *q, int64_t lo, int64_t hi) {
+  event_fp64_ctx *c = (event_fp64_ctx *)q;
+  for (int64_t e = lo; e < hi; e++) {
+    int64_t base = c->off[e], n = c->off[e + 1] - c->off[e], k = c->pair_off[e];
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t j = i + 1; j < n; j++)
+        c->pair_m[k++] = pair_mass_fp64(c->p + 4 * (base + i), c->p + 4 * (base + j));
+    double s[4] = {0, 0, 0, 0};
+    for (int64_t i = 0; i < n; i++) {
+      double v[4];
+      leg_to_cartesian_fp64(c->p + 4 * (base + i), v);
+      for (int r = 0; r < 4; r++) s[r] += v[r];
+    }
+    for (int r = 0; r < 4; r++) c->sums[4 * e + r] = s[r];
+  }
+}
+
+static int check_offsets(const int64_t *off, int64_t n_events) {
+  if (n_events < 0 || off[0] != 0) return -1;
+  for (int64_t e = 0; e < n_events; e++)
+    if (off[e + 1] < off[e]) return -1;
+  return 0;
+}
+
+/* O2 counterpart of orc_event_pairs_def (same packing and outputs): pair masses by the O2
+ * identity, event sums accumulated in double; events split over nthreads threads. */
+int orc_event_pairs_fp64(const double *p, const int64_t *off, int64_t n_events, int64_t *pair_off,
+                         double *pair_m, double *sums, int nthreads) {
+  if (check_offsets(off, n_events)) return -1;
+  pair_off[0] = 0;
+  for (int64_t e = 0; e < n_events; e++) {
+    int64_t n = off[e + 1] - off[e];
+    pair_off[e + 1] = pair_off[e] + n * (n - 1) / 2;
+  }
+  event_fp64_ctx c = {p, off, pair_off, pair_m, sums, NULL, NULL, NULL, 0};
+  run_ranges(event_pairs_fp64_range, &c, n_events, nthreads);
+  return 0;
+}
+
+static void event_pairs_grad_fp64_range(void *q, int64_t lo, int64_t hi) {
+  event_fp64_ctx *c = (event_fp64_ctx *)q;
+  for (int64_t e = lo; e < hi; e++) {
+    int64_t base = c->off[e], n = c->off[e + 1] - c->off[e], pbase = c->pair_off[e];
+    for (int64_t i = 0; i < n; i++) {
+      const double *pi = c->p + 4 * (base + i);
+      double acc[4] = {0, 0, 0, 0};
+      for (int64_t j = 0; j < n; j++) {
+        if (j == i) continue;
+        int64_t a = i < j ? i : j, b = i < j ? j : i;
+        int64_t k = a * n - a * (a + 1) / 2 + (b - a - 1);
+        double d[4], other[4];
+        if (i < j)
+          pair_mass_dm_fp64(pi, c->p + 4 * (base + j), d, other);
+        else
+          pair_mass_dm_fp64(c->p + 4 * (base + j), pi, other, d);
+        for (int r = 0; r < 4; r++)
+          acc[r] += c->magnitudes ? fabs(c->gpm[pbase + k] * d[r]) : c->gpm[pbase + k] * d[r];
+      }
+      if (c->gsum) {
+        double t[4];
+        leg_jacobian_t_fp64(pi, c->gsum + 4 * e, c->magnitudes, t);
+        for (int r = 0; r < 4; r++) acc[r] += t[r];
+      }
+      for (int r = 0; r < 4; r++) c->grad_p[4 * (base + i) + r] = acc[r];
+    }
+  }
+}
+
+/* O2 counterpart of orc_event_pairs_grad_def (same inputs and packing; gsum may be NULL), in
+ * double; with magnitudes set, the per-particle sums of the contributions' magnitudes instead
+ * (|gpm| |dm/dp| over the particle's pairs plus |J|^T |gsum|): the scale that a correct
+ * summation in any order reaches, used to bound an adjoint's error. */
+int orc_event_pairs_grad_fp64(const double *p, const int64_t *off, int64_t n_events,
+                              const double *gpm, const double *gsum, int magnitudes,
+                              double *grad_p, int nthreads) {
+  if (check_offsets(off, n_events)) return -1;
+  int64_t *pair_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_events + 1));
+  if (!pair_off) return -2;
+  pair_off[0] = 0;
+  for (int64_t e = 0; e < n_events; e++) {
+    int64_t n = off[e + 1] - off[e];
+    pair_off[e + 1] = pair_off[e] + n * (n - 1) / 2;
+  }
+  event_fp64_ctx c = {p, off, pair_off, NULL, NULL, gpm, gsum, grad_p, magnitudes};
+  run_ranges(event_pairs_grad_fp64_range, &c, n_events, nthreads);
+  free(pair_off);
+  return 0;
+}
+
 /* Boost in vector form:
  *   E' = gamma (E + beta.p),  p' = p + (k (beta.p) + gamma E) beta,  k = gamma^2 / (1 + gamma),
  * using (gamma - 1)/b2 = gamma^2/(1 + gamma), which has no 0/0 at beta = 0. */

@@ -741,3 +741,122 @@ def test_ptetaphie_mass_closed_forms(orc):
     assert np.all(np.abs(orc.mass_cart_def(ar, br, "ptetaphie") - m) <= 1e-12 * m)
     mm = orc.mass_def(p[:200], p[200:])
     assert np.all(np.abs(m - mm) <= 1e-12 * mm)
+
+
+# ----------------------------------------------------------------- O2 adjoint and jagged forms
+
+def _grad_err(g, r, x):
+    """Normwise: components weighted by max(|x_k|, 1), relative to the weighted 1-norm of r."""
+    s = np.maximum(np.abs(x), 1.0)
+    den = np.sum(np.abs(r) * s, axis=1)
+    return np.max(np.abs(g - r) * s, axis=1) / np.where(den > 0, den, 1.0)
+
+
+def test_mass_grad_fp64_vs_definition(orc):
+    """O2's adjoint (the O2 identity differentiated term by term, in double) against O1's (the
+    chain rule through the binary128 definition): within 1e-14 normwise on the workload, on light
+    and heavy mixes, on near-collinear light legs (where m is resolved by O1), with azimuths
+    across +-pi, and with massless and zero-pt legs; zero where the mass is zero."""
+    e = lambda x: np.sqrt((x[:, 0] * np.cosh(x[:, 1])) ** 2 + x[:, 3] ** 2)
+    g = syn.rng(120)
+    n = 20000
+    wrap_a, wrap_b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    gap = 10 ** g.uniform(-6, -1, n)
+    wrap_a[:, 2] = np.pi - gap * g.random(n)
+    wrap_b[:, 2] = -np.pi + gap * g.random(n)
+    deg_a, deg_b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    deg_a[::3, 3] = 0.0          # massless legs
+    deg_b[1::5, 3] = 0.0
+    deg_a[2::7, 0] = 0.0         # pt = 0 legs (with mass)
+    cases = [(syn.ptetaphim(g, n), syn.ptetaphim(g, n)),
+             (syn.ptetaphim_light_mix(g, n), syn.ptetaphim_light_mix(g, n)),
+             _adversarial_pairs(n, 121), (wrap_a, wrap_b), (deg_a, deg_b)]
+    for k, (a, b) in enumerate(cases):
+        gm = syn.upstream(g, n)
+        ra, rb = orc.mass_grad_def(a, b, gm, nthreads=4)
+        oa, ob = orc.mass_grad_fp64(a, b, gm, nthreads=4)
+        m1 = orc.mass_def(a, b, nthreads=4)
+        sel = m1 >= 1e-9 * (e(a) + e(b))
+        assert sel.mean() > 0.9, k
+        err = _grad_err(np.hstack([oa, ob])[sel], np.hstack([ra, rb])[sel], np.hstack([a, b])[sel])
+        assert err.max() <= 1e-14, (k, err.max())
+    a = np.array([[10.0, 0.3, 0.1, 0.0], [0.0, 0.0, 0.0, 0.0]])
+    oa, ob = orc.mass_grad_fp64(a, a, np.ones(2))  # identical massless legs, zero vectors: m = 0
+    assert np.all(oa == 0) and np.all(ob == 0)
+    # a planted sign error in the azimuthal term fails the comparison (the pin is sensitive)
+    a, b = cases[0]
+    gm = syn.upstream(syn.rng(122), n)
+    ra, _ = orc.mass_grad_def(a, b, gm)
+    oa, _ = orc.mass_grad_fp64(a, b, gm)
+    bad = oa.copy()
+    bad[:, 2] = -bad[:, 2]
+    assert _grad_err(bad, ra, a).max() > 1e-3
+
+
+def test_mass_grad_fp64_threads_agree(orc):
+    g = syn.rng(123)
+    a, b, gm = syn.ptetaphim(g, 5000), syn.ptetaphim(g, 5000), syn.upstream(g, 5000)
+    r1, r3 = orc.mass_grad_fp64(a, b, gm, 1), orc.mass_grad_fp64(a, b, gm, 3)
+    assert np.array_equal(r1[0], r3[0]) and np.array_equal(r1[1], r3[1])
+
+
+def test_event_pairs_fp64_vs_definition(orc):
+    """O2 jagged forms against O1 on 3000 Poisson(8) events plus empty, single-particle and
+    65-particle events: offsets equal, pair masses within 1e-14 relative, event sums within
+    1e-14 of the summed component magnitudes, the adjoint within 1e-14 of the summed
+    contribution magnitudes (which the magnitudes mode returns, checked against an explicit
+    sum over the pairs); thread counts do not change the bits."""
+    g = syn.rng(124)
+    counts = np.concatenate([np.diff(syn.jagged_offsets(g, 3000)), [0, 1, 2, 65]])
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    p = syn.ptetaphim(g, int(off[-1]))
+    p[7::31, 3] = 0.0
+    po1, pm1, s1 = orc.event_pairs_def(p, off)
+    po2, pm2, s2 = orc.event_pairs_fp64(p, off, nthreads=4)
+    assert np.array_equal(po1, po2)
+    assert np.all(np.abs(pm2 - pm1) <= 1e-14 * pm1)
+    cart = np.abs(orc.to_cartesian_def(p))
+    ev = np.repeat(np.arange(len(counts)), counts)
+    mag = np.zeros((len(counts), 4))
+    np.add.at(mag, ev, cart)
+    assert np.all(np.abs(s2 - s1) <= 1e-14 * mag)
+    _, pm3, s3 = orc.event_pairs_fp64(p, off, nthreads=1)
+    assert np.array_equal(pm2, pm3) and np.array_equal(s2, s3)
+    gpm = syn.upstream(g, len(pm1))
+    gsum = syn.upstream(g, (len(counts), 4))
+    r1 = orc.event_pairs_grad_def(p, off, gpm, gsum)
+    r2 = orc.event_pairs_grad_fp64(p, off, gpm, gsum, nthreads=4)
+    mg = orc.event_pairs_grad_fp64(p, off, gpm, gsum, magnitudes=True, nthreads=4)
+    s = np.maximum(np.abs(p), 1.0)
+    den = np.sum(mg * s, axis=1)
+    err = np.max(np.abs(r2 - r1) * s, axis=1) / np.where(den > 0, den, 1.0)
+    assert err.max() <= 1e-14
+    assert np.array_equal(r2, orc.event_pairs_grad_fp64(p, off, gpm, gsum, nthreads=1))
+    # the magnitudes: for a sample of events, the sum over the event's pairs of |gpm| |dm/dp|
+    # (the elementwise O2 adjoint) plus |J|^T |gsum| (O1's sum part, unit by unit)
+    po = po1
+    for e in (0, 5, 17, len(counts) - 1):
+        lo, hi = off[e], off[e + 1]
+        n = hi - lo
+        want = np.zeros((n, 4))
+        if n >= 2:
+            ii, jj = np.triu_indices(n, 1)
+            ga, gb = orc.mass_grad_fp64(p[lo + ii], p[lo + jj], np.abs(gpm[po[e]:po[e + 1]]))
+            np.add.at(want, ii, np.abs(ga))
+            np.add.at(want, jj, np.abs(gb))
+        for r in range(4):
+            unit = np.zeros((1, 4))
+            unit[0, r] = 1.0
+            J_r = orc.event_pairs_grad_def(p[lo:hi], [0, n], np.zeros(n * (n - 1) // 2), unit)
+            want += np.abs(J_r) * abs(gsum[e, r])
+        assert np.allclose(mg[lo:hi], want, rtol=1e-12, atol=0), e
+    # without sums: the pair part alone
+    r1 = orc.event_pairs_grad_def(p, off, gpm)
+    r2 = orc.event_pairs_grad_fp64(p, off, gpm)
+    mg = orc.event_pairs_grad_fp64(p, off, gpm, magnitudes=True)
+    den = np.sum(mg * s, axis=1)
+    assert (np.max(np.abs(r2 - r1) * s, axis=1) / np.where(den > 0, den, 1.0)).max() <= 1e-14
+    with pytest.raises(ValueError):
+        orc.event_pairs_fp64(p, off[::-1])
+    with pytest.raises(ValueError):
+        orc.event_pairs_grad_fp64(p, off, gpm[:-1])
