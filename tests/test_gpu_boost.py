@@ -4,6 +4,8 @@ and applied in binary128).
 Error measure (per vector, normwise): max_k |x'_k - ref_k| / E'_ref -- a component can vanish,
 the energy cannot (E' >= |p'|).  FP64 gate 1e-12; FP32 error measured and bounded.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -82,11 +84,28 @@ def test_boost_f64_ragged(orc, n):
         assert normwise(_run(v, beta, lv, lv), ref, ref[:, 3]).max() <= TOL_F64
 
 
-def test_boost_f64_full_size_sampled(orc):
+@pytest.mark.parametrize("layout", ["soa", "aos"])
+def test_boost_f64_full_size(orc, layout):
+    """All 2^26 boosts by per-vector beta (|beta| <= 0.99) against O2 (the FP64 vector form,
+    pinned to O1 at 1e-14), normwise relative to E'; plus a uniform sample and the 4096
+    worst-conditioned vectors against O1."""
     torch = torch_cuda()
     import paper_2312_02756_gb300 as gvx
     g = syn.rng(1)
     v, beta = syn.pxpypze(g, N_FULL), syn.velocities(g, N_FULL, 0.99)
+    dv, db = dev(v, layout), dev(beta, layout)
+    out = gvx.boost(dv, db, layout=layout, beta_layout=layout)
+    torch.cuda.synchronize()
+    del dv, db
+    oh = host(out, layout)
+    del out
+    torch.cuda.empty_cache()
+    assert np.all(np.isfinite(oh))
+    ref2 = orc.boost_fp64(v, beta, nthreads=os.cpu_count() or 8)
+    err2 = normwise(oh, ref2, ref2[:, 3])
+    print("FP64 boost 2^26 (%s) vs O2, every element: %s" % (layout, summary(err2)))
+    assert err2.max() <= TOL_F64
+    del ref2, err2
     # a uniform sample plus the 4096 worst-conditioned vectors: there p' nearly cancels (the
     # boost lands close to the vector's rest frame) and (E + |beta| |p|) / (E + beta.p) is largest
     cond = (v[:, 3] + np.linalg.norm(beta, axis=1) * np.linalg.norm(v[:, :3], axis=1)) / (
@@ -95,15 +114,9 @@ def test_boost_f64_full_size_sampled(orc):
     del cond
     idx = np.union1d(syn.rng(102).choice(N_FULL, 1 << 16, replace=False), worst)
     ref = orc.boost_def(v[idx], beta[idx], nthreads=8)
-    dv, db = dev(v, "soa"), dev(beta, "soa")
-    out = gvx.boost(dv, db)
-    torch.cuda.synchronize()
-    del dv, db
-    oh = host(out, "soa")
-    del out
-    torch.cuda.empty_cache()
-    assert np.all(np.isfinite(oh))
-    assert normwise(oh[idx], ref, ref[:, 3]).max() <= TOL_F64
+    err1 = normwise(oh[idx], ref, ref[:, 3])
+    print("FP64 boost 2^26 (%s) vs O1, sample + worst-conditioned: %s" % (layout, summary(err1)))
+    assert err1.max() <= TOL_F64
 
 
 def test_boost_f32_error_per_output(orc):

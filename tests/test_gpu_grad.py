@@ -6,6 +6,8 @@ Mass gradient error measure: per pair, components weighted by max(|x_k|, 1) (so 
 unit of m), normwise relative to the weighted 1-norm of the reference (helpers.scaled_grad_err).
 FP64 gate 1e-12.  Boost: normwise relative to the largest reference component, FP64 gate 1e-12.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -36,6 +38,20 @@ def test_mass_grad_f64_vs_oracle(orc, layout):
     ra, rb = orc.mass_grad_def(a, b, gm, nthreads=8)
     err = scaled_grad_err(np.hstack([ga, gb]), np.hstack([ra, rb]), np.hstack([a, b]))
     print("FP64 mass grad vs O1 (%s): %s" % (layout, summary(err)))
+    assert err.max() <= TOL_F64
+
+
+def test_mass_grad_f64_full_size(orc):
+    """2^24 pairs (SoA, the saved masses passed to the adjoint as autograd does): every gradient
+    against O2's adjoint (pinned to O1 at 1e-14), normwise as above."""
+    g = syn.rng(39)
+    n = 1 << 24
+    a, b = syn.ptetaphim(g, n), syn.ptetaphim(g, n)
+    gm = syn.upstream(g, n)
+    ga, gb, _ = _mass_grads(a, b, gm, "soa")
+    ra, rb = orc.mass_grad_fp64(a, b, gm, nthreads=os.cpu_count() or 8)
+    err = scaled_grad_err(np.hstack([ga, gb]), np.hstack([ra, rb]), np.hstack([a, b]))
+    print("FP64 mass grad 2^24 vs O2, every element: %s" % summary(err))
     assert err.max() <= TOL_F64
 
 

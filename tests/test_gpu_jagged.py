@@ -5,12 +5,13 @@ elementwise FP64 mass).  Event sums: normwise, |sum - ref| <= 1e-12 * sum_i |E_i
 order is correct).
 """
 import ctypes
+import os
 
 import numpy as np
 import pytest
 
 import gvx_synth as syn
-from helpers import TOL_F64, dev, host, torch_cuda
+from helpers import TOL_F64, dev, host, summary, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -103,13 +104,28 @@ def test_event_pairs_edge_events(orc):
     assert np.array_equal(po, [0])
 
 
-def test_event_pairs_full_size_sampled(orc):
-    """2^20 events, Poisson(8) multiplicities: offsets exact everywhere, 400 events against O1."""
+def test_event_pairs_full_size(orc):
+    """2^20 events, Poisson(8) multiplicities: offsets exact everywhere; every pair mass and
+    every event sum against O2 (pinned to O1 at 1e-14); 400 events against O1."""
     g = syn.rng(3)
     off = syn.jagged_offsets(g, 1 << 20)
     p = syn.ptetaphim(g, int(off[-1]))
     po, pm, sums = _run(p, off)
     assert np.all(np.isfinite(pm)) and np.all(pm >= 0)
+    r_off, r_m, r_s = orc.event_pairs_fp64(p, off, nthreads=os.cpu_count() or 8)
+    assert np.array_equal(po, r_off)
+    pos = r_m > 0
+    rel = np.abs(pm[pos] - r_m[pos]) / r_m[pos]
+    print("jagged pair masses (%d) vs O2, every element: %s" % (len(pm), summary(rel)))
+    assert rel.max() <= TOL_F64 and np.all(pm[~pos] == 0)
+    cart = np.abs(orc.to_cartesian_def(p))
+    ev = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    mag = np.zeros((len(off) - 1, 4))
+    np.add.at(mag, ev, cart)
+    mag = mag.sum(axis=1)
+    es = np.max(np.abs(sums - r_s), axis=1) / np.where(mag > 0, mag, 1.0)
+    print("jagged event sums (%d) vs O2, relative to sum |components|: %s" % (len(sums), summary(es)))
+    assert es.max() <= TOL_F64
     events = np.sort(syn.rng(33).choice(1 << 20, 400, replace=False))
     _check(orc, p, off, po, pm, sums, events)
 

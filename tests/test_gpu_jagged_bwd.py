@@ -6,11 +6,13 @@ the same weighting of the summed magnitudes of the contributions (|upstream| * |
 particle's pairs, plus |J|^T |grad_event_sum|) -- the scale a correct summation in any order
 reaches.  Gate 1e-12 (as the elementwise FP64 adjoint).
 """
+import os
+
 import numpy as np
 import pytest
 
 import gvx_synth as syn
-from helpers import TOL_F64, dev, host, torch_cuda
+from helpers import TOL_F64, dev, host, summary, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -119,9 +121,10 @@ def test_event_pairs_bwd_through_autograd(orc):
     assert _err(direct, ref, _magnitudes(orc, p, off, gpm, gsum), p).max() <= TOL_F64
 
 
-def test_event_pairs_bwd_full_size_sampled(orc):
-    """2^20 events, Poisson(8) multiplicities clamped to [0, 64]: every gradient finite, and 300
-    sampled events against the oracle."""
+def test_event_pairs_bwd_full_size(orc):
+    """2^20 events, Poisson(8) multiplicities clamped to [0, 64]: every gradient against O2
+    (pinned to O1 at 1e-14), each particle's error relative to its summed contribution
+    magnitudes (O2's magnitudes mode); 300 sampled events against O1."""
     import paper_2312_02756_gb300 as gvx
     torch = torch_cuda()
     g = syn.rng(43)
@@ -131,6 +134,13 @@ def test_event_pairs_bwd_full_size_sampled(orc):
     gsum = syn.upstream(g, (1 << 20, 4))
     got = _gpu_bwd(p, off, gpm, gsum)
     assert np.all(np.isfinite(got))
+    nt = os.cpu_count() or 8
+    ref2 = orc.event_pairs_grad_fp64(p, off, gpm, gsum, nthreads=nt)
+    mag2 = orc.event_pairs_grad_fp64(p, off, gpm, gsum, magnitudes=True, nthreads=nt)
+    err2 = _err(got, ref2, mag2, p)
+    print("jagged adjoint (%d particles) vs O2, every element: %s" % (len(p), summary(err2)))
+    assert err2.max() <= TOL_F64
+    del ref2, mag2, err2
     po = _pair_offsets(off)
     for e in np.sort(syn.rng(143).choice(1 << 20, 300, replace=False)):
         lo, hi = off[e], off[e + 1]
