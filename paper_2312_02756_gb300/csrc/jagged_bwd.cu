@@ -7,36 +7,55 @@
 //   grad_i = sum over j != i of gm[pair(i, j)] dm(p_i, p_j)/dp_i  +  J_i^T gs[e],
 // J_i = d(px, py, pz, E)/d(pt, eta, phi, m) of the particle.
 //
-// One thread per particle accumulates its own gradient over its partners in a fixed order, so the
-// result does not depend on scheduling and no atomics are needed; each pair is therefore
-// evaluated from both sides, but each side computes only its own leg's gradient.  CTAs take tiles
-// of kTE consecutive events (grid-stride over tiles) and stage them in sub-batches of whole
-// events of at most kNT particles: per particle once, its raw values, the event's scale and the
-// float-float leg terms (mass_ff.cuh, leg_grad_prep) go to shared memory, and its event-sum part
-// (the Jacobian rows from the float-float tables) starts a float-float accumulator.  After one
-// barrier every particle walks its partners with the float-float pair gradient
-// (pair_grad_terms, leg_grad_terms), adding to that accumulator at the event's scale, and
-// converts it to double once at the end; pairs outside the float-float domain use the FP64
-// formulas and a separate FP64 accumulator.  (The FP64 pipe is the scarce one: per directed pair
-// this leaves the FP64 differences of the angles only.)
-// An event with more than kNT particles is handled alone, straight from global memory.  The
-// pair offsets are those the forward call wrote; each tile checks them (and the offsets) against
-// the event sizes and the pair count before it reads any pair gradient, and records
-// GVX_ERR_OFFSETS for a tile that does not match (its particles' gradients are then not written).
+// Pair part in light-cone form (mass_lc_grad.cuh): with Y = E + P, D = E - P = m^2/Y,
+// F = m^2 = (D_i + D_j)(Y_i + Y_j) + 4 pt_i pt_j S and c_ij = gm_ij / (2 m_ij),
+//   dm/dpt_i  = (cosh eta_i / E_i) (Y_i A1 - D_i A2) + 4 A5,
+//   dm/deta_i = (pt_i sinh eta_i / E_i) (Y_i A1 - D_i A2) + pt_i A6,
+//   dm/dphi_i = pt_i A7,
+//   dm/dm_i   = (2 m_i / E_i) (E_i A3 + A4),
+// summed over the partners j through seven accumulators (float-float sums whose absolute error
+// stays within ~2^-47 of the summed magnitudes)
+//   A1 = sum c D_j,  A2 = sum c Y_j,  A3 = sum c,  A4 = sum c E_j,  A5 = sum c pt_j S_ij,
+//   A6 = sum c pt_j 2 sinh(eta_i - eta_j),  A7 = sum c pt_j 2 sin(phi_i - phi_j),
+// so that a partner costs its angular terms, its pair mass and seven float-float
+// multiply-accumulates (paired FP32 lanes where two share a factor).
+//
+// One thread per particle walks its partners in a fixed order, so the result does not depend on
+// scheduling and no atomics are needed.  CTAs take tiles of kTE consecutive events (grid-stride
+// over tiles) and stage them in sub-batches of whole events of at most kNT particles: (a) the
+// raw particles, and the order of the sub-batch's events by decreasing size (so that the lanes
+// of a warp walk partner loops of similar length); (b) per particle, by the thread that will
+// take it in (c), its event's scale and light-cone terms (at the event's scale, as the forward
+// kernel stages them) and its event-sum part J^T gs (float-float, in double in the thread's own
+// shared-memory slot); (c) the partner loop, the pair part from the accumulators and the
+// conversion to double.  Pairs outside the float-float domain (either
+// particle outside the forward's domain at the event scale, |d_phi|/2 within 2^-7 of pi, a scaled
+// m^2 below 2^-80, |gm| outside [2^-60, 2^20]) take the FP64 formulas, summed in FP64 in the
+// thread's own shared-memory slot.  An event with more than kNT particles is handled alone,
+// straight from global memory, with the elementwise kernels' pair adjoint.  The pair offsets are
+// those the forward call wrote; each tile checks them (and the offsets) against the event sizes
+// and the pair count before it reads any pair gradient, and records GVX_ERR_OFFSETS for a tile
+// that does not match (its particles' gradients are then not written).
 #include <cuda_runtime.h>
 
+#include <limits.h>
+
 #include "common.cuh"
-#include "mass_ff.cuh"
+#include "mass_lc_grad.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
 namespace {
 
-constexpr int kTE = 28;    // events per tile (about 224 particles at the benchmark multiplicity)
-constexpr int kNT = 256;   // threads per CTA, and particles staged per sub-batch
-constexpr int kNoFast = -100000;  // scale marker of a particle outside the float-float domain
-// per staged particle: pt, eta, phi, m (doubles), the ff leg terms, leg exponent and scale (ints)
-constexpr size_t kDynSmem = (size_t)kNT * (4 * sizeof(double) + sizeof(ffm::LegGradFF) + 2 * sizeof(int));
+constexpr int kTE = 28;   // events per tile (about 224 particles at the benchmark multiplicity)
+constexpr int kNT = 256;  // threads per CTA, and particles staged per sub-batch
+constexpr int kNoFast = INT_MIN;  // scale marker of a particle outside the float-float domain
+// per staged particle: pt, eta, phi, m and the FP64 accumulator (doubles); (pt, Y), (D, E),
+// (cosh, sinh) (float4) and m (float2); the larger high word of pt and |m|, and its event's scale
+// field or kNoFast (ints)
+constexpr size_t kDynSmem =
+    (size_t)kNT * (4 * sizeof(double) + sizeof(double4) + 3 * sizeof(float4) + sizeof(float2) +
+                   2 * sizeof(int));
 
 struct BArgs {
   Lv p;
@@ -49,28 +68,15 @@ struct BArgs {
   int32_t *status;
 };
 
-// J^T gs for one particle: gs = (gx, gy, gz, gE) against the rows
+// J^T gs in FP64 for one particle: gs = (gx, gy, gz, gE) against the rows
 //   px: (cos phi, 0, -pt sin phi, 0)       py: (sin phi, 0, pt cos phi, 0)
-//   pz: (sinh eta, pt cosh eta, 0, 0)      E:  (pt cosh^2 eta, pt^2 cosh eta sinh eta, 0, m) / E,
-// and for a massless particle (E = pt cosh eta) the E row (cosh eta, pt sinh eta, 0, 0).
-__device__ __forceinline__ V4<double> sum_part(V4<double> x, V4<double> gs, const ffm::TabRef &T) {
+//   pz: (sinh eta, pt cosh eta, 0, 0)      E:  (P cosh eta, P pt sinh eta, 0, m) / E,
+// P = pt cosh eta; for a massless particle (E = P) the E row is (cosh eta, pt sinh eta, 0, 0).
+__device__ __noinline__ V4<double> sum_part(V4<double> x, V4<double> gs) {
   const double pt = x.x, eta = x.y, phi = x.z, m = x.w;
-  double c, s, sh, ch;
-  bool ok = ((ffm::dhi(eta) >> 20) & 0x7ffu) <= 1026u;  // |eta| < 16 for the tables
-  if (ok) {
-    ffm::ff sn, cs, fsh, fch;
-    ffm::sincos_t(phi, T, &sn, &cs, &ok);
-    ffm::sinhcosh_t(ffm::from_double(eta, &ok), T, &fsh, &fch);
-    c = ffm::to_double(cs);
-    s = ffm::to_double(sn);
-    sh = ffm::to_double(fsh);
-    ch = ffm::to_double(fch);
-  }
-  if (!ok) {
-    sincos(phi, &s, &c);
-    sh = sinh(eta);
-    ch = cosh(eta);
-  }
+  double s, c;
+  sincos(phi, &s, &c);
+  const double sh = sinh(eta), ch = cosh(eta);
   double eE0, eE1, eE3;  // E row: d/dpt, d/deta, d/dm
   if (m == 0.0) {
     eE0 = ch;
@@ -91,40 +97,52 @@ __device__ __forceinline__ V4<double> sum_part(V4<double> x, V4<double> gs, cons
   return g;
 }
 
-// gm-weighted gradient of particle i's leg over its partners in one event, everything read from
-// global memory (the path of events too large to stage).
-// The same J^T gs for a particle on the float-float path, from its prepared leg (scaled by 2^-sc)
-// and returned in the accumulator convention of leg_grad_terms (components 1 and 2 times 2^-sc).
-// False when an upstream component is outside the ff range (the caller then uses sum_part).
-__device__ __forceinline__ bool sum_part_ff(const ffm::LegGradFF &L, double phi, V4<double> gs,
-                                            const ffm::TabRef &T, ffm::ff *out) {
+// The same J^T gs in float-float from the particle's staged light-cone terms (scaled by 2^-s:
+// pt, P, E, m; cosh and sinh of |eta|), gs converted at its own scale 2^sg; returned in double.
+// False when gs has a nonzero component outside [2^-300, 2^300] (the caller then uses sum_part).
+__device__ __forceinline__ bool sum_part_lc(ffm::ff pt, ffm::ff E, ffm::ff mm, ffm::ff ch,
+                                            ffm::ff sh, double eta, double phi, double m,
+                                            uint32_t eoff_s, V4<double> gs, const ffm::LcTab &T,
+                                            V4<double> *out) {
   using namespace ffm;
-  bool ok = true;
-  ff sn, cs;
-  sincos_t(phi, T, &sn, &cs, &ok);
-  const ff gx = from_double(gs.x, &ok), gy = from_double(gs.y, &ok);
-  const ff gz = from_double(gs.z, &ok), gE = from_double(gs.w, &ok);
-  if (!ok) return false;
-  ff e0, e1, e3;  // E row: d/dpt, d/deta (times 2^-sc), d/dm
-  if (L.m.hi == 0.0f) {
-    e0 = L.ch;
-    e1 = mul(L.pt, L.sh);
-    e3 = make(0.0f);
-  } else {
-    const ff rE = recip(L.E);
-    e0 = mul(mul(L.P, L.ch), rE);
-    e1 = mul(mul(L.P, mul(L.pt, L.sh)), rE);
-    e3 = mul(L.m, rE);
+  const uint32_t h0 = dhi(gs.x) & 0x7fffffffu, h1 = dhi(gs.y) & 0x7fffffffu;
+  const uint32_t h2 = dhi(gs.z) & 0x7fffffffu, h3 = dhi(gs.w) & 0x7fffffffu;
+  const uint32_t hmax = umax32(umax32(h0, h1), umax32(h2, h3));
+  if (hmax == 0u && (dlo(gs.x) | dlo(gs.y) | dlo(gs.z) | dlo(gs.w)) == 0u) {
+    *out = V4<double>{0.0, 0.0, 0.0, 0.0};
+    return true;
   }
-  out[0] = add(add(mul(gx, cs), mul(gy, sn)), add(mul(gz, L.sh), mul(gE, e0)));
-  out[1] = add(mul(gz, L.P), mul(gE, e1));
-  out[2] = mul(L.pt, add(mul(gy, cs), neg(mul(gx, sn))));
-  out[3] = mul(gE, e3);
+  if (hmax - (723u << 20) >= (600u << 20)) return false;  // scale field 723..1322
+  const uint32_t ewg = hmax & 0x7ff00000u, rbg = ewg - (127u << 20);
+  const ff gx = cvt1(cvt_parts(h0, dlo(gs.x), rbg)), gy = cvt1(cvt_parts(h1, dlo(gs.y), rbg));
+  const ff gz = cvt1(cvt_parts(h2, dlo(gs.z), rbg)), gE = cvt1(cvt_parts(h3, dlo(gs.w), rbg));
+  const float sx = sign_of(gs.x), sy = sign_of(gs.y), sz = sign_of(gs.z), sE = sign_of(gs.w);
+  const float seta = sign_of(eta), sphi = sign_of(phi), sm = sign_of(m);
+  ff sn, cs;  // sin and cos of |phi|
+  sincos_lc(cvt1(cvt_parts(dhi(phi) & 0x7fffffffu, dlo(phi), kRebaseOne)), T.sin, &sn, &cs);
+  const ff P = lc_mul(pt, ch);
+  const ff rE = lc_div(ff{1.0f, 0.0f}, E);
+  const ff e0 = lc_mul(lc_mul(P, ch), rE);           // dE/dpt
+  const ff e1 = lc_mul(lc_mul(P, lc_mul(pt, sh)), rE);  // |dE/deta| (times 2^-s)
+  const ff e3 = lc_mul(mm, rE);                       // |dE/dm|
+  // signed products (the sign of a product of signed values, on the hi and lo parts)
+  const auto sp = [](const ff &a, const ff &b, float sgn) { return lc_scale(lc_mul(a, b), sgn); };
+  const ff dpt = add_same(add_same(sp(gx, cs, sx), sp(gy, sn, sy * sphi)),
+                     add_same(sp(gz, sh, sz * seta), sp(gE, e0, sE)));
+  const ff deta = add_same(sp(gz, P, sz), sp(gE, e1, sE * seta));
+  const ff dphi = lc_mul(pt, add_same(sp(gy, cs, sy), sp(gx, sn, -sx * sphi)));
+  const ff dm = sp(gE, e3, sE * sm);
+  const uint32_t eoff_g = ewg - (127u << 20);       // 2^sg
+  const uint32_t eoff_gs = eoff_g + eoff_s - (896u << 20);  // 2^(sg + s)
+  *out = V4<double>{lc_to_double(dpt, eoff_g), lc_to_double(deta, eoff_gs),
+                    lc_to_double(dphi, eoff_gs), lc_to_double(dm, eoff_g)};
   return true;
 }
 
+// gm-weighted gradient of particle i's leg over its partners in one event, everything read from
+// global memory (the path of events too large to stage).
 template <int LP>
-__device__ __forceinline__ void partners_from_global(const BArgs &A, const ffm::TabRef &T,
+__device__ __forceinline__ void partners_from_global(const BArgs &A, const ffm::LcTab &T,
                                                      int64_t i, int64_t base, int64_t n,
                                                      int64_t pair0, double *acc) {
   const V4<double> x = ld4c<LP>(A.p, i);
@@ -135,7 +153,7 @@ __device__ __forceinline__ void partners_from_global(const BArgs &A, const ffm::
     const double g = __ldg(A.gpm + pair0 + r * n - r * (r + 1) / 2 + (q - r - 1));
     const V4<double> y = ld4c<LP>(A.p, base + lj);
     double o[8];
-    if (!ffm::pair_mass_grad_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, T, o)) {
+    if (!ffm::pair_mass_grad_lc(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, g, false, 0.0, T, o)) {
       V4<double> g1, g2;
       pair_mass_grad(x, y, g, g1, g2);
       o[0] = g1.x;
@@ -147,20 +165,61 @@ __device__ __forceinline__ void partners_from_global(const BArgs &A, const ffm::
   }
 }
 
+// An event with more than kNT particles (rare): its particles in strides of the CTA, each
+// against all its partners from global memory.  Out of line, so that its registers do not count
+// against the staged path's.
+template <int LP, int LS, int LG>
+__device__ __noinline__ void big_event(const BArgs &A, const ffm::LcTab &T, int64_t e, int64_t pbeg,
+                                       int64_t n, int64_t pair0) {
+  for (int64_t t = threadIdx.x; t < n; t += kNT) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const V4<double> x = ld4c<LP>(A.p, pbeg + t);
+    if (A.has_gsum) {
+      const V4<double> sp = sum_part(x, ld4c<LS>(A.gsum, e));
+      acc[0] = sp.x;
+      acc[1] = sp.y;
+      acc[2] = sp.z;
+      acc[3] = sp.w;
+    }
+    partners_from_global<LP>(A, T, pbeg + t, pbeg, n, pair0, acc);
+    st4<double, LG>(A.grad, pbeg + t, V4<double>{acc[0], acc[1], acc[2], acc[3]});
+  }
+}
+
+// One pair outside the float-float domain: its FP64 gradient of the first leg added to *slot.
+__device__ __noinline__ void slow_pair_add(V4<double> x, V4<double> y, double g, double4 *slot) {
+  V4<double> g1, g2;
+  pair_mass_grad(x, y, g, g1, g2);
+  double4 a = *slot;
+  a.x += g1.x;
+  a.y += g1.y;
+  a.z += g1.z;
+  a.w += g1.w;
+  *slot = a;
+}
+
+__device__ __forceinline__ float4 pack4(const ffm::ff &a, const ffm::ff &b) {
+  return make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
 template <int LP, int LS, int LG>
 __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
+  using ffm::ff;
+  using ffm::ff2;
   extern __shared__ double s_dyn[];
   double *s_pt = s_dyn, *s_eta = s_pt + kNT, *s_phi = s_eta + kNT, *s_m = s_phi + kNT;
-  ffm::LegGradFF *s_leg = reinterpret_cast<ffm::LegGradFF *>(s_m + kNT);
-  int *s_ex = reinterpret_cast<int *>(s_leg + kNT), *s_fs = s_ex + kNT;
-  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
-  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
+  double4 *s_acc = reinterpret_cast<double4 *>(s_m + kNT);  // FP64 part of each gradient
+  float4 *s_pY = reinterpret_cast<float4 *>(s_acc + kNT);   // (pt, Y)
+  float4 *s_DE = s_pY + kNT;                                // (D, E)
+  float4 *s_cs = s_DE + kNT;                                // (cosh, sinh) of |eta|
+  float2 *s_mm = reinterpret_cast<float2 *>(s_cs + kNT);    // |m|
+  int *s_sc = reinterpret_cast<int *>(s_mm + kNT), *s_fs = s_sc + kNT;
   __shared__ int64_t s_off[kTE + 1], s_poff[kTE + 1];
   __shared__ int s_order[kTE], s_start[kTE];
   __shared__ int s_bad;
-  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);
+  const ffm::LcTab T{ffm::kHypTab, ffm::kSinTab};
   const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
-  const int k = threadIdx.x;  // the particle this thread stages in every sub-batch
+  const int k = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t e0 = tile * kTE;
     const int ne = (int)(A.n_events - e0 < kTE ? A.n_events - e0 : kTE);
@@ -191,60 +250,22 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
           threadIdx.x >= sb && threadIdx.x < ne && s_off[threadIdx.x + 1] - pbeg <= kNT;
       const int sbe = sb + __syncthreads_count(fits);
       if (sbe == sb) {  // one event larger than a sub-batch
-        const int64_t n = s_off[sb + 1] - pbeg;
-        for (int64_t t = threadIdx.x; t < n; t += kNT) {
-          double acc[4] = {0.0, 0.0, 0.0, 0.0};
-          const V4<double> x = ld4c<LP>(A.p, pbeg + t);
-          if (A.has_gsum) {
-            const V4<double> sp = sum_part(x, ld4c<LS>(A.gsum, e0 + sb), T);
-            acc[0] = sp.x;
-            acc[1] = sp.y;
-            acc[2] = sp.z;
-            acc[3] = sp.w;
-          }
-          partners_from_global<LP>(A, T, pbeg + t, pbeg, n, s_poff[sb], acc);
-          st4<double, LG>(A.grad, pbeg + t, V4<double>{acc[0], acc[1], acc[2], acc[3]});
-        }
+        big_event<LP, LS, LG>(A, T, e0 + sb, pbeg, s_off[sb + 1] - pbeg, s_poff[sb]);
         sb++;
         __syncthreads();
         continue;
       }
       const int np = (int)(s_off[sbe] - pbeg);
-      // (a) raw particles and their leg exponents
-      V4<double> x = {0.0, 0.0, 0.0, 0.0};
+      const int ns = sbe - sb;
+      // (a) raw particles, the larger high word of pt and |m|; the events' order
       if (k < np) {
-        x = ld4c<LP>(A.p, pbeg + k);
+        const V4<double> x = ld4c<LP>(A.p, pbeg + k);
         s_pt[k] = x.x;
         s_eta[k] = x.y;
         s_phi[k] = x.z;
         s_m[k] = x.w;
-        s_ex[k] = ffm::leg_exponent(x.x, x.w);
+        s_sc[k] = (int)ffm::umax32(ffm::dhi(x.x), ffm::dhi(x.w) & 0x7fffffffu);
       }
-      __syncthreads();
-      // (b) the particle's event and scale and its ff leg terms; and the order of phase (c):
-      // events by decreasing size, so that the partner loops of a warp have similar lengths
-      if (k < np) {
-        int e = sb, hi = sbe - 1;  // the particle's event: the last e with s_off[e] <= pbeg + k
-        while (e < hi) {
-          const int mid = (e + hi + 1) >> 1;
-          if (s_off[mid] <= pbeg + k) e = mid;
-          else hi = mid - 1;
-        }
-        int emax = 0;
-        for (int t = (int)(s_off[e] - pbeg); t < (int)(s_off[e + 1] - pbeg); t++)
-          emax = s_ex[t] > emax ? s_ex[t] : emax;
-        int sc = kNoFast;
-        if (ffm::scale_exponent_ok(emax) && ffm::leg_in_domain(x.x, x.y, x.z, x.w, emax)) {
-          bool ok = true;
-          const ffm::LegGradFF L = ffm::leg_grad_prep(x.x, x.y, x.w, emax - 1023, T, &ok);
-          if (ok) {
-            sc = emax - 1023;
-            s_leg[k] = L;
-          }
-        }
-        s_fs[k] = sc;
-      }
-      const int ns = sbe - sb;
       if (threadIdx.x < ns) {  // rank of event sb + threadIdx.x: larger first, ties by position
         const int me = sb + threadIdx.x;
         const int64_t nme = s_off[me + 1] - s_off[me];
@@ -261,63 +282,151 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
         s_start[rank] = (int)before;
       }
       __syncthreads();
-      // (c) one particle per thread in that order: its event-sum part, then its partners in
-      // order; fast-path terms accumulate in ff at the event's scale
+      // the particle this thread takes in (b) and (c): thread k holds position k of the sorted
+      // events
+      int e = 0, b0 = 0, li = 0, p = 0;
       if (k < np) {
-        int r = 0, hi = ns - 1;  // the sorted event holding thread position k
+        int r = 0, hi = ns - 1;
         while (r < hi) {
           const int mid = (r + hi + 1) >> 1;
           if (s_start[mid] <= k) r = mid;
           else hi = mid - 1;
         }
-        const int e = s_order[r];
-        const int b0 = (int)(s_off[e] - pbeg);
-        const int li32 = k - s_start[r];
-        const int p = b0 + li32;  // the particle this thread now takes
-        const V4<double> xp = {s_pt[p], s_eta[p], s_phi[p], s_m[p]};
-        const int sc = s_fs[p];
-        ffm::ff acc_f[4] = {ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f), ffm::make(0.0f)};
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};  // FP64 contributions (off the fast path)
+        e = s_order[r];
+        b0 = (int)(s_off[e] - pbeg);
+        li = k - s_start[r];
+        p = b0 + li;
+      }
+      const int n = k < np ? (int)(s_off[e + 1] - s_off[e]) : 0;
+      // (b) the particle's event scale, domain and light-cone terms
+      int sc = kNoFast;
+      if (k < np) {
+        uint32_t wmax = 0;
+        for (int t = b0; t < b0 + n; t++) wmax = ffm::umax32((uint32_t)s_sc[t], wmax);
+        const double pt = s_pt[p], eta = s_eta[p], phi = s_phi[p], m = s_m[p];
+        const uint32_t ew = wmax & 0x7ff00000u;
+        const uint32_t hp = ffm::dhi(pt), hm = ffm::dhi(m) & 0x7fffffffu;
+        const uint32_t he = ffm::dhi(eta) & 0x7fffffffu, hf = ffm::dhi(phi) & 0x7fffffffu;
+        if (wmax - (200u << 20) < (1700u << 20) &&
+            ffm::umin32(hp - 0x100000u, hm - 0x100000u) >= ew - (41u << 20) &&
+            ffm::umax32(hp, hm) >= 0x100000u && he < 0x40200000u && hf < 0x400C0000u) {
+          const uint32_t rb = ew - (127u << 20);
+          const ff pt_i = ffm::cvt1(ffm::cvt_parts(hp, ffm::dlo(pt), rb));
+          const ff mmf = ffm::cvt1(ffm::cvt_parts(hm, ffm::dlo(m), rb));
+          const ff xe = ffm::cvt1(ffm::cvt_parts_normal(ffm::umax32(he, 0x3E100000u),
+                                                        ffm::dlo(eta), ffm::kRebaseOne));
+          ff sh, ch;
+          const ffm::LcLeg<ff> L = ffm::lc_leg(pt_i, mmf, xe, T.hyp, &sh, &ch);
+          s_pY[p] = pack4(pt_i, L.Y);
+          s_DE[p] = pack4(L.D, L.E);
+          s_cs[p] = pack4(ch, sh);
+          s_mm[p] = make_float2(mmf.hi, mmf.lo);
+          sc = (int)ew;
+        }
+        s_fs[p] = sc;
+        // the event-sum part starts the particle's FP64 slot
+        V4<double> sp = {0.0, 0.0, 0.0, 0.0};
         if (A.has_gsum) {
           const V4<double> gsv = ld4c<LS>(A.gsum, e0 + e);
-          if (sc == kNoFast || !sum_part_ff(s_leg[p], xp.z, gsv, T, acc_f)) {
-            const V4<double> sp = sum_part(xp, gsv, T);
-            acc[0] = sp.x;
-            acc[1] = sp.y;
-            acc[2] = sp.z;
-            acc[3] = sp.w;
+          const V4<double> xp = {pt, eta, phi, m};
+          bool done = false;
+          if (sc != kNoFast) {
+            const float4 pY = s_pY[p], DE = s_DE[p], cs = s_cs[p];
+            const float2 mm2 = s_mm[p];
+            done = sum_part_lc(ff{pY.x, pY.y}, ff{DE.z, DE.w}, ff{mm2.x, mm2.y}, ff{cs.x, cs.y},
+                               ff{cs.z, cs.w}, eta, phi, m, (uint32_t)sc - (127u << 20), gsv, T, &sp);
           }
+          if (!done) sp = sum_part(xp, gsv);
         }
-        const int64_t n = s_off[e + 1] - s_off[e], li = li32, pair0 = s_poff[e];
-        for (int64_t lj = 0; lj < n; lj++) {
-          if (lj == li) continue;
-          const int64_t rr = li < lj ? li : lj, q = li < lj ? lj : li;
-          const double g = __ldg(A.gpm + pair0 + rr * n - rr * (rr + 1) / 2 + (q - rr - 1));
-          const int j = b0 + (int)lj;
-          int done = 0;
-          if (sc != kNoFast && s_fs[j] != kNoFast) {
-            const ffm::LegGradFF &a = s_leg[p], &b = s_leg[j];
-            ffm::PairGradFF pg;
-            done = ffm::pair_grad_terms(a, b, xp.y, s_eta[j], xp.z, s_phi[j], g, T, &pg);
-            if (done == 2) {
-              ffm::ff t[4];
-              ffm::leg_grad_terms(a, b, pg, pg.sdeta, pg.sdphi, t);
-              for (int c = 0; c < 4; c++) acc_f[c] = ffm::add(acc_f[c], t[c]);
+        s_acc[p] = make_double4(sp.x, sp.y, sp.z, sp.w);
+      }
+      __syncthreads();
+      // (c) the partners in order, then the event-sum part and the conversion
+      if (k < np) {
+        const double eta_i = s_eta[p], phi_i = s_phi[p];
+        const int64_t pair0 = s_poff[e];
+        ff2 A12 = {ffm::bc2(0.0f), ffm::bc2(0.0f)};  // (A1, A2)
+        ff2 A34 = A12, A56 = A12;                    // (A3, A4), (A5, A6)
+        ff A7 = {0.0f, 0.0f};
+        // packed index of pair (min(li, j), max(li, j)): for j < li it is j n - j(j+1)/2 + li - j - 1
+        // (step n - j - 2), for j > li it is li n - li(li+1)/2 + j - li - 1 (step 1)
+        int64_t idx = li - 1;  // the index for j = 0 (when li > 0)
+        for (int j = 0; j < n; j++) {
+          if (j == li) {
+            idx = (int64_t)li * n - (int64_t)li * (li + 1) / 2;  // the index for j = li + 1
+            continue;
+          }
+          const double g = __ldg(A.gpm + pair0 + idx);
+          idx += j < li ? n - j - 2 : 1;
+          const int q = b0 + j;
+          const uint32_t hg = ffm::dhi(g) & 0x7fffffffu;
+          bool done = false;
+          if (sc != kNoFast && s_fs[q] != kNoFast) {
+            if ((hg | ffm::dlo(g)) == 0u) {
+              done = true;  // gm = 0: no contribution
+            } else if (hg - (963u << 20) < (81u << 20)) {  // |gm| in [2^-60, 2^20]
+              ff S;
+              ff2 sd;
+              const bool oka = ffm::lc_pair_angles(eta_i, s_eta[q], phi_i, s_phi[q], T, &S, &sd);
+              const float4 pY = s_pY[q], DE = s_DE[q];
+              const ff pt_j = {pY.x, pY.y}, Y_j = {pY.z, pY.w}, D_j = {DE.x, DE.y}, E_j = {DE.z, DE.w};
+              const float4 pYi = s_pY[p];  // the thread's own particle, read again (registers)
+              const float2 Di = reinterpret_cast<const float2 *>(s_DE + p)[0];
+              ff m2s;
+              const bool okm = ffm::lc_pair_m2(ff{pYi.x, pYi.y}, pt_j, ff{pYi.z, pYi.w}, Y_j,
+                                               ff{Di.x, Di.y}, D_j, S, &m2s);
+              if (oka && okm) {
+                done = true;
+                if (m2s.hi != 0.0f) {  // where m = 0 the gradient is 0
+                  const ff m = ffm::lc_sqrt_refined(m2s);
+                  const ff gf = ffm::cvt1(ffm::cvt_parts(hg, ffm::dlo(g), ffm::kRebaseOne));
+                  const ff c = ffm::lc_scale(ffm::lc_div(gf, ff{ffm::fmul(m.hi, 2.0f), ffm::fmul(m.lo, 2.0f)}),
+                                             ffm::sign_of(g));
+                  const ff2 cb = {ffm::bc2(c.hi), ffm::bc2(c.lo)};
+                  A12 = ffm::add_same(A12, ffm::lc_mul(cb, ff2{ffm::mk2(D_j.hi, Y_j.hi), ffm::mk2(D_j.lo, Y_j.lo)}));
+                  const ff cE = ffm::lc_mul(c, E_j);
+                  A34 = ffm::add_same(A34, ff2{ffm::mk2(c.hi, cE.hi), ffm::mk2(c.lo, cE.lo)});
+                  const ff cp = ffm::lc_mul(c, pt_j);
+                  A56 = ffm::add_same(A56, ffm::lc_mul(ff2{ffm::bc2(cp.hi), ffm::bc2(cp.lo)},
+                                                  ff2{ffm::mk2(S.hi, sd.hi.x), ffm::mk2(S.lo, sd.lo.x)}));
+                  A7 = ffm::add_same(A7, ffm::lc_mul(cp, ffm::lane_y(sd)));
+                }
+              }
             }
           }
-          if (!done) {
-            V4<double> g1, g2;
-            pair_mass_grad(xp, V4<double>{s_pt[j], s_eta[j], s_phi[j], s_m[j]}, g, g1, g2);
-            acc[0] += g1.x;
-            acc[1] += g1.y;
-            acc[2] += g1.z;
-            acc[3] += g1.w;
-          }
+          if (!done)  // into this thread's own slot
+            slow_pair_add(V4<double>{s_pt[p], eta_i, phi_i, s_m[p]},
+                          V4<double>{s_pt[q], s_eta[q], s_phi[q], s_m[q]}, g, s_acc + p);
         }
-        double out[4] = {0.0, 0.0, 0.0, 0.0};
-        if (sc != kNoFast) ffm::leg_grad_out(acc_f, sc, out);
-        st4<double, LG>(A.grad, pbeg + p,
-                        V4<double>{out[0] + acc[0], out[1] + acc[1], out[2] + acc[2], out[3] + acc[3]});
+        // the pair part from the accumulators, plus the FP64 slot (event-sum part, slow pairs)
+        const double4 a = s_acc[p];
+        double out[4] = {a.x, a.y, a.z, a.w};
+        if (sc != kNoFast) {
+          const float4 DE = s_DE[p], cs = s_cs[p];
+          const float2 mm2 = s_mm[p];
+          const ff E_i = {DE.z, DE.w}, ch = {cs.x, cs.y}, sh = {cs.z, cs.w}, mm = {mm2.x, mm2.y};
+          const uint32_t eoff_s = (uint32_t)sc - (127u << 20);  // 2^s
+          const float4 pYi = s_pY[p];
+          const ff pt_i = {pYi.x, pYi.y}, Y_i = {pYi.z, pYi.w}, D_i = {DE.x, DE.y};
+          const ff2 yd = ffm::lc_mul(ff2{ffm::mk2(Y_i.hi, D_i.hi), ffm::mk2(Y_i.lo, D_i.lo)}, A12);
+          const ff G = ffm::add_same(ffm::lane_x(yd), ffm::lc_scale(ffm::lane_y(yd), -1.0f));  // Y A1 - D A2
+          const ff rE = ffm::lc_div(ff{1.0f, 0.0f}, E_i);
+          const float seta = ffm::sign_of(eta_i), sm = ffm::sign_of(s_m[p]);
+          const ff dpt = ffm::add_same(ffm::lc_mul(ffm::lc_mul(ch, rE), G),
+                                       ff{ffm::fmul(ffm::lane_x(A56).hi, 4.0f), ffm::fmul(ffm::lane_x(A56).lo, 4.0f)});
+          const ff deta = ffm::add_same(ffm::lc_scale(ffm::lc_mul(ffm::lc_mul(ffm::lc_mul(pt_i, sh), rE), G), seta),
+                                        ffm::lc_mul(pt_i, ffm::lane_y(A56)));
+          const ff dphi = ffm::lc_mul(pt_i, A7);
+          const ff dm = ffm::lc_scale(ffm::lc_mul(ffm::lc_mul(mm, rE),
+                                                  ffm::add_same(ffm::lc_mul(E_i, ffm::lane_x(A34)), ffm::lane_y(A34))),
+                                      2.0f * sm);
+          constexpr uint32_t kUnscaled = 896u << 20;
+          out[0] += ffm::lc_to_double(dpt, kUnscaled);
+          out[1] += ffm::lc_to_double(deta, eoff_s);
+          out[2] += ffm::lc_to_double(dphi, eoff_s);
+          out[3] += ffm::lc_to_double(dm, kUnscaled);
+        }
+        st4<double, LG>(A.grad, pbeg + p, V4<double>{out[0], out[1], out[2], out[3]});
       }
       __syncthreads();  // before the next sub-batch overwrites the staged particles
       sb = sbe;

@@ -42,6 +42,36 @@ GVX_HD F lc_scale(const F &x, lane_t<F> k) {
 
 GVX_HD float sign_of(double d) { return (dhi(d) >> 31) ? -1.0f : 1.0f; }
 
+// The angular terms of a pair for its adjoint: *S = sinh^2(|d_eta|/2) + sin^2(|d_phi|/2) and
+// *sd = (2 sinh(d_eta), 2 sin(d_phi)) = 4 (sinh, sin)(cosh, cos) of the half-angles, signed like
+// d_eta = eta1 - eta2 and d_phi = phi1 - phi2 (both FP64 differences, as in the forward).  False
+// when |d_phi|/2 is within 2^-7 of pi (the caller takes the FP64 formulas).
+GVX_HD bool lc_pair_angles(double eta1, double eta2, double phi1, double phi2, const LcTab &T,
+                           ff *S, ff2 *sd) {
+  const double de = eta1 - eta2, dp = phi1 - phi2;
+  const uint32_t hde = dhi(de) & 0x7fffffffu, hdp = dhi(dp) & 0x7fffffffu;
+  const CvtParts cp = cvt_parts(hdp, dlo(dp), kRebaseHalf);
+  const ff2 xa = cvt2(cvt_parts(hde, dlo(de), kRebaseHalf), cp);
+  const int32_t e3 = (int32_t)(cp.hb & 0x7f800000u) - (int32_t)(46u << 23);
+  const uint32_t el3 = (uint32_t)(e3 > 0 ? e3 : 0);
+  const float lo3 = fsub(u2f(el3 | ((dlo(dp) & 63u) << 17)), u2f(el3));
+  uint32_t nj[2];
+  ff2 r = lc_reduce(xa, nj);
+  r.lo = add2(r.lo, mk2(0.0f, lo3));
+  const gvx_f4 th = ldtab(&T.hyp[umin32(nj[0], GVX_HYP_N)]);
+  const gvx_f4 ts = ldtab(&T.sin[umin32(nj[1], GVX_SIN_N)]);
+  const ff2 A = {mk2(th.z, ts.x), mk2(th.w, ts.y)};    // (sinh, sin) of the table point
+  const ff2 B = {mk2(th.x, ts.z), mk2(th.y, ts.w)};    // (cosh, cos)
+  const ff2 Bn = {mk2(th.z, -ts.x), mk2(th.w, -ts.y)};  // (sinh, -sin)
+  const TabPoly<f2> tp = tab_poly(r, mk2(0.5f, -0.5f));
+  const ff2 w = tab_comb(A, B, r, tp);        // (sinh |d_eta|/2, sin |d_phi|/2)
+  const ff2 wc = tab_comb_any(B, Bn, r, tp);  // (cosh |d_eta|/2, cos |d_phi|/2)
+  const ff2 w2 = lc_sqr(w);
+  *S = lc_add(lane_x(w2), lane_y(w2));
+  *sd = lc_scale(lc_mul(w, wc), mk2(4.0f * sign_of(de), 4.0f * sign_of(dp)));
+  return nj[1] - 802u > 4u;
+}
+
 // gm dm/d(pt, eta, phi, m) of both legs: out[0..3] leg 1, out[4..7] leg 2.  has_ms: ms is the
 // forward's mass of this pair.  False outside the fast-path domain (out untouched).
 GVX_HD bool pair_mass_grad_lc(double pt1, double eta1, double phi1, double m1, double pt2,
@@ -70,30 +100,10 @@ GVX_HD bool pair_mass_grad_lc(double pt1, double eta1, double phi1, double m1, d
   }
   const uint32_t rb = ew - (127u << 20);
 
-  // -- angular terms: lanes (sinh, sin) and (cosh, cos) of the half-angles |d_eta|/2, |d_phi|/2 --
-  const double de = eta1 - eta2, dp = phi1 - phi2;
-  const uint32_t hde = dhi(de) & 0x7fffffffu, hdp = dhi(dp) & 0x7fffffffu;
-  const CvtParts cp = cvt_parts(hdp, dlo(dp), kRebaseHalf);
-  const ff2 xa = cvt2(cvt_parts(hde, dlo(de), kRebaseHalf), cp);
-  const int32_t e3 = (int32_t)(cp.hb & 0x7f800000u) - (int32_t)(46u << 23);
-  const uint32_t el3 = (uint32_t)(e3 > 0 ? e3 : 0);
-  const float lo3 = fsub(u2f(el3 | ((dlo(dp) & 63u) << 17)), u2f(el3));
-  uint32_t nj[2];
-  ff2 r = lc_reduce(xa, nj);
-  r.lo = add2(r.lo, mk2(0.0f, lo3));
-  if (nj[1] - 802u <= 4u) return false;  // |d_phi|/2 within 2^-7 of pi
-  const gvx_f4 th = ldtab(&T.hyp[umin32(nj[0], GVX_HYP_N)]);
-  const gvx_f4 ts = ldtab(&T.sin[umin32(nj[1], GVX_SIN_N)]);
-  const ff2 A = {mk2(th.z, ts.x), mk2(th.w, ts.y)};    // (sinh, sin) of the table point
-  const ff2 B = {mk2(th.x, ts.z), mk2(th.y, ts.w)};    // (cosh, cos)
-  const ff2 Bn = {mk2(th.z, -ts.x), mk2(th.w, -ts.y)};  // (sinh, -sin)
-  const TabPoly<f2> tp = tab_poly(r, mk2(0.5f, -0.5f));
-  const ff2 w = tab_comb(A, B, r, tp);        // (sinh |d_eta|/2, sin |d_phi|/2)
-  const ff2 wc = tab_comb_any(B, Bn, r, tp);  // (cosh |d_eta|/2, cos |d_phi|/2)
-  const ff2 w2 = lc_sqr(w);
-  const ff S = lc_add(lane_x(w2), lane_y(w2));
-  // 2 (sinh d_eta, sin d_phi) = 4 (sinh, sin)(cosh, cos), signed like d_eta and d_phi
-  const ff2 sd = lc_scale(lc_mul(w, wc), mk2(4.0f * sign_of(de), 4.0f * sign_of(dp)));
+  // -- angular terms --
+  ff S;
+  ff2 sd;
+  if (!lc_pair_angles(eta1, eta2, phi1, phi2, T, &S, &sd)) return false;
 
   // -- the legs (lane x: leg 1, lane y: leg 2) --
   const ff2 pt = cvt2(cvt_parts(hp1, dlo(pt1), rb), cvt_parts(hp2, dlo(pt2), rb));
