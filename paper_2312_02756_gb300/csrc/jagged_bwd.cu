@@ -17,21 +17,23 @@
 // stays within ~2^-47 of the summed magnitudes)
 //   A1 = sum c D_j,  A2 = sum c Y_j,  A3 = sum c,  A4 = sum c E_j,  A5 = sum c pt_j S_ij,
 //   A6 = sum c pt_j 2 sinh(eta_i - eta_j),  A7 = sum c pt_j 2 sin(phi_i - phi_j),
-// so that a partner costs its angular terms, its pair mass and seven float-float
+// so that a pair costs its angular terms and its mass once and each direction seven float-float
 // multiply-accumulates (paired FP32 lanes where two share a factor).
 //
-// One thread per particle walks its partners in a fixed order, so the result does not depend on
-// scheduling and no atomics are needed.  CTAs take tiles of kTE consecutive events (grid-stride
-// over tiles) and stage them in sub-batches of whole events of at most kNT particles: (a) the
-// raw particles, and the order of the sub-batch's events by decreasing size (so that the lanes
-// of a warp walk partner loops of similar length); (b) per particle, by the thread that will
-// take it in (c), its event's scale and light-cone terms (at the event's scale, as the forward
-// kernel stages them) and its event-sum part J^T gs (float-float, in double in the thread's own
-// shared-memory slot); (c) the partner loop, the pair part from the accumulators and the
-// conversion to double.  Pairs outside the float-float domain (either
-// particle outside the forward's domain at the event scale, |d_phi|/2 within 2^-7 of pi, a scaled
-// m^2 below 2^-80, |gm| outside [2^-60, 2^20]) take the FP64 formulas, summed in FP64 in the
-// thread's own shared-memory slot.  An event with more than kNT particles is handled alone,
+// CTAs take tiles of kTE consecutive events (grid-stride over tiles) and stage them in
+// sub-batches of whole events of at most kNT particles and kPC pairs: (a) the raw particles, and
+// the order of the sub-batch's events by decreasing size (so that the lanes of a warp walk
+// partner loops of similar length); (b) per particle, by the thread that will take it in (d),
+// its event's scale and light-cone terms (at the event's scale, as the forward kernel stages
+// them) and its event-sum part J^T gs (float-float, in double in the thread's own shared-memory
+// slot); (c) one thread per pair: the pair's angular terms, m and c once, stored per pair as
+// c, c S and c (2 sinh d_eta, 2 sin d_phi); (d) one thread per particle walks its partners in a
+// fixed order, adding the seven sums from the pair slots and the partners' staged terms, and
+// assembles and converts its gradient -- so the result does not depend on scheduling and no
+// atomics are needed.  Pairs outside the float-float domain (either particle outside the
+// forward's domain at the event scale, |d_phi|/2 within 2^-7 of pi, a scaled m^2 below 2^-80,
+// |gm| outside [2^-60, 2^20]) are marked in (c) and take the FP64 formulas in (d), summed in FP64
+// in the thread's own slot.  An event with more than kNT particles or kPC pairs is handled alone,
 // straight from global memory, with the elementwise kernels' pair adjoint.  The pair offsets are
 // those the forward call wrote; each tile checks them (and the offsets) against the event sizes
 // and the pair count before it reads any pair gradient, and records GVX_ERR_OFFSETS for a tile
@@ -42,20 +44,24 @@
 
 #include "common.cuh"
 #include "mass_lc_grad.cuh"
+#include "pair_index.cuh"
 #include "pair_math.cuh"
 
 namespace gvx {
 namespace {
 
-constexpr int kTE = 28;   // events per tile (about 224 particles at the benchmark multiplicity)
-constexpr int kNT = 256;  // threads per CTA, and particles staged per sub-batch
+constexpr int kTE = 14;    // events per tile (about 112 particles at the benchmark multiplicity)
+constexpr int kNT = 128;   // threads per CTA, and particles staged per sub-batch
+constexpr int kPC = 640;   // pairs staged per sub-batch (the events of a sub-batch average ~450)
 constexpr int kNoFast = INT_MIN;  // scale marker of a particle outside the float-float domain
+constexpr uint32_t kSlowPair = 0x7fc00000u;  // the bits of c.hi marking a pair for FP64
 // per staged particle: pt, eta, phi, m and the FP64 accumulator (doubles); (pt, Y), (D, E),
 // (cosh, sinh) (float4) and m (float2); the larger high word of pt and |m|, and its event's scale
-// field or kNoFast (ints)
+// field or kNoFast (ints); per staged pair: (c, c S) and (c 2 sinh d_eta, c 2 sin d_phi) (float4)
 constexpr size_t kDynSmem =
     (size_t)kNT * (4 * sizeof(double) + sizeof(double4) + 3 * sizeof(float4) + sizeof(float2) +
-                   2 * sizeof(int));
+                   2 * sizeof(int)) +
+    (size_t)kPC * 2 * sizeof(float4);
 
 struct BArgs {
   Lv p;
@@ -203,7 +209,7 @@ __device__ __forceinline__ float4 pack4(const ffm::ff &a, const ffm::ff &b) {
 }
 
 template <int LP, int LS, int LG>
-__global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
+__global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
   using ffm::ff;
   using ffm::ff2;
   extern __shared__ double s_dyn[];
@@ -214,6 +220,8 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
   float4 *s_cs = s_DE + kNT;                                // (cosh, sinh) of |eta|
   float2 *s_mm = reinterpret_cast<float2 *>(s_cs + kNT);    // |m|
   int *s_sc = reinterpret_cast<int *>(s_mm + kNT), *s_fs = s_sc + kNT;
+  float4 *s_w0 = reinterpret_cast<float4 *>(s_fs + kNT);  // per pair: (c, c S)
+  float4 *s_w1 = s_w0 + kPC;                              // (c 2 sinh d_eta, c 2 sin d_phi)
   __shared__ int64_t s_off[kTE + 1], s_poff[kTE + 1];
   __shared__ int s_order[kTE], s_start[kTE];
   __shared__ int s_bad;
@@ -246,10 +254,11 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
     int sb = 0;
     while (sb < ne) {
       const int64_t pbeg = s_off[sb];
-      const bool fits =
-          threadIdx.x >= sb && threadIdx.x < ne && s_off[threadIdx.x + 1] - pbeg <= kNT;
+      const bool fits = threadIdx.x >= sb && threadIdx.x < ne &&
+                        s_off[threadIdx.x + 1] - pbeg <= kNT &&
+                        s_poff[threadIdx.x + 1] - s_poff[sb] <= kPC;
       const int sbe = sb + __syncthreads_count(fits);
-      if (sbe == sb) {  // one event larger than a sub-batch
+      if (sbe == sb) {  // one event larger than a sub-batch (particles or pairs)
         big_event<LP, LS, LG>(A, T, e0 + sb, pbeg, s_off[sb + 1] - pbeg, s_poff[sb]);
         sb++;
         __syncthreads();
@@ -341,62 +350,90 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
         s_acc[p] = make_double4(sp.x, sp.y, sp.z, sp.w);
       }
       __syncthreads();
-      // (c) the partners in order, then the event-sum part and the conversion
+      // (c) pair-parallel: each pair's angular terms, m and c = gm / (2m) once, into the pair's
+      // slot (the sd terms for the orientation (i, j), i < j); a pair outside the float-float
+      // domain gets the marker kSlowPair
+      const int64_t q0 = s_poff[sb];
+      const int npq = (int)(s_poff[sbe] - q0);
+      for (int q = threadIdx.x; q < npq; q += kNT) {
+        int lo = sb, hi = sbe - 1;  // the pair's event: the last with s_poff[ev] <= q0 + q
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_poff[mid] <= q0 + q) lo = mid;
+          else hi = mid - 1;
+        }
+        int64_t i, j;
+        decode_pair(q0 + q - s_poff[lo], s_off[lo + 1] - s_off[lo], i, j);
+        const int ia = (int)(s_off[lo] - pbeg + i), ib = (int)(s_off[lo] - pbeg + j);
+        const double g = __ldg(A.gpm + q0 + q);
+        const uint32_t hg = ffm::dhi(g) & 0x7fffffffu;
+        float4 w0 = make_float4(__uint_as_float(kSlowPair), 0.0f, 0.0f, 0.0f);
+        float4 w1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (s_fs[ia] != kNoFast && s_fs[ib] != kNoFast) {
+          if ((hg | ffm::dlo(g)) == 0u) {
+            w0 = w1;  // gm = 0: no contribution
+          } else if (hg - (963u << 20) < (81u << 20)) {  // |gm| in [2^-60, 2^20]
+            ff S;
+            ff2 sd;
+            const bool oka = ffm::lc_pair_angles(s_eta[ia], s_eta[ib], s_phi[ia], s_phi[ib], T, &S, &sd);
+            const float4 pa = s_pY[ia], pb = s_pY[ib], da = s_DE[ia], db = s_DE[ib];
+            ff m2s;
+            const bool okm = ffm::lc_pair_m2(ff{pa.x, pa.y}, ff{pb.x, pb.y}, ff{pa.z, pa.w},
+                                             ff{pb.z, pb.w}, ff{da.x, da.y}, ff{db.x, db.y}, S, &m2s);
+            if (oka && okm) {
+              w0 = w1;  // m = 0: the gradient is 0
+              if (m2s.hi != 0.0f) {
+                const ff m = ffm::lc_sqrt_refined(m2s);
+                const ff gf = ffm::cvt1(ffm::cvt_parts(hg, ffm::dlo(g), ffm::kRebaseOne));
+                const ff c = ffm::lc_scale(ffm::lc_div(gf, ff{ffm::fmul(m.hi, 2.0f), ffm::fmul(m.lo, 2.0f)}),
+                                           ffm::sign_of(g));
+                const ff cS = ffm::lc_mul(c, S);
+                const ff2 csd = ffm::lc_mul(ff2{ffm::bc2(c.hi), ffm::bc2(c.lo)}, sd);
+                w0 = make_float4(c.hi, c.lo, cS.hi, cS.lo);
+                w1 = make_float4(csd.hi.x, csd.lo.x, csd.hi.y, csd.lo.y);
+              }
+            }
+          }
+        }
+        s_w0[q] = w0;
+        s_w1[q] = w1;
+      }
+      __syncthreads();
+      // (d) per particle, its partners in order: seven float-float sums from the pair slots, the
+      // FP64 formulas for marked pairs; then the pair part and the conversion
       if (k < np) {
-        const double eta_i = s_eta[p], phi_i = s_phi[p];
-        const int64_t pair0 = s_poff[e];
+        const int slot0 = (int)(s_poff[e] - q0);  // the event's first pair slot
         ff2 A12 = {ffm::bc2(0.0f), ffm::bc2(0.0f)};  // (A1, A2)
         ff2 A34 = A12, A56 = A12;                    // (A3, A4), (A5, A6)
         ff A7 = {0.0f, 0.0f};
         // packed index of pair (min(li, j), max(li, j)): for j < li it is j n - j(j+1)/2 + li - j - 1
         // (step n - j - 2), for j > li it is li n - li(li+1)/2 + j - li - 1 (step 1)
-        int64_t idx = li - 1;  // the index for j = 0 (when li > 0)
+        int idx = li - 1;  // the index for j = 0 (when li > 0)
         for (int j = 0; j < n; j++) {
           if (j == li) {
-            idx = (int64_t)li * n - (int64_t)li * (li + 1) / 2;  // the index for j = li + 1
+            idx = li * n - li * (li + 1) / 2;  // the index for j = li + 1
             continue;
           }
-          const double g = __ldg(A.gpm + pair0 + idx);
+          const int pidx = idx;
           idx += j < li ? n - j - 2 : 1;
+          const float4 w0 = s_w0[slot0 + pidx], w1 = s_w1[slot0 + pidx];
           const int q = b0 + j;
-          const uint32_t hg = ffm::dhi(g) & 0x7fffffffu;
-          bool done = false;
-          if (sc != kNoFast && s_fs[q] != kNoFast) {
-            if ((hg | ffm::dlo(g)) == 0u) {
-              done = true;  // gm = 0: no contribution
-            } else if (hg - (963u << 20) < (81u << 20)) {  // |gm| in [2^-60, 2^20]
-              ff S;
-              ff2 sd;
-              const bool oka = ffm::lc_pair_angles(eta_i, s_eta[q], phi_i, s_phi[q], T, &S, &sd);
-              const float4 pY = s_pY[q], DE = s_DE[q];
-              const ff pt_j = {pY.x, pY.y}, Y_j = {pY.z, pY.w}, D_j = {DE.x, DE.y}, E_j = {DE.z, DE.w};
-              const float4 pYi = s_pY[p];  // the thread's own particle, read again (registers)
-              const float2 Di = reinterpret_cast<const float2 *>(s_DE + p)[0];
-              ff m2s;
-              const bool okm = ffm::lc_pair_m2(ff{pYi.x, pYi.y}, pt_j, ff{pYi.z, pYi.w}, Y_j,
-                                               ff{Di.x, Di.y}, D_j, S, &m2s);
-              if (oka && okm) {
-                done = true;
-                if (m2s.hi != 0.0f) {  // where m = 0 the gradient is 0
-                  const ff m = ffm::lc_sqrt_refined(m2s);
-                  const ff gf = ffm::cvt1(ffm::cvt_parts(hg, ffm::dlo(g), ffm::kRebaseOne));
-                  const ff c = ffm::lc_scale(ffm::lc_div(gf, ff{ffm::fmul(m.hi, 2.0f), ffm::fmul(m.lo, 2.0f)}),
-                                             ffm::sign_of(g));
-                  const ff2 cb = {ffm::bc2(c.hi), ffm::bc2(c.lo)};
-                  A12 = ffm::add_same(A12, ffm::lc_mul(cb, ff2{ffm::mk2(D_j.hi, Y_j.hi), ffm::mk2(D_j.lo, Y_j.lo)}));
-                  const ff cE = ffm::lc_mul(c, E_j);
-                  A34 = ffm::add_same(A34, ff2{ffm::mk2(c.hi, cE.hi), ffm::mk2(c.lo, cE.lo)});
-                  const ff cp = ffm::lc_mul(c, pt_j);
-                  A56 = ffm::add_same(A56, ffm::lc_mul(ff2{ffm::bc2(cp.hi), ffm::bc2(cp.lo)},
-                                                  ff2{ffm::mk2(S.hi, sd.hi.x), ffm::mk2(S.lo, sd.lo.x)}));
-                  A7 = ffm::add_same(A7, ffm::lc_mul(cp, ffm::lane_y(sd)));
-                }
-              }
-            }
+          if (__float_as_uint(w0.x) == kSlowPair) {  // into this thread's own slot
+            slow_pair_add(V4<double>{s_pt[p], s_eta[p], s_phi[p], s_m[p]},
+                          V4<double>{s_pt[q], s_eta[q], s_phi[q], s_m[q]},
+                          __ldg(A.gpm + s_poff[e] + pidx), s_acc + p);
+            continue;
           }
-          if (!done)  // into this thread's own slot
-            slow_pair_add(V4<double>{s_pt[p], eta_i, phi_i, s_m[p]},
-                          V4<double>{s_pt[q], s_eta[q], s_phi[q], s_m[q]}, g, s_acc + p);
+          const float sg = j > li ? 1.0f : -1.0f;  // the slot's sd terms are for (min, max)
+          const float4 pY = s_pY[q], DE = s_DE[q];
+          const ff c = {w0.x, w0.y};
+          const ff2 cb = {ffm::bc2(c.hi), ffm::bc2(c.lo)};
+          A12 = ffm::add_same(A12, ffm::lc_mul(cb, ff2{ffm::mk2(DE.x, pY.z), ffm::mk2(DE.y, pY.w)}));
+          const ff cE = ffm::lc_mul(c, ff{DE.z, DE.w});
+          A34 = ffm::add_same(A34, ff2{ffm::mk2(c.hi, cE.hi), ffm::mk2(c.lo, cE.lo)});
+          const ff2 ptb = {ffm::bc2(pY.x), ffm::bc2(pY.y)};
+          A56 = ffm::add_same(A56, ffm::lc_mul(ptb, ff2{ffm::mk2(w0.z, sg * w1.x), ffm::mk2(w0.w, sg * w1.y)}));
+          A7 = ffm::add_same(A7, ffm::lc_mul(ff{pY.x, pY.y}, ff{sg * w1.z, sg * w1.w}));
         }
         // the pair part from the accumulators, plus the FP64 slot (event-sum part, slow pairs)
         const double4 a = s_acc[p];
@@ -411,7 +448,7 @@ __global__ void __launch_bounds__(kNT, 3) event_pairs_bwd_kernel(BArgs A) {
           const ff2 yd = ffm::lc_mul(ff2{ffm::mk2(Y_i.hi, D_i.hi), ffm::mk2(Y_i.lo, D_i.lo)}, A12);
           const ff G = ffm::add_same(ffm::lane_x(yd), ffm::lc_scale(ffm::lane_y(yd), -1.0f));  // Y A1 - D A2
           const ff rE = ffm::lc_div(ff{1.0f, 0.0f}, E_i);
-          const float seta = ffm::sign_of(eta_i), sm = ffm::sign_of(s_m[p]);
+          const float seta = ffm::sign_of(s_eta[p]), sm = ffm::sign_of(s_m[p]);
           const ff dpt = ffm::add_same(ffm::lc_mul(ffm::lc_mul(ch, rE), G),
                                        ff{ffm::fmul(ffm::lane_x(A56).hi, 4.0f), ffm::fmul(ffm::lane_x(A56).lo, 4.0f)});
           const ff deta = ffm::add_same(ffm::lc_scale(ffm::lc_mul(ffm::lc_mul(ffm::lc_mul(pt_i, sh), rE), G), seta),
