@@ -24,6 +24,7 @@
 #include "cart_fixed.cuh"
 #include "cart_mass.cuh"
 #include "common.cuh"
+#include "pair_math.cuh"
 
 namespace gvx {
 namespace {
@@ -202,9 +203,64 @@ __global__ void __launch_bounds__(256) to_pxpypze_kernel(Lv v, LvOut out, int64_
   }
 }
 
-// Pair masses of PtEtaPhiE legs.  FP64: the float-float identity of ptetaphie_ff.cuh; outside its
-// domain (and in FP32) both legs converted as above, then the exact fixed-point mass of the
-// converted legs (cart_fixed.cuh), the FP64 form outside that one's domain.
+// FP32 PtEtaPhiE pair mass in the form of the FP32 PtEtaPhiM one (pair_math.cuh pair_terms), the
+// mass of v1 + v2 (Sec. 4.1): with P_i = pt_i cosh(eta_i), the stored E_i,
+// m_i^2 = (E_i - P_i)(E_i + P_i), Q = E_1 E_2 - P_1 P_2 and S = sinh^2(d_eta/2) + sin^2(d_phi/2),
+//   m^2 = m_1^2 + m_2^2 + 2 Q + 4 pt_1 pt_2 S     (P_1 P_2 - p_1.p_2 = 2 pt_1 pt_2 S).
+// Every term is bounded by (M_1 + M_2)^2, M_i = max(|E_i|, |P_i|), and carries a few ulps of it,
+// so the error in m|m| stays within ~8 u (M_1 + M_2)^2 (u = 2^-24).  A spacelike sum gives
+// -sqrt(-m^2).  False when m^2 is not finite (the caller takes the exact route).
+__device__ __forceinline__ bool pair_mass_e_f32(const V4<float> &x, const V4<float> &y, float *r) {
+  const float P1 = x.x * coshf(x.y), P2 = y.x * coshf(y.y);
+  const float q1 = (x.w - P1) * (x.w + P1), q2 = (y.w - P2) * (y.w + P2);
+  const float Q = fmaf(x.w, y.w, -P1 * P2);
+  const float se = sinhf(0.5f * (x.y - y.y));
+  const float sp = sinf(half_dphi(x.z, y.z));
+  const float S = fmaf(se, se, sp * sp);
+  const float m2 = fmaf(4.0f * x.x * y.x, S, fmaf(2.0f, Q, q1 + q2));
+  if (!isfinite(m2)) return false;
+  *r = m2 >= 0.0f ? sqrtf(m2) : -sqrtf(-m2);
+  return true;
+}
+
+__device__ __forceinline__ float pair_mass_e_f32_any(const V4<float> &x, const V4<float> &y) {
+  float r;
+  if (pair_mass_e_f32(x, y, &r)) return r;
+  float ca[4], cb[4];
+  to_cart_f32(x, GVX_PTETAPHIE, ca);
+  to_cart_f32(y, GVX_PTETAPHIE, cb);
+  if (!cfix::mass_pxpypze(ca, cb, &r)) {
+    const double pa[4] = {ca[0], ca[1], ca[2], ca[3]}, pb[4] = {cb[0], cb[1], cb[2], cb[3]};
+    r = (float)cart::mass(pa, pb, 0);
+  }
+  return r;
+}
+
+// FP32 PtEtaPhiE pair masses: HBM-bound, so each thread loads kUnrollE pairs (strided by the grid)
+// before it computes any of them, to keep more loads in flight per SM.
+constexpr int kUnrollE = 4;
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(256) mass_ptetaphie_f32_kernel(Lv a, Lv b, float *__restrict__ m,
+                                                                 int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnrollE - 1) * stride < n; i += kUnrollE * stride) {
+    V4<float> x[kUnrollE], y[kUnrollE];
+#pragma unroll
+    for (int u = 0; u < kUnrollE; u++) {
+      x[u] = ld4<float, LA>(a, i + u * stride);
+      y[u] = ld4<float, LB>(b, i + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnrollE; u++) st_s(m + i + u * stride, pair_mass_e_f32_any(x[u], y[u]));
+  }
+  for (; i < n; i += stride) st_s(m + i, pair_mass_e_f32_any(ld4<float, LA>(a, i), ld4<float, LB>(b, i)));
+}
+
+// Pair masses of PtEtaPhiE legs in FP64: the float-float identity of ptetaphie_ff.cuh; outside its
+// domain both legs converted as above, then the exact fixed-point mass of the converted legs
+// (cart_fixed.cuh), the FP64 form outside that one's domain.  (FP32: mass_ptetaphie_f32_kernel.)
 template <typename T, int LA, int LB>
 __global__ void __launch_bounds__(256) mass_ptetaphie_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
   __shared__ ffm::gvx_f4 s_exp[sizeof(T) == 8 ? GVX_EXP_N : 1];
@@ -276,6 +332,22 @@ cudaError_t launch_apply_t(const T *L, const Lv &v, const LvOut &out, int64_t n,
 template <typename T>
 cudaError_t launch_ptetaphie_t(const Lv &a, const Lv &b, T *m, int64_t n, cudaStream_t s) {
   const int threads = 256;
+  if constexpr (sizeof(T) == 4) {
+    if (a.layout == GVX_SOA && b.layout == GVX_SOA) {
+      constexpr auto k = mass_ptetaphie_f32_kernel<GVX_SOA, GVX_SOA>;
+      k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+    } else if (a.layout == GVX_SOA) {
+      constexpr auto k = mass_ptetaphie_f32_kernel<GVX_SOA, GVX_AOS>;
+      k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+    } else if (b.layout == GVX_SOA) {
+      constexpr auto k = mass_ptetaphie_f32_kernel<GVX_AOS, GVX_SOA>;
+      k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+    } else {
+      constexpr auto k = mass_ptetaphie_f32_kernel<GVX_AOS, GVX_AOS>;
+      k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
+    }
+    return cudaGetLastError();
+  }
   if (a.layout == GVX_SOA && b.layout == GVX_SOA) {
     constexpr auto k = mass_ptetaphie_kernel<T, GVX_SOA, GVX_SOA>;
     k<<<balanced_grid_of<k>(threads, 0, n), threads, 0, s>>>(a, b, m, n);
