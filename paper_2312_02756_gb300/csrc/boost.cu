@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) boost_kernel(Lv v, Lv beta, LvOut out, in
 // This is the FP32 evaluation and the FP64 one outside the float-float domain (there gamma, k,
 // k' = (1 + 2 s)/(1 + s)^2 and gamma^3, s = 1/gamma = sqrt(1 - b2), come from float-float
 // arithmetic and the multiply-adds stay in FP64); FP64 inputs inside it take boost_bwd_ff
-// (boost_ff.cuh), which keeps 21 FP64 operations per vector.
+// (boost_ff.cuh), which keeps 15 FP64 operations per vector.
 template <typename T>
 struct BoostCoefBwd {
   BoostCoef<T> c;

@@ -72,13 +72,13 @@ GVX_HD bool boost_ff(const BetaFF &B, double bx, double by, double bz, double px
 // k' = dk/dgamma = gamma (gamma + 2)/(gamma + 1)^2 (so k' - 1 = -(s w)^2):
 //   grad_beta = A beta + B p + f grad_p,
 //   A = gamma^3 [gb (t + (k' - 1) bp) + gE t],   B = k gb + gamma gE,   f = k t + w E.
-// bp, t, gb and tg are FP64 (the sums that can cancel); A, B, f and the boost of grad_out are
-// formed in ff from the scaled inputs and return to double by integer operations; the
-// combinations with beta, p and grad_p are FP64 multiply-adds: 21 FP64 operations per vector.
+// t = E + bp and tg = gE + gb are FP64 (the sums that can cancel); bp = t - E, gb = tg - gE,
+// A, B, f and the boost of grad_out are formed in ff from the scaled inputs and return to double
+// by integer operations; the combinations of grad_beta with beta, p and grad_p are FP64
+// multiply-adds (they can cancel by more than ff would resolve): 15 FP64 operations per vector.
 
 struct BetaBwdFF {
   ff gf, w, k, kpm1, g3;  // gamma, 1/(1 + s), gamma w, k' - 1, gamma^3
-  double g;               // gamma
   bool ok;
 };
 
@@ -93,7 +93,6 @@ GVX_HD BetaBwdFF beta_bwd_ff(double bx, double by, double bz) {
   B.k = mul(g, B.w);
   B.kpm1 = neg(sqr(mul(s, B.w)));
   B.g3 = mul(sqr(g), g);
-  B.g = ok ? to_double_int(g, 0) : 0.0;
   B.ok = ok;
   return B;
 }
@@ -117,23 +116,25 @@ GVX_HD bool boost_bwd_ff(const BetaBwdFF &B, double bx, double by, double bz, co
   }
   if (eq < 200 || eq > 2035 || ev + eq - 2046 < -800 || ev + eq - 2046 > 900) return false;
   const int sv = ev - 1023, sq = eq - 1023;
-  const double bp = fma(bx, p[0], fma(by, p[1], bz * p[2]));
-  const double t = p[3] + bp;
-  const double gb = fma(bx, q[0], fma(by, q[1], bz * q[2]));
-  const double tg = q[3] + gb;
-  const ff T = from_double_ranged(t, sv), BP = from_double_ranged(bp, sv);
-  const ff En = from_double_ranged(p[3], sv);
-  const ff TG = from_double_ranged(tg, sq), GB = from_double_ranged(gb, sq);
-  const ff GE = from_double_ranged(q[3], sq);
+  // the two sums that can cancel, in FP64 as in the forward; beta.p and beta.grad_p follow from
+  // them in ff (t - E is exact up to t's own rounding, which stays at the FP64 level)
+  const double t = fma(bx, p[0], fma(by, p[1], fma(bz, p[2], p[3])));
+  const double tg = fma(bx, q[0], fma(by, q[1], fma(bz, q[2], q[3])));
+  const ff T = from_double_ranged(t, sv), En = from_double_ranged(p[3], sv);
+  const ff BP = add(T, neg(En));
+  const ff TG = from_double_ranged(tg, sq), GE = from_double_ranged(q[3], sq);
+  const ff GB = add(TG, neg(GE));
   const double f = to_double_int(add(mul(B.k, T), mul(B.w, En)), sv);
-  const double fq = to_double_int(add(mul(B.k, TG), mul(B.w, GE)), sq);
+  const ff FQ = add(mul(B.k, TG), mul(B.w, GE));
   const ff A = mul(B.g3, add(mul(GB, add(T, mul(B.kpm1, BP))), mul(GE, T)));
   const double a = to_double_int(renorm(A), sv + sq);
   const double bq = to_double_int(add(mul(B.k, GB), mul(B.gf, GE)), sq);
-  gv[0] = fma(fq, bx, q[0]);
-  gv[1] = fma(fq, by, q[1]);
-  gv[2] = fma(fq, bz, q[2]);
-  gv[3] = B.g * tg;
+  // grad_v = L grad_out in ff (its terms cancel by at most the condition of L, gamma (1 + |beta|)):
+  // q_k + fq beta_k and gamma tg, returned to double by integer operations
+  gv[0] = to_double_int(renorm(add(from_double_ranged(q[0], sq), mul(FQ, from_double_ranged(bx, 0)))), sq);
+  gv[1] = to_double_int(renorm(add(from_double_ranged(q[1], sq), mul(FQ, from_double_ranged(by, 0)))), sq);
+  gv[2] = to_double_int(renorm(add(from_double_ranged(q[2], sq), mul(FQ, from_double_ranged(bz, 0)))), sq);
+  gv[3] = to_double_int(renorm(mul(B.gf, TG)), sq);
   gbeta[0] = fma(a, bx, fma(bq, p[0], f * q[0]));
   gbeta[1] = fma(a, by, fma(bq, p[1], f * q[1]));
   gbeta[2] = fma(a, bz, fma(bq, p[2], f * q[2]));
