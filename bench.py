@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import ctypes
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -36,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "inv-mass & boost vectors/s at N=2^26 FP64/FP32, % roofline; fwd+bwd vs fwd"
 UNIT = "vectors/s"
 N_FULL = 1 << 26
+LOAD_WINDOW_S = 1.5  # seconds of back-to-back untimed steps under the clock sampler
 FORMS = ("fp32", "jagged", "fwd_bwd", "coords")
 WORKLOAD = ("FP64 invariant mass of 2^26 PtEtaPhiM pairs in SoA and in AoS, plus FP64 boost of "
             "2^26 PxPyPzE vectors by per-vector beta (|beta| <= 0.99)")
@@ -87,7 +89,7 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
-    def start(self):
+    def start(self, settle=0.3):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -97,12 +99,12 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(settle)
 
-    def stop(self):
+    def stop(self, settle=0.25):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(settle)
         self.proc.terminate()
         self.proc.wait()
         sm, smax, reasons = [], [], set()
@@ -525,18 +527,27 @@ def run_gvx(args):
     a, b, v, beta = make_inputs(N_FULL)
     step = Step(torch, gvx, a, b, v, beta)
     stream = torch.cuda.current_stream()
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
     for _ in range(args.warmup):
         step(stream)
+    w1.record(stream)
     torch.cuda.synchronize()
+    warm_ms = w0.elapsed_time(w1) / max(args.warmup, 1)
     ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)]
           for _ in range(args.steps)]
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     uuid = getattr(props, "uuid", None)
     clocks = ClockSampler(("GPU-%s" % uuid) if uuid else torch.cuda.current_device())
-    clocks.start()
+    # the clocks are sampled (every 200 ms) over a load window of back-to-back untimed steps,
+    # --clock-window seconds long, that runs straight into the timed region: a timed region of a few
+    # steps alone is shorter than one sample interval
+    n_load = int(math.ceil(args.clock_window * 1e3 / max(warm_ms, 1e-3)))
+    clocks.start(settle=0.0)
+    for _ in range(n_load):
+        step(stream)
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
@@ -545,7 +556,10 @@ def run_gvx(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(settle=0.0)
+    if isinstance(clk, dict):
+        clk["window"] = ("nvidia-smi every 200 ms over %d untimed steps (%.2f s) running straight "
+                         "into the %d timed steps" % (n_load, n_load * warm_ms / 1e3, args.steps))
     ms = max_over_ranks(torch, dist, e0.elapsed_time(e1) / args.steps, "cuda")
     per_kernel = [statistics.mean(ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps))
                   for j in range(3)]
@@ -696,6 +710,9 @@ def main():
     ap.add_argument("--forms", default=",".join(FORMS),
                     help="comma-separated subset of %s" % ",".join(FORMS))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clock-window", type=float, default=LOAD_WINDOW_S,
+                    help="seconds of untimed back-to-back steps sampled for clocks before the "
+                         "timed region (0 under a profiler)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-log2", type=int, default=26,
                     help="problem size for profiling captures only (the benchmark is 2^26)")

@@ -66,7 +66,9 @@ typedef enum {
   GVX_ERR_CUDA = 8,       /* the CUDA runtime refused a launch or copy */
   GVX_ERR_TIMEOUT = 9,    /* a bounded device-side wait gave up (device-detected) */
   GVX_ERR_CAPACITY = 10,  /* a jagged output is larger than its buffer (device-detected) */
-  GVX_ERR_ARG = 11        /* any other invalid argument */
+  GVX_ERR_ARG = 11,       /* any other invalid argument */
+  GVX_ERR_BOUNDS = 12     /* an index failed an explicit check of a GVX_DEBUG_BOUNDS build
+                             (device-detected; the access was skipped) */
 } gvx_status;
 
 typedef enum { GVX_F64 = 0, GVX_F32 = 1 } gvx_dtype;

@@ -18,7 +18,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
-LIB_PATH = os.path.join(BUILD, "libgvx_%s.so" % platform.machine())
+# GVX_DEBUG_BOUNDS=1 in the environment builds and loads a separate variant with the explicit
+# index checks of the jagged kernels compiled in (csrc/common.cuh, GVX_IN_BOUNDS).
+DEBUG_BOUNDS = os.environ.get("GVX_DEBUG_BOUNDS", "") == "1"
+_VARIANT = "dbg_" if DEBUG_BOUNDS else ""
+LIB_PATH = os.path.join(BUILD, "libgvx_%s%s.so" % (_VARIANT, platform.machine()))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC, "-I" + BUILD]
@@ -70,9 +74,11 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
         return LIB_PATH
     exe = nvcc()
     srcs = _sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + "_%s.o" % platform.machine())
+    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + "_%s%s.o" % (_VARIANT, platform.machine()))
             for s in srcs]
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+    if DEBUG_BOUNDS:
+        extra.append("-DGVX_DEBUG_BOUNDS")
 
     def compile_one(pair):
         src, obj = pair

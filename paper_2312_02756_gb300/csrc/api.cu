@@ -196,6 +196,7 @@ const char *gvx_status_string(int32_t s) {
     case GVX_ERR_TIMEOUT: return "GVX_ERR_TIMEOUT: a bounded device-side wait gave up";
     case GVX_ERR_CAPACITY: return "GVX_ERR_CAPACITY: jagged output larger than its buffer";
     case GVX_ERR_ARG: return "GVX_ERR_ARG: invalid argument";
+    case GVX_ERR_BOUNDS: return "GVX_ERR_BOUNDS: an index failed a GVX_DEBUG_BOUNDS check";
     default: return "unknown gvx status";
   }
 }

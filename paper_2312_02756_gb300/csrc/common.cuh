@@ -143,4 +143,18 @@ __device__ __forceinline__ void raise_status(int32_t *word, int32_t code) {
   atomicCAS(word, 0, code);
 }
 
+// Explicit index checks at the computed indices of the jagged kernels (partners, pair slots,
+// pair gradients, particles).  In a build with GVX_DEBUG_BOUNDS defined a failed check records
+// GVX_ERR_BOUNDS and the caller skips the access; otherwise the checks compile to nothing.
+#ifdef GVX_DEBUG_BOUNDS
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, int32_t *status) {
+  if (i >= 0 && i < n) return true;
+  raise_status(status, GVX_ERR_BOUNDS);
+  return false;
+}
+#define GVX_IN_BOUNDS(i, n, status) ::gvx::in_bounds((int64_t)(i), (int64_t)(n), (status))
+#else
+#define GVX_IN_BOUNDS(i, n, status) true
+#endif
+
 }  // namespace gvx

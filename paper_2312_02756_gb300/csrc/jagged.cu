@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
       // (a) raw particles; pt and m parked in the px/py slots, the larger high word of pt and
       // |m| in s_sc
       for (int k = threadIdx.x; k < np; k += NT) {
+        if (!GVX_IN_BOUNDS(pb + k, A.n_particles, A.status)) continue;
         V4<double> v = ld4<double, LP>(A.p, pb + k);
         s_eta[k] = v.y;
         s_phi[k] = v.z;
@@ -306,6 +307,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
         int64_t i, j;
         decode_pair(q - s_pp[lo], n, i, j);
         const int ia = (int)(s_off[lo] - pb + i), ib = (int)(s_off[lo] - pb + j);
+        if (!(GVX_IN_BOUNDS(ia, np, A.status) && GVX_IN_BOUNDS(ib, np, A.status))) continue;
         double mass;
         bool done = false;
         const int sc = s_fs[ia];

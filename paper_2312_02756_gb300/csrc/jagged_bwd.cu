@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
       const int np = (int)(s_off[sbe] - pbeg);
       const int ns = sbe - sb;
       // (a) raw particles, the larger high word of pt and |m|; the events' order
-      if (k < np) {
+      if (k < np && GVX_IN_BOUNDS(pbeg + k, A.n_particles, A.status)) {
         const V4<double> x = ld4c<LP>(A.p, pbeg + k);
         s_pt[k] = x.x;
         s_eta[k] = x.y;
@@ -365,6 +365,9 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
         int64_t i, j;
         decode_pair(q0 + q - s_poff[lo], s_off[lo + 1] - s_off[lo], i, j);
         const int ia = (int)(s_off[lo] - pbeg + i), ib = (int)(s_off[lo] - pbeg + j);
+        if (!(GVX_IN_BOUNDS(ia, np, A.status) && GVX_IN_BOUNDS(ib, np, A.status) &&
+              GVX_IN_BOUNDS(q, kPC, A.status) && GVX_IN_BOUNDS(q0 + q, A.n_pairs, A.status)))
+          continue;
         const double g = __ldg(A.gpm + q0 + q);
         const uint32_t hg = ffm::dhi(g) & 0x7fffffffu;
         float4 w0 = make_float4(__uint_as_float(kSlowPair), 0.0f, 0.0f, 0.0f);
@@ -416,8 +419,10 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
           }
           const int pidx = idx;
           idx += j < li ? n - j - 2 : 1;
-          const float4 w0 = s_w0[slot0 + pidx], w1 = s_w1[slot0 + pidx];
           const int q = b0 + j;
+          if (!(GVX_IN_BOUNDS(slot0 + pidx, npq, A.status) && GVX_IN_BOUNDS(q, np, A.status)))
+            continue;
+          const float4 w0 = s_w0[slot0 + pidx], w1 = s_w1[slot0 + pidx];
           if (__float_as_uint(w0.x) == kSlowPair) {  // into this thread's own slot
             slow_pair_add(V4<double>{s_pt[p], s_eta[p], s_phi[p], s_m[p]},
                           V4<double>{s_pt[q], s_eta[q], s_phi[q], s_m[q]},

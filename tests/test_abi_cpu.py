@@ -31,8 +31,9 @@ def test_exports_every_declared_symbol(lib):
 
 def test_version_and_status_strings(lib):
     assert re.match(rb"^\d+\.\d+\.\d+$", lib.gvx_version())
-    for code in range(12):
+    for code in range(13):
         assert lib.gvx_status_string(code).startswith(b"GVX_")
+    assert lib.gvx_status_string(12).startswith(b"GVX_ERR_BOUNDS")
     assert lib.gvx_status_string(99) == b"unknown gvx status"
 
 
@@ -148,3 +149,22 @@ def test_python_coordinate_names():
     assert gvx._coords_code("ptetaphie") == 3 and gvx._coords_code("pxpypze") == 1
     with pytest.raises(ValueError):
         gvx._coords_code("xyzt")
+
+
+def test_debug_bounds_variant_compiles(tmp_path):
+    """The GVX_DEBUG_BOUNDS variant of the jagged kernels (explicit index checks that record
+    GVX_ERR_BOUNDS) compiles for sm_103a, and selecting it changes the library's file name (so
+    the two builds never overwrite each other)."""
+    import subprocess
+    import sys
+    from paper_2312_02756_gb300 import build as b
+    b.generate_tables()
+    for name in ("jagged.cu", "jagged_bwd.cu"):
+        cmd = [b.nvcc(), *b.ARCH, *b.NVCC_FLAGS, "-DGVX_DEBUG_BOUNDS", "-c",
+               os.path.join(b.CSRC, name), "-o", str(tmp_path / (name + ".o"))]
+        subprocess.run(cmd, check=True, capture_output=True)
+    code = "from paper_2312_02756_gb300 import build as b; print(b.LIB_PATH)"
+    env = dict(os.environ, GVX_DEBUG_BOUNDS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, check=True,
+                         capture_output=True, text=True).stdout.strip()
+    assert os.path.basename(out).startswith("libgvx_dbg_") and out != b.LIB_PATH
