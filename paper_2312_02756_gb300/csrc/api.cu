@@ -207,6 +207,7 @@ void gvx_testing_skip_first_tile(int32_t enable) { t_skip_first_tile = enable !=
 
 gvx_status gvx_invariant_mass(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n, int32_t dtype,
                               void *stream) {
+  GVX_NVTX_RANGE("gvx_invariant_mass");
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
   if (n == 0) return GVX_OK;
@@ -220,6 +221,7 @@ gvx_status gvx_invariant_mass(const gvx_lv *a, const gvx_lv *b, void *m, int64_t
 
 gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, int64_t n,
                                    int32_t coords, int32_t dtype, void *stream) {
+  GVX_NVTX_RANGE("gvx_invariant_mass_cart");
   if (coords == GVX_PTETAPHIM) return gvx_invariant_mass(a, b, m, n, dtype, stream);
   if (coords != GVX_PXPYPZE && coords != GVX_PXPYPZM && coords != GVX_PTETAPHIE) return GVX_ERR_ARG;
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
@@ -235,6 +237,7 @@ gvx_status gvx_invariant_mass_cart(const gvx_lv *a, const gvx_lv *b, void *m, in
 
 gvx_status gvx_to_pxpypze(const gvx_lv *v, gvx_lv *out, int64_t n, int32_t coords, int32_t dtype,
                           void *stream) {
+  GVX_NVTX_RANGE("gvx_to_pxpypze");
   if (coords != GVX_PTETAPHIM && coords != GVX_PTETAPHIE && coords != GVX_PXPYPZM) return GVX_ERR_ARG;
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
@@ -247,6 +250,7 @@ gvx_status gvx_to_pxpypze(const gvx_lv *v, gvx_lv *out, int64_t n, int32_t coord
 
 gvx_status gvx_lorentz_apply(const void *L, int64_t l_stride, const gvx_lv *v, gvx_lv *out,
                              int64_t n, int32_t dtype, void *stream) {
+  GVX_NVTX_RANGE("gvx_lorentz_apply");
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
   if (l_stride != 0 && l_stride != 1) return GVX_ERR_ARG;
@@ -262,6 +266,7 @@ gvx_status gvx_lorentz_apply(const void *L, int64_t l_stride, const gvx_lv *v, g
 gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *m_saved,
                                   const void *grad_m, gvx_lv *grad_a, gvx_lv *grad_b, int64_t n,
                                   int32_t dtype, void *stream) {
+  GVX_NVTX_RANGE("gvx_invariant_mass_bwd");
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
   if (n == 0) return GVX_OK;
@@ -279,6 +284,7 @@ gvx_status gvx_invariant_mass_bwd(const gvx_lv *a, const gvx_lv *b, const void *
 
 gvx_status gvx_boost(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride, gvx_lv *out,
                      int64_t n, int32_t dtype, void *stream) {
+  GVX_NVTX_RANGE("gvx_boost");
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
   if (beta_stride != 0 && beta_stride != 1) return GVX_ERR_ARG;
@@ -298,6 +304,7 @@ size_t gvx_boost_bwd_workspace(int64_t n, int64_t beta_stride, int32_t dtype) {
 gvx_status gvx_boost_bwd(const gvx_lv *v, const gvx_lv *beta, int64_t beta_stride,
                          const gvx_lv *grad_out, gvx_lv *grad_v, gvx_lv *grad_beta, int64_t n,
                          int32_t dtype, void *workspace, size_t workspace_bytes, void *stream) {
+  GVX_NVTX_RANGE("gvx_boost_bwd");
   if (!valid_dtype(dtype)) return GVX_ERR_DTYPE;
   if (n < 0) return GVX_ERR_SIZE;
   if (beta_stride != 0 && beta_stride != 1) return GVX_ERR_ARG;
@@ -324,6 +331,7 @@ gvx_status gvx_event_pair_masses(const gvx_lv *particles, const int64_t *offsets
                                  int64_t n_particles, int64_t *pair_offsets, double *pair_m,
                                  int64_t pair_capacity, gvx_lv *event_sum, void *workspace,
                                  size_t workspace_bytes, void *stream) {
+  GVX_NVTX_RANGE("gvx_event_pair_masses");
   JaggedCall c{particles, offsets, n_events, n_particles, pair_offsets, pair_m,
                pair_capacity, event_sum, workspace, workspace_bytes};
   GVX_TRY(check_jagged(c));
@@ -335,6 +343,7 @@ gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *off
                                      int64_t n_particles, const double *grad_pair_m,
                                      int64_t n_pairs, const gvx_lv *grad_event_sum,
                                      gvx_lv *grad_particles, void *stream) {
+  GVX_NVTX_RANGE("gvx_event_pair_masses_bwd");
   if (n_events < 0 || n_particles < 0 || n_pairs < 0) return GVX_ERR_SIZE;
   if (!offsets || !pair_offsets) return GVX_ERR_NULL;
   if ((uintptr_t)offsets % 8 || (uintptr_t)pair_offsets % 8) return GVX_ERR_ALIGN;
@@ -358,6 +367,7 @@ gvx_status gvx_event_pair_select(const gvx_lv *particles, const int64_t *offsets
                                  double eta_max, double lo, double hi, int32_t n_bins,
                                  double target, uint64_t *counts, int64_t *best_k, double *best_m,
                                  void *stream) {
+  GVX_NVTX_RANGE("gvx_event_pair_select");
   if (n_events < 0 || n_particles < 0) return GVX_ERR_SIZE;
   if (n_bins < 1 || n_bins > GVX_SELECT_MAX_BINS) return GVX_ERR_SIZE;
   if (!(hi > lo) || !(fabs(hi - lo) < INFINITY)) return GVX_ERR_ARG;
@@ -400,6 +410,7 @@ gvx_status gvx_event_pair_masses_autotune(const gvx_lv *particles, const int64_t
                                           int64_t pair_capacity, gvx_lv *event_sum,
                                           void *workspace, size_t workspace_bytes, int32_t reps,
                                           void *stream, int32_t *best_shape, float *best_ms) {
+  GVX_NVTX_RANGE("gvx_event_pair_masses_autotune");
   JaggedCall c{particles, offsets, n_events, n_particles, pair_offsets, pair_m,
                pair_capacity, event_sum, workspace, workspace_bytes};
   GVX_TRY(check_jagged(c));
@@ -446,6 +457,7 @@ gvx_status gvx_event_pair_masses_graph_create(const gvx_lv *particles, const int
                                               int64_t pair_capacity, gvx_lv *event_sum,
                                               void *workspace, size_t workspace_bytes,
                                               gvx_graph *out) {
+  GVX_NVTX_RANGE("gvx_event_pair_masses_graph_create");
   if (!out) return GVX_ERR_NULL;
   *out = nullptr;
   JaggedCall c{particles, offsets, n_events, n_particles, pair_offsets, pair_m,
@@ -479,6 +491,7 @@ gvx_status gvx_event_pair_masses_graph_create(const gvx_lv *particles, const int
 }
 
 gvx_status gvx_graph_launch(gvx_graph g, void *stream) {
+  GVX_NVTX_RANGE("gvx_graph_launch");
   if (!g) return GVX_ERR_NULL;
   return from_cuda(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
 }

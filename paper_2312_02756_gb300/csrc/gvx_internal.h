@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "gvx.h"
@@ -57,4 +58,15 @@ cudaError_t launch_event_pairs_bwd(const Lv &p, const int64_t *off, const int64_
                                    int64_t n_pairs, const Lv *gsum, const LvOut &grad,
                                    cudaStream_t s);
 
+// One NVTX range per compute call of the ABI, named after it (visible in Nsight timelines;
+// NVTX costs a pointer check when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 }  // namespace gvx
+
+#define GVX_NVTX_RANGE(name) ::gvx::NvtxRange gvx_nvtx_range_(name)

@@ -75,6 +75,7 @@ extern "C" gvx_status gvx_event_pair_masses_noalloc(const gvx_lv *particles,
                                                     int64_t n_particles, int64_t *pair_offsets,
                                                     double *pair_m, int64_t pair_capacity,
                                                     gvx_lv *event_sum, void *stream) {
+  GVX_NVTX_RANGE("gvx_event_pair_masses_noalloc");
   if (n_events < 0 || n_particles < 0 || pair_capacity < 0) return GVX_ERR_SIZE;
   if (n_events > kMaxEvents) return GVX_ERR_SIZE;  // beyond the fixed scratch
   if (!offsets || !pair_offsets) return GVX_ERR_NULL;
