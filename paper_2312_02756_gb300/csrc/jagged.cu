@@ -12,10 +12,12 @@
 //      per-particle terms once per particle (one thread each, which also finds its event's
 //      scale) -- the float-float light-cone terms of the leg (pt, Y = E + P, D = m^2 / Y, scaled
 //      by the event's power of two, bit for bit a lane of the elementwise FP64 kernel's legs) and
-//      the Cartesian components for the sums -- then, after one barrier, the event sums (one
-//      thread per event, FP64) and the pair masses (one thread per pair over the flattened pair
-//      range of the sub-batch, coalesced stores) with the elementwise kernel's pair arithmetic
-//      (mass_lc.cuh: lc_pair_m2), falling back to FP64 for pairs outside its domain;
+//      the Cartesian components for the sums, in float-float -- then, after one barrier, the
+//      event sums (one thread per event and component, float-float at the event's scale and one
+//      conversion per sum) and the pair masses (one thread per pair over the flattened pair range
+//      of the sub-batch, coalesced stores) with the elementwise kernel's pair arithmetic
+//      (mass_lc.cuh: lc_pair_m2; the output assembled by integer operations, so that a pair
+//      costs two FP64 operations), falling back to FP64 for pairs outside its domain;
 //   4. an event with more than kCP particles is handled alone, straight from global memory.
 // Tile descriptors are 64-bit words: 2 flag bits (aggregate / inclusive prefix) + 62-bit value.
 #include <cuda_runtime.h>
@@ -73,6 +75,15 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 
 __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// A float-float value kept in a double-sized shared-memory slot (its two floats' bits).
+__device__ __forceinline__ void st_ff(double *slot, const ffm::ff &x) {
+  *reinterpret_cast<float2 *>(slot) = make_float2(x.hi, x.lo);
+}
+__device__ __forceinline__ ffm::ff ld_ff(const double *slot) {
+  const float2 v = *reinterpret_cast<const float2 *>(slot);
+  return {v.x, v.y};
 }
 
 template <int NT, int LP, int LS>
@@ -266,12 +277,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
           s_pt[k] = ptf;
           s_Y[k] = L.Y;
           s_D[k] = L.D;
-          const int e2 = (int)(ew >> 20) - 1023;
-          const double sphi = (ffm::dhi(phi) >> 31) ? -1.0 : 1.0, seta = (ffm::dhi(eta) >> 31) ? -1.0 : 1.0;
-          s_px[k] = ffm::to_double(ffm::lc_mul(ptf, cs), e2);
-          s_py[k] = sphi * ffm::to_double(ffm::lc_mul(ptf, sn), e2);
-          s_pz[k] = seta * ffm::to_double(ffm::lc_mul(ptf, sh), e2);
-          s_E[k] = ffm::to_double(L.E, e2);
+          // the Cartesian components in float-float at the event's scale (summed per event in
+          // float-float and converted once per event: no FP64 operation per particle)
+          const float sphi = (ffm::dhi(phi) >> 31) ? -1.0f : 1.0f, seta = (ffm::dhi(eta) >> 31) ? -1.0f : 1.0f;
+          st_ff(s_px + k, ffm::lc_mul(ptf, cs));
+          st_ff(s_py + k, ffm::lc_scale(ffm::lc_mul(ptf, sn), sphi));
+          st_ff(s_pz + k, ffm::lc_scale(ffm::lc_mul(ptf, sh), seta));
+          st_ff(s_E + k, L.E);
         } else {  // FP64 evaluation
           double sphi, cphi;
           sincos(phi, &sphi, &cphi);
@@ -283,16 +295,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
         s_fs[k] = sc;
       }
       __syncthreads();
-      for (int e = sb + threadIdx.x; e < sbe; e += NT) {
-        double sx = 0, sy = 0, sz = 0, sE = 0;
+      // event sums: one thread per (event, component), taken by the last threads of the CTA (those
+      // with one pair fewer in the pair loop's last round); float-float terms of the fast-path
+      // particles summed in float-float at the event's scale, FP64 terms of the others in FP64
+      for (int t = NT - 1 - (int)threadIdx.x; t < 4 * (sbe - sb); t += NT) {
+        const int e = sb + (t >> 2), c = t & 3;
+        const double *col = c == 0 ? s_px : c == 1 ? s_py : c == 2 ? s_pz : s_E;
+        ffm::ff sf = {0.0f, 0.0f};
+        double sd = 0.0;
+        int sce = kNoFast;
         const int k1 = (int)(s_off[e + 1] - pb);
         for (int k = (int)(s_off[e] - pb); k < k1; k++) {
-          sx += s_px[k];
-          sy += s_py[k];
-          sz += s_pz[k];
-          sE += s_E[k];
+          if (s_fs[k] != kNoFast) {
+            sf = ffm::add_same(sf, ld_ff(col + k));
+            sce = s_fs[k];
+          } else {
+            sd += col[k];
+          }
         }
-        st4<double, LS>(A.sums, e0 + e, V4<double>{sx, sy, sz, sE});
+        const double total = sce != kNoFast ? ffm::lc_to_double(sf, (uint32_t)sce - (127u << 20)) + sd : sd;
+        double *dst = LS == GVX_SOA ? (double *)A.sums.c[c] + (e0 + e) : (double *)A.sums.c[0] + 4 * (e0 + e) + c;
+        st_s(dst, total);
       }
       const int64_t q0 = s_pp[sb], q1 = s_pp[sbe];
       bool over = false;
@@ -315,7 +338,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) event_pairs_kernel(JArgs A) {
           ffm::ff S, m2s;
           const bool oks = ffm::lc_pair_S(s_eta[ia], s_eta[ib], s_phi[ia], s_phi[ib], T, &S);
           if (ffm::lc_pair_m2(s_pt[ia], s_pt[ib], s_Y[ia], s_Y[ib], s_D[ia], s_D[ib], S, &m2s) && oks) {
-            mass = ffm::lc_mass_out(m2s, (uint32_t)sc);
+            mass = ffm::lc_mass_out_int(m2s, (uint32_t)sc);
             done = true;
           }
         }

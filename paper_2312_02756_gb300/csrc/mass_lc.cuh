@@ -183,6 +183,11 @@ GVX_HD F lc_mul(const F &x, const F &y) {
   const auto e = vfma(x.hi, y.hi, vneg(p));
   return {p, vfma(x.lo, y.hi, vfma(x.hi, y.lo, e))};
 }
+// x times a power of two or a sign (exact)
+template <class F>
+GVX_HD F lc_scale(const F &x, lane_t<F> k) {
+  return {vmul(x.hi, k), vmul(x.lo, k)};
+}
 // x + y for x, y >= 0: Fast2Sum of the leading parts ordered by max/min (exact for non-negative
 // operands; the comparisons run on the integer ALU, leaving the FMA pipes three operations).
 template <class F>
@@ -474,6 +479,36 @@ GVX_HD double lc_mass_out(ff m2s, uint32_t ew) {
                         ? hilo2d(((lm >> 3) + eoff) | (lb & 0x80000000u), lm << 29)
                         : 0.0;
   return dh + dl;
+}
+
+// A normalized ff (|lo| at most half an ulp of hi; hi normal or 0) times 2^shift -> double with
+// integer operations only (no FP64 instruction): hi exactly plus lo truncated to hi's double ulp,
+// an error below one ulp of the result.  eoff = (896 + shift) << 20 moves the float exponent
+// field to the double one.  With hi a power of two and lo of the other sign the result lies in
+// the binade below, whose ulp is half hi's: lo is then taken to one more bit.  A denormal lo
+// counts as 0.  The result must lie in the normal range of double; a zero or denormal hi gives 0.
+GVX_HD double lc_to_double_int(const ff &x, uint32_t eoff) {
+  const uint32_t hb = f2u(x.hi), lb = f2u(x.lo);
+  const uint32_t ah = hb & 0x7fffffffu, al = lb & 0x7fffffffu;
+  const uint32_t sub = (hb ^ lb) >> 31;
+  const uint32_t fix = sub & (uint32_t)((ah & 0x7fffffu) == 0u);
+  // lo in units of hi's double ulp (of the ulp below for fix): (ml 2^6) 2^-(eh - el - 23 - fix)
+  const uint32_t ml = al >= 0x800000u ? ((al & 0x7fffffu) | 0x800000u) : 0u;
+  const uint32_t sh = umin32((ah >> 23) - (al >> 23) - 23u - fix, 31u);
+  const uint32_t L = (ml << 6) >> sh;
+  const uint64_t base = ((uint64_t)((((ah >> 3) + eoff) | (hb & 0x80000000u))) << 32) |
+                        (uint64_t)(hb << 29);
+  const uint64_t r = sub ? base - L : base + L;
+  return ah >= 0x800000u ? u2d(r) : 0.0;
+}
+
+// lc_mass_out without its FP64 addition: the refined root renormalized (Fast2Sum) and assembled
+// by lc_to_double_int (truncation below one ulp of the double).  For kernels whose FP64 pipe is
+// the scarce one (the jagged pair masses).
+GVX_HD double lc_mass_out_int(ff m2s, uint32_t ew) {
+  if (m2s.hi == 0.0f) return 0.0;
+  const ff m = lc_sqrt_refined(m2s);
+  return lc_to_double_int(fast_two_sum(m.hi, m.lo), ew - (127u << 20));
 }
 
 // Returns false (and leaves *out untouched) outside the fast-path domain.

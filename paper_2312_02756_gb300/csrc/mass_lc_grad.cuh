@@ -34,11 +34,6 @@ GVX_HD F lc_sum(const F &x, const F &y) {
   const auto e = vadd(vsub(x.hi, vsub(s, bb)), vsub(y.hi, bb));
   return {s, vadd(e, vadd(x.lo, y.lo))};
 }
-// x times a power of two or a sign (exact)
-template <class F>
-GVX_HD F lc_scale(const F &x, lane_t<F> k) {
-  return {vmul(x.hi, k), vmul(x.lo, k)};
-}
 
 GVX_HD float sign_of(double d) { return (dhi(d) >> 31) ? -1.0f : 1.0f; }
 

@@ -52,7 +52,8 @@ int64_t ffh_mass_lc(const double *a, const double *b, int64_t n, double *m, uint
 
 // The jagged kernel's route for the same pairs: each particle's light-cone terms computed alone
 // (scalar) at the scale of the larger high word of (pt, |m|) over both legs and `extra` (an
-// event's other particles), then the shared pair step.  ok[i] = 0 where either route declines.
+// event's other particles), then the shared pair step and the integer-assembled output.
+// ok[i] = 0 where either route declines.
 int64_t ffh_mass_lc_event(const double *a, const double *b, const double *extra, int64_t n,
                           double *m, uint8_t *ok) {
   int64_t c = 0;
@@ -77,7 +78,7 @@ int64_t ffh_mass_lc_event(const double *a, const double *b, const double *extra,
     const bool oks = lc_pair_S(x[1], y[1], x[2], y[2], T, &S);
     bool f = lc_pair_m2(pt[0], pt[1], Y[0], Y[1], D[0], D[1], S, &m2s) && oks;
     ok[i] = f;
-    m[i] = f ? lc_mass_out(m2s, ew) : NAN;
+    m[i] = f ? lc_mass_out_int(m2s, ew) : NAN;
     c += f;
   }
   return c;
@@ -120,6 +121,12 @@ int64_t ffh_mass_grad_lc(const double *a, const double *b, const double *gm, con
     c += f;
   }
   return c;
+}
+
+// lc_to_double_int of the ff (hi[i], lo[i]) times 2^shift (mass_lc.cuh)
+void ffh_lc_to_double_int(const float *hi, const float *lo, int64_t n, int shift, double *out) {
+  for (int64_t i = 0; i < n; i++)
+    out[i] = lc_to_double_int(ff{hi[i], lo[i]}, (uint32_t)(896 + shift) << 20);
 }
 
 // lc_to_double of the ff (hi[i], lo[i]) times 2^shift (mass_lc.cuh)

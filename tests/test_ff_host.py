@@ -170,6 +170,50 @@ def test_lc_to_double_conversion(ffh):
     assert np.all(out == 0)
 
 
+def test_lc_to_double_int_conversion(ffh):
+    """The jagged pair mass's integer ff -> double conversion (mass_lc.cuh lc_to_double_int)
+    against the exact sum hi + lo (fractions): below one ulp of the result on normalized pairs of
+    every relative size and sign, in the binade below a power-of-two hi too; exactly hi where lo
+    is 0; a denormal lo counts as 0; 0 for a zero or denormal hi."""
+    from fractions import Fraction
+    g = syn.rng(81)
+    n = 20000
+    e = g.integers(-100, 100, n)
+    hi = np.ldexp(g.uniform(1, 2, n), e).astype(np.float32)
+    hi[: n // 4] = np.ldexp(1.0, e[: n // 4]).astype(np.float32)       # powers of two
+    hi *= np.where(g.random(n) < 0.5, -1, 1).astype(np.float32)
+    ulp = np.spacing(np.abs(hi)).astype(np.float64)
+    lo = (g.uniform(-0.5, 0.5, n) * ulp * np.ldexp(1.0, -g.integers(0, 40, n)))
+    lo[::7] = 0.5 * ulp[::7] * np.sign(g.uniform(-1, 1, n)[::7])      # exactly half an ulp
+    lo = lo.astype(np.float32)
+    lo[::11] = 0.0
+
+    def normalized(h, l):
+        h, l = float(h), float(l)
+        below = l * h < 0 and abs(h) == 2.0 ** np.floor(np.log2(abs(h)))
+        return abs(l) <= float(np.spacing(np.float32(abs(h) / 2 if below else abs(h)))) / 2
+    keep = np.array([normalized(h, l) for h, l in zip(hi, lo)])
+    hi, lo = np.ascontiguousarray(hi[keep]), np.ascontiguousarray(lo[keep])
+    assert len(hi) > 0.9 * n
+    for shift in (0, -300, 500):
+        out = np.empty(len(hi))
+        ffh.ffh_lc_to_double_int(hi.ctypes.data_as(ctypes.c_void_p), lo.ctypes.data_as(ctypes.c_void_p),
+                                 ctypes.c_int64(len(hi)), ctypes.c_int(shift), _p(out))
+        for h, l, o in zip(hi, lo, out):
+            exact = (Fraction(float(h)) + Fraction(float(l))) * Fraction(2) ** shift
+            # a denormal lo counts as 0: an absolute error below 2^-126 (times 2^shift)
+            bound = Fraction(float(np.spacing(abs(o)))) + Fraction(2) ** (shift - 126)
+            assert abs(Fraction(float(o)) - exact) < bound, (h, l, o)
+            if l == 0:
+                assert o == np.ldexp(float(h), shift)
+    tiny = np.array([0.0, -0.0, 1e-40], np.float32)
+    out = np.empty(3)
+    z = np.zeros(3, np.float32)
+    ffh.ffh_lc_to_double_int(tiny.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                             ctypes.c_int64(3), ctypes.c_int(0), _p(out))
+    assert np.all(out == 0)
+
+
 def _mass_grad_lc(lib, a, b, gm, ms=None):
     a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
     gm = np.ascontiguousarray(gm, dtype=np.float64)
