@@ -7,12 +7,14 @@
 // events of at most kNT particles.  Per sub-batch:
 //   (a) one thread per particle: load, cuts, and a block scan of the selection flags that gives
 //       every selected particle its place in a compacted list;
-//   (b) one thread per selected particle: the scale of its event (the largest leg exponent of
-//       the event's selected particles) and its float-float leg, stored at its compacted place;
+//   (b) one thread per selected particle: the scale of its event (the largest high word of pt
+//       and |m| over the event's selected particles) and its light-cone terms (pt, Y = E + P,
+//       D = m^2 / Y in float-float at that scale, as the jagged kernel stages them), stored at
+//       its compacted place;
 //       one thread per event: its number of selected pairs, and a block scan of those;
 //   (c) one thread per selected pair (in rounds of kRound): its packed index k in the order of
-//       gvx_event_pair_masses, its mass with the float-float pair arithmetic of the FP64 mass
-//       kernel (FP64 formulas outside its domain), its histogram slot (shared-memory integer
+//       gvx_event_pair_masses, its mass with the light-cone pair step of the FP64 mass kernels
+//       (mass_lc.cuh; FP64 formulas outside its domain), its histogram slot (shared-memory integer
 //       atomics, so the totals do not depend on the order) and its |m - target| in shared
 //       memory; then one thread per event walks its pairs of the round in order and keeps the
 //       first smallest |m - target| -- exact, and the smaller k on ties.
@@ -21,10 +23,11 @@
 // to the caller's counts.
 #include <cuda_runtime.h>
 
+#include <limits.h>
 #include <math.h>
 
 #include "common.cuh"
-#include "mass_ff.cuh"
+#include "mass_lc.cuh"
 #include "pair_index.cuh"
 #include "pair_math.cuh"
 
@@ -34,12 +37,13 @@ namespace {
 constexpr int kTE = 64;       // events per tile
 constexpr int kNT = 256;      // threads per CTA, and particles per sub-batch
 constexpr int kRound = 512;   // selected pairs evaluated per round
-constexpr int kNoFast = -100000;
-// dynamic shared memory, first part: per compacted particle a leg, eta, phi, scale and original
-// position; per sub-batch particle its leg exponent and scan value; per round of pairs |m - t|,
-// m and k
-constexpr size_t kDynFixed = (size_t)kNT * (sizeof(ffm::LegFF) + 2 * sizeof(double) + 4 * sizeof(int)) +
-                             sizeof(int) + (size_t)kRound * (2 * sizeof(double) + sizeof(long long));
+constexpr int kNoFast = INT_MIN;  // scale marker of a particle outside the float-float domain
+// dynamic shared memory, first part: per compacted particle (pt, Y) and D, eta, phi, scale and
+// original position; per sub-batch particle its scale word and scan value; per round of pairs
+// |m - t|, m and k
+constexpr size_t kDynFixed =
+    (size_t)kNT * (sizeof(float4) + sizeof(float2) + 2 * sizeof(double) + 4 * sizeof(int)) +
+    sizeof(int) + (size_t)kRound * (2 * sizeof(double) + sizeof(long long));
 
 struct SArgs {
   Lv p;
@@ -69,9 +73,9 @@ __device__ __forceinline__ int slot_of(double m, const SArgs &A) {
 }
 
 // The pair mass of two particles given by their raw values (elementwise fast path, FP64 fallback).
-__device__ __forceinline__ double pair_mass_raw(V4<double> x, V4<double> y, const ffm::TabRef &T) {
+__device__ __forceinline__ double pair_mass_raw(V4<double> x, V4<double> y, const ffm::LcTab &T) {
   double m;
-  if (!ffm::pair_mass_ff(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T, &m))
+  if (!ffm::pair_mass_lc(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T, &m))
     m = sqrt(pair_terms(make_leg(x), make_leg(y)).m2);
   return m;
 }
@@ -83,7 +87,7 @@ __device__ __forceinline__ bool better(double d, long long k, double d0, long lo
 
 // One event of more than kNT particles, by the whole block from global memory.
 template <int LP>
-__device__ void big_event_select(const SArgs &A, const ffm::TabRef &T, unsigned *s_hist,
+__device__ void big_event_select(const SArgs &A, const ffm::LcTab &T, unsigned *s_hist,
                                  int64_t pb, int64_t n, double *best_d, long long *best_k,
                                  double *best_m, double *s_rd, long long *s_rk, double *s_rm) {
   double bd = INFINITY, bm = NAN;
@@ -122,23 +126,22 @@ __device__ void big_event_select(const SArgs &A, const ffm::TabRef &T, unsigned 
 }
 
 template <int LP>
-__global__ void __launch_bounds__(kNT) pair_select_kernel(SArgs A) {
+__global__ void __launch_bounds__(kNT, 3) pair_select_kernel(SArgs A) {
   extern __shared__ double s_dyn[];
-  ffm::LegFF *s_leg = reinterpret_cast<ffm::LegFF *>(s_dyn);          // by compacted place
-  double *s_eta = reinterpret_cast<double *>(s_leg + kNT), *s_phi = s_eta + kNT;
+  float4 *s_pY = reinterpret_cast<float4 *>(s_dyn);                    // by compacted place
+  float2 *s_D = reinterpret_cast<float2 *>(s_pY + kNT);
+  double *s_eta = reinterpret_cast<double *>(s_D + kNT), *s_phi = s_eta + kNT;
   double *s_d = s_phi + kNT, *s_m = s_d + kRound;                       // by pair of the round
   long long *s_k = reinterpret_cast<long long *>(s_m + kRound);
   int *s_fs = reinterpret_cast<int *>(s_k + kRound), *s_orig = s_fs + kNT;  // by compacted place
   int *s_ex = s_orig + kNT, *s_cs = s_ex + kNT;  // by particle of the sub-batch (s_cs: kNT + 1)
   unsigned *s_hist = reinterpret_cast<unsigned *>(s_cs + kNT + 1);
-  __shared__ ffm::gvx_f4 s_exp[GVX_EXP_N];
-  __shared__ ffm::gvx_f4 s_trig[GVX_TRIG_N + 1];
   __shared__ int64_t s_off[kTE + 1], s_pp[kTE + 1], s_warp[kNT / 32];
   __shared__ double s_bd[kTE], s_bm[kTE];
   __shared__ long long s_bk[kTE];
   __shared__ int s_bad;
   for (int s = threadIdx.x; s < A.n_bins + 2; s += kNT) s_hist[s] = 0u;
-  const ffm::TabRef T = ffm::stage_tables(s_exp, s_trig);  // ends with a barrier
+  const ffm::LcTab T{ffm::kHypTab, ffm::kSinTab};  // read through L1
 
   const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kNT) pair_select_kernel(SArgs A) {
       if (k < np) {
         x = ld4<double, LP>(A.p, pb + k);
         pass = passes(x.x, x.y, A);
-        s_ex[k] = pass ? ffm::leg_exponent(x.x, x.w) : 0;
+        s_ex[k] = pass ? (int)ffm::umax32(ffm::dhi(x.x), ffm::dhi(x.w) & 0x7fffffffu) : 0;
       }
       int64_t nsel;
       const int c = (int)block_excl_scan<kNT>(pass ? 1 : 0, s_warp, &nsel);  // ends synchronised
@@ -203,14 +206,26 @@ __global__ void __launch_bounds__(kNT) pair_select_kernel(SArgs A) {
           if (s_off[mid] <= pb + k) e = mid;
           else hi = mid - 1;
         }
-        int emax = 0;
+        uint32_t wmax = 0;  // the event's scale word over its selected particles
         for (int t = (int)(s_off[e] - pb); t < (int)(s_off[e + 1] - pb); t++)
-          emax = s_ex[t] > emax ? s_ex[t] : emax;
+          wmax = ffm::umax32((uint32_t)s_ex[t], wmax);
+        // the domain of the elementwise fast path (mass_lc.cuh), at the event's scale
+        const uint32_t ew = wmax & 0x7ff00000u;
+        const uint32_t hp = ffm::dhi(x.x), hm = ffm::dhi(x.w) & 0x7fffffffu;
+        const uint32_t he = ffm::dhi(x.y) & 0x7fffffffu, hf = ffm::dhi(x.z) & 0x7fffffffu;
         int sc = kNoFast;
-        if (ffm::scale_exponent_ok(emax) && ffm::leg_in_domain(x.x, x.y, x.z, x.w, emax)) {
-          bool ok = true;
-          s_leg[c] = ffm::make_leg_ff(x.x, x.y, x.w, emax - 1023, T, &ok);
-          sc = emax - 1023;
+        if (wmax - (200u << 20) < (1700u << 20) &&
+            ffm::umin32(hp - 0x100000u, hm - 0x100000u) >= ew - (41u << 20) &&
+            ffm::umax32(hp, hm) >= 0x100000u && he < 0x40200000u && hf < 0x400C0000u) {
+          const uint32_t rb = ew - (127u << 20);
+          const ffm::ff ptf = ffm::cvt1(ffm::cvt_parts(hp, ffm::dlo(x.x), rb));
+          const ffm::ff mmf = ffm::cvt1(ffm::cvt_parts(hm, ffm::dlo(x.w), rb));
+          const ffm::ff xe = ffm::cvt1(ffm::cvt_parts_normal(ffm::umax32(he, 0x3E100000u),
+                                                             ffm::dlo(x.y), ffm::kRebaseOne));
+          const ffm::LcLeg<ffm::ff> L = ffm::lc_leg(ptf, mmf, xe, T.hyp);
+          s_pY[c] = make_float4(ptf.hi, ptf.lo, L.Y.hi, L.Y.lo);
+          s_D[c] = make_float2(L.D.hi, L.D.lo);
+          sc = (int)ew;
         }
         s_fs[c] = sc;
         s_orig[c] = k;
@@ -250,10 +265,16 @@ __global__ void __launch_bounds__(kNT) pair_select_kernel(SArgs A) {
           bool done = false;
           const int sc = s_fs[ci];
           if (sc != kNoFast && s_fs[cj] != kNoFast) {
-            bool ok = true;
-            const ffm::ff m2 = ffm::pair_m2_ff(s_leg[ci], s_leg[cj], s_eta[ci], s_eta[cj],
-                                                s_phi[ci], s_phi[cj], T, &ok);
-            done = ffm::finish_mass(m2, sc, ok, &m);
+            ffm::ff S, m2s;
+            const bool oks = ffm::lc_pair_S(s_eta[ci], s_eta[cj], s_phi[ci], s_phi[cj], T, &S);
+            const float4 a4 = s_pY[ci], b4 = s_pY[cj];
+            const float2 da = s_D[ci], db = s_D[cj];
+            if (ffm::lc_pair_m2(ffm::ff{a4.x, a4.y}, ffm::ff{b4.x, b4.y}, ffm::ff{a4.z, a4.w},
+                                ffm::ff{b4.z, b4.w}, ffm::ff{da.x, da.y}, ffm::ff{db.x, db.y}, S,
+                                &m2s) && oks) {
+              m = ffm::lc_mass_out_int(m2s, (uint32_t)sc);
+              done = true;
+            }
           }
           if (!done) m = pair_mass_raw(ld4c<LP>(A.p, pb + st + i), ld4c<LP>(A.p, pb + st + j), T);
           atomicAdd(&s_hist[slot_of(m, A)], 1u);
