@@ -633,9 +633,8 @@ def run_gvx(args):
 # The sources each timed kernel's device code is built from (the committed counters are valid
 # while these match; gvx_internal.h, which only declares the host-side launch functions, is left
 # out).
-_MASS_SRC = ("mass.cu", "mass_lc.cuh", "mass_lc_grad.cuh", "mass_ff.cuh", "mass_ff2.cuh", "mass_grad_ff2.cuh",
-             "ff2.cuh", "ff_tables.cuh", "ff.cuh", "pair_math.cuh", "common.cuh",
-             "../gen_tables.py")
+_MASS_SRC = ("mass.cu", "mass_lc.cuh", "mass_lc_grad.cuh", "ff2.cuh", "ff_tables.cuh", "ff.cuh",
+             "pair_math.cuh", "common.cuh", "../gen_tables.py")
 KERNEL_SOURCES = {
     "mass_f64_soa": _MASS_SRC,
     "mass_f64_aos": _MASS_SRC,

@@ -8,8 +8,8 @@
 // and E^2 - |p|^2), on the FP64 pipe for both storage precisions.
 //
 // gvx_to_pxpypze: PtEtaPhiM, PtEtaPhiE or PxPyPzM vectors to PxPyPzE (convert_ff.cuh in FP64, the
-// float functions in FP32).  PtEtaPhiE pair masses: in FP64 the float-float identity of
-// ptetaphie_ff.cuh; otherwise both legs converted the same way and the exact fixed-point mass of
+// float functions in FP32).  PtEtaPhiE pair masses: in FP64 the light-cone form of
+// ptetaphie_lc.cuh; otherwise both legs converted the same way and the exact fixed-point mass of
 // the converted legs.
 //
 // gvx_lorentz_apply: out = L v for a row-major 4x4 matrix L, shared or one per vector.  One
@@ -20,7 +20,7 @@
 
 #include "apply_ff.cuh"
 #include "convert_ff.cuh"
-#include "ptetaphie_ff.cuh"
+#include "ptetaphie_lc.cuh"
 #include "cart_fixed.cuh"
 #include "cart_mass.cuh"
 #include "common.cuh"
@@ -258,23 +258,23 @@ __global__ void __launch_bounds__(256) mass_ptetaphie_f32_kernel(Lv a, Lv b, flo
   for (; i < n; i += stride) st_s(m + i, pair_mass_e_f32_any(ld4<float, LA>(a, i), ld4<float, LB>(b, i)));
 }
 
-// Pair masses of PtEtaPhiE legs in FP64: the float-float identity of ptetaphie_ff.cuh; outside its
+// Pair masses of PtEtaPhiE legs in FP64: the light-cone form of ptetaphie_lc.cuh; outside its
 // domain both legs converted as above, then the exact fixed-point mass of the converted legs
 // (cart_fixed.cuh), the FP64 form outside that one's domain.  (FP32: mass_ptetaphie_f32_kernel.)
 template <typename T, int LA, int LB>
-__global__ void __launch_bounds__(256) mass_ptetaphie_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
-  __shared__ ffm::gvx_f4 s_exp[sizeof(T) == 8 ? GVX_EXP_N : 1];
-  __shared__ ffm::gvx_f4 s_trig[sizeof(T) == 8 ? GVX_TRIG_N + 1 : 1];
-  ffm::TabRef T_{nullptr, nullptr};
-  if constexpr (sizeof(T) == 8) T_ = ffm::stage_tables(s_exp, s_trig);
+__global__ void __launch_bounds__(256, 4) mass_ptetaphie_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
+  // the light-cone tables of the fast path and, for the conversion route, the older float-float
+  // tables, all read through L1
+  const ffm::LcTab L{ffm::kHypTab, ffm::kSinTab};
+  const ffm::TabRef T_{ffm::kExpTab, ffm::kTrigTab};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const V4<T> x = ld4<T, LA>(a, i), y = ld4<T, LB>(b, i);
     T ca[4], cb[4], r;
     if constexpr (sizeof(T) == 8) {
       double rf;
-      if (ffm::pair_mass_e_ff_lp(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, T_, &rf)) {
-        st_s(m + i, rf);  // the float-float identity, legs paired (ptetaphie_ff.cuh)
+      if (ffm::pair_mass_e_lc(x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, L, &rf)) {
+        st_s(m + i, rf);  // the light-cone form, legs paired (ptetaphie_lc.cuh)
         continue;
       }
       to_cart_f64(x, GVX_PTETAPHIE, T_, ca);

@@ -16,9 +16,6 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
-#include "mass_ff.cuh"
-#include "mass_ff2.cuh"
-#include "mass_grad_ff2.cuh"
 #include "mass_lc.cuh"
 #include "mass_lc_grad.cuh"
 #include "pair_math.cuh"

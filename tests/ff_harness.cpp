@@ -10,11 +10,10 @@
 #include "../paper_2312_02756_gb300/csrc/cart_fixed.cuh"
 #include "../paper_2312_02756_gb300/csrc/apply_ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/convert_ff.cuh"
-#include "../paper_2312_02756_gb300/csrc/ptetaphie_ff.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_ff2.cuh"
-#include "../paper_2312_02756_gb300/csrc/mass_grad_ff2.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_lc.cuh"
 #include "../paper_2312_02756_gb300/csrc/mass_lc_grad.cuh"
+#include "../paper_2312_02756_gb300/csrc/ptetaphie_lc.cuh"
 
 using namespace gvx::ffm;
 
@@ -119,6 +118,20 @@ int64_t ffh_mass_grad_lc(const double *a, const double *b, const double *gm, con
       gb[4 * i + k] = f ? out[4 + k] : NAN;
     }
     c += f;
+  }
+  return c;
+}
+
+// The light-cone PtEtaPhiE pair mass of the FP64 kernel (ptetaphie_lc.cuh).
+int64_t ffh_mass_e_lc(const double *a, const double *b, int64_t n, double *m, uint8_t *ok) {
+  int64_t c = 0;
+  const LcTab T{kHypTab, kSinTab};
+  for (int64_t i = 0; i < n; i++) {
+    const double *x = a + 4 * i, *y = b + 4 * i;
+    double out = NAN;
+    ok[i] = pair_mass_e_lc(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], T, &out);
+    m[i] = out;
+    c += ok[i];
   }
   return c;
 }
@@ -259,51 +272,6 @@ int64_t ffh_convert(const double *p, int64_t n, int coords, double *out, uint8_t
     double *o = out + 4 * i;
     ok[i] = coords == 2 ? pxpypzm_to_cart(x, o)
                         : ptetaphi_to_cart(x[0], x[1], x[2], x[3], coords == 3, tables(), o);
-    c += ok[i];
-  }
-  return c;
-}
-
-// The float-float PtEtaPhiE pair mass: a, b (n, 4) rows (pt, eta, phi, E); ok[i] = fast path.
-int64_t ffh_mass_e(const double *a, const double *b, int64_t n, double *m, uint8_t *ok) {
-  int64_t c = 0;
-  for (int64_t i = 0; i < n; i++) {
-    const double *x = a + 4 * i, *y = b + 4 * i;
-    double out = NAN;
-    ok[i] = pair_mass_e_ff(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], tables(), &out);
-    m[i] = out;
-    c += ok[i];
-  }
-  return c;
-}
-
-// The pair-mass gradient with its two legs prepared paired (pair_mass_grad_ff_lp).
-int64_t ffh_mass_grad_lp(const double *a, const double *b, const double *gm, int64_t n,
-                         double *ga, double *gb, uint8_t *ok) {
-  int64_t c = 0;
-  for (int64_t i = 0; i < n; i++) {
-    const double *x = a + 4 * i, *y = b + 4 * i;
-    double out[8];
-    bool f = pair_mass_grad_ff_lp(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], gm[i],
-                                  tables(), out);
-    ok[i] = f;
-    for (int k = 0; k < 4; k++) {
-      ga[4 * i + k] = f ? out[k] : NAN;
-      gb[4 * i + k] = f ? out[4 + k] : NAN;
-    }
-    c += f;
-  }
-  return c;
-}
-
-// The PtEtaPhiE pair mass with its two legs paired (pair_mass_e_ff_lp).
-int64_t ffh_mass_e_lp(const double *a, const double *b, int64_t n, double *m, uint8_t *ok) {
-  int64_t c = 0;
-  for (int64_t i = 0; i < n; i++) {
-    const double *x = a + 4 * i, *y = b + 4 * i;
-    double out = NAN;
-    ok[i] = pair_mass_e_ff_lp(x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], tables(), &out);
-    m[i] = out;
     c += ok[i];
   }
   return c;

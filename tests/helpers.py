@@ -105,8 +105,8 @@ def build_ff_harness(out_dir):
                    check=True)
     lib = ctypes.CDLL(out)
     for name in ("ffh_mass", "ffh_mass_grad", "ffh_boost", "ffh_boost_bwd", "ffh_mass_cart",
-                 "ffh_mass_cart_fixed", "ffh_apply", "ffh_convert", "ffh_mass_e", "ffh_mass_lp",
-                 "ffh_mass_e_lp", "ffh_mass_grad_lp", "ffh_mass_lc", "ffh_mass_lc_event",
-                 "ffh_mass_grad_lc"):
+                 "ffh_mass_cart_fixed", "ffh_apply", "ffh_convert", "ffh_mass_lp",
+                 "ffh_mass_lc", "ffh_mass_lc_event",
+                 "ffh_mass_grad_lc", "ffh_mass_e_lc"):
         getattr(lib, name).restype = ctypes.c_int64
     return lib
