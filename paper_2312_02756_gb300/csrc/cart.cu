@@ -7,8 +7,8 @@
 // their domain take the cancellation-free FP64 form of cart_mass.cuh (an FMA-exact cross product
 // and E^2 - |p|^2), on the FP64 pipe for both storage precisions.
 //
-// gvx_to_pxpypze: PtEtaPhiM, PtEtaPhiE or PxPyPzM vectors to PxPyPzE (convert_ff.cuh in FP64, the
-// float functions in FP32).  PtEtaPhiE pair masses: in FP64 the light-cone form of
+// gvx_to_pxpypze: PtEtaPhiM, PtEtaPhiE or PxPyPzM vectors to PxPyPzE (convert_ff.cuh in FP64 with
+// the light-cone tables, the float functions in FP32).  PtEtaPhiE pair masses: in FP64 the light-cone form of
 // ptetaphie_lc.cuh; otherwise both legs converted the same way and the exact fixed-point mass of
 // the converted legs.
 //
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256, 4) lorentz_apply_kernel(const T *__restri
 
 // One leg to PxPyPzE in FP64 (the float-float path, FP64 outside its domain); coords as in
 // gvx_coords.
-__device__ __forceinline__ void to_cart_f64(const V4<double> &x, int coords, const ffm::TabRef &T,
+__device__ __forceinline__ void to_cart_f64(const V4<double> &x, int coords, const ffm::LcTab &T,
                                             double *o) {
   if (coords == GVX_PXPYPZM) {
     const double xv[4] = {x.x, x.y, x.z, x.w};
@@ -153,7 +153,7 @@ __device__ __forceinline__ void to_cart_f64(const V4<double> &x, int coords, con
     return;
   }
   const bool e_stored = coords == GVX_PTETAPHIE;
-  if (!ffm::ptetaphi_to_cart(x.x, x.y, x.z, x.w, e_stored, T, o)) {
+  if (!ffm::ptetaphi_to_cart_lc(x.x, x.y, x.z, x.w, e_stored, T, o)) {
     double sn, cs;
     sincos(x.z, &sn, &cs);
     o[0] = x.x * cs;
@@ -182,10 +182,7 @@ __device__ __forceinline__ void to_cart_f32(const V4<float> &x, int coords, floa
 
 template <typename T, int LV, int LO, int COORDS>
 __global__ void __launch_bounds__(256) to_pxpypze_kernel(Lv v, LvOut out, int64_t n) {
-  __shared__ ffm::gvx_f4 s_exp[sizeof(T) == 8 ? GVX_EXP_N : 1];
-  __shared__ ffm::gvx_f4 s_trig[sizeof(T) == 8 ? GVX_TRIG_N + 1 : 1];
-  ffm::TabRef T_{nullptr, nullptr};
-  if constexpr (sizeof(T) == 8 && COORDS != GVX_PXPYPZM) T_ = ffm::stage_tables(s_exp, s_trig);
+  const ffm::LcTab T_{ffm::kHypTab, ffm::kSinTab};  // read through L1
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   V4<T> xn = {0, 0, 0, 0};
@@ -263,10 +260,8 @@ __global__ void __launch_bounds__(256) mass_ptetaphie_f32_kernel(Lv a, Lv b, flo
 // (cart_fixed.cuh), the FP64 form outside that one's domain.  (FP32: mass_ptetaphie_f32_kernel.)
 template <typename T, int LA, int LB>
 __global__ void __launch_bounds__(256, 4) mass_ptetaphie_kernel(Lv a, Lv b, T *__restrict__ m, int64_t n) {
-  // the light-cone tables of the fast path and, for the conversion route, the older float-float
-  // tables, all read through L1
+  // the light-cone tables of the fast path and of the conversion route, read through L1
   const ffm::LcTab L{ffm::kHypTab, ffm::kSinTab};
-  const ffm::TabRef T_{ffm::kExpTab, ffm::kTrigTab};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const V4<T> x = ld4<T, LA>(a, i), y = ld4<T, LB>(b, i);
@@ -277,8 +272,8 @@ __global__ void __launch_bounds__(256, 4) mass_ptetaphie_kernel(Lv a, Lv b, T *_
         st_s(m + i, rf);  // the light-cone form, legs paired (ptetaphie_lc.cuh)
         continue;
       }
-      to_cart_f64(x, GVX_PTETAPHIE, T_, ca);
-      to_cart_f64(y, GVX_PTETAPHIE, T_, cb);
+      to_cart_f64(x, GVX_PTETAPHIE, L, ca);
+      to_cart_f64(y, GVX_PTETAPHIE, L, cb);
     } else {
       to_cart_f32(x, GVX_PTETAPHIE, ca);
       to_cart_f32(y, GVX_PTETAPHIE, cb);

@@ -267,11 +267,12 @@ int64_t ffh_apply(const double *L, const double *v, int64_t n, double *out, uint
 // gvx_coords codes); p, out (n, 4); ok[i] = inside the fast path.
 int64_t ffh_convert(const double *p, int64_t n, int coords, double *out, uint8_t *ok) {
   int64_t c = 0;
+  const LcTab T{kHypTab, kSinTab};
   for (int64_t i = 0; i < n; i++) {
     const double *x = p + 4 * i;
     double *o = out + 4 * i;
     ok[i] = coords == 2 ? pxpypzm_to_cart(x, o)
-                        : ptetaphi_to_cart(x[0], x[1], x[2], x[3], coords == 3, tables(), o);
+                        : ptetaphi_to_cart_lc(x[0], x[1], x[2], x[3], coords == 3, T, o);
     c += ok[i];
   }
   return c;

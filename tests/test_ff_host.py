@@ -703,31 +703,50 @@ def conversion_scale(p, coords):
     return np.maximum(pm, E)
 
 
-def test_ff_conversion_to_pxpypze(ffh, orc):
-    """The float-float conversion of PtEtaPhiM, PtEtaPhiE and PxPyPzM rows to PxPyPzE against the
-    binary128 conversion: every component within 2^-44 max(|E|, |p|), on the collider-like draws
-    (light/heavy mix, |eta| up to 4, on-shell and off-shell energies) and on rows at the edges of
-    the domain (negative pt, |eta| = 16, |phi| slightly beyond pi, NaN: refused)."""
+def test_ff_conversion_pxpypzm_to_pxpypze(ffh, orc):
+    """The float-float conversion of PxPyPzM rows to PxPyPzE (E = sqrt(|p|^2 + m^2)) against the
+    binary128 conversion: every component within 2^-44 max(|E|, |p|)."""
     g = syn.rng(192)
+    c = syn.pxpypze(g, 20000)
+    c[:, 3] = g.uniform(0, 10, len(c))
+    out, ok = _convert(ffh, c, 2)
+    assert ok.all()
+    ref = orc.to_pxpypze_def(c, "pxpypzm")
+    err = np.max(np.abs(out - ref), axis=1) / conversion_scale(c, "pxpypzm")
+    assert err.max() <= 2.0 ** -44, np.log2(err.max())
+
+
+def test_lc_conversion_to_pxpypze(ffh, orc):
+    """The FP64 kernel's conversion (convert_ff.cuh ptetaphi_to_cart_lc: one paired reduction of
+    (|eta|, |phi|) on the light-cone tables) of PtEtaPhiM and PtEtaPhiE rows against the binary128
+    conversion: every component within 2^-43 max(|E|, |p|) (the bound gvx_to_pxpypze states), on
+    the collider-like draws, tiny eta (sinh(eta) ~ eta kept), azimuths up to 3.5 and rows at
+    the edges of the domain (negative pt, |eta| >= 8, NaN: refused; pt = 0 with a mass: taken)."""
+    def conv(rows, code):
+        rows = np.ascontiguousarray(rows, dtype=np.float64)
+        out, ok = np.full(rows.shape, np.nan), np.zeros(len(rows), np.uint8)
+        ffh.ffh_convert(_p(rows), ctypes.c_int64(len(rows)), code, _p(out), _p(ok))
+        return out, ok.astype(bool)
+    g = syn.rng(195)
     p = syn.ptetaphim_light_mix(g, 20000)
+    p[::7, 1] = g.choice([1e-300, 1e-20, 1e-9, -1e-5], len(p[::7]))
+    p[1::11, 2] = g.uniform(-3.5, 3.5, len(p[1::11])) * 0.9999
     e_on = orc.to_cartesian_def(p)[:, 3]
     pe = p.copy()
     pe[:, 3] = e_on * g.uniform(0.999, 1.5, len(p))
-    c = syn.pxpypze(g, 20000)
-    c[:, 3] = g.uniform(0, 10, len(c))
-    for rows, coords, code in ((p, "ptetaphim", 0), (pe, "ptetaphie", 3), (c, "pxpypzm", 2)):
-        out, ok = _convert(ffh, rows, code)
+    for rows, coords, code in ((p, "ptetaphim", 0), (pe, "ptetaphie", 3)):
+        out, ok = conv(rows, code)
         assert ok.all(), coords
         ref = orc.to_pxpypze_def(rows, coords)
         err = np.max(np.abs(out - ref), axis=1) / conversion_scale(rows, coords)
-        assert err.max() <= 2.0 ** -44, (coords, np.log2(err.max()))
-    edge = np.array([[0.0, 1.0, 0.5, 2.0], [-1.0, 1.0, 0.5, 2.0], [1.0, 16.0, 0.5, 2.0],
-                     [1.0, 1.0, 3.1415927, 2.0], [1.0, np.nan, 0.5, 2.0], [1.0, 15.9, -np.pi, 0.0]])
-    out, ok = _convert(ffh, edge, 0)
-    assert ok.tolist() == [True, False, False, False, False, True]  # pt = 0 with m > 0 is fine
+        assert err.max() <= 2.0 ** -43, (coords, np.log2(err.max()))
+    edge = np.array([[0.0, 1.0, 0.5, 2.0], [-1.0, 1.0, 0.5, 2.0], [1.0, 8.0, 0.5, 2.0],
+                     [1.0, 1.0, 3.1415927, 2.0], [1.0, np.nan, 0.5, 2.0], [1.0, 7.9, -np.pi, 0.0]])
+    out, ok = conv(edge, 0)
+    assert ok.tolist() == [True, False, False, True, False, True]
     ref = orc.to_pxpypze_def(edge[ok], "ptetaphim")
-    assert np.all(np.abs(out[ok] - ref) <= 2.0 ** -44 * conversion_scale(edge[ok], "ptetaphim")[:, None])
-    _, ok = _convert(ffh, edge, 3)
+    assert np.all(np.abs(out[ok] - ref) <= 2.0 ** -43 * conversion_scale(edge[ok], "ptetaphim")[:, None])
+    _, ok = conv(edge, 3)
     assert not ok[0]  # E stored: a zero pt leaves no scale
 
 
