@@ -10,7 +10,8 @@
 // for |beta| <= 0.99), so t, the one step whose rounding C amplifies, stays in FP64, as do
 // E' = gamma t (exact for beta = 0) and the multiply-adds p_k + f beta_k.  1 - b2 is exact in
 // 64-bit fixed point; s, gamma, w, k and f are formed in ff on the FP32 pipe, and gamma and f
-// return to double with integer operations.  That leaves seven FP64 operations per vector
+// return to double with integer operations (lc_to_double_int of mass_lc.cuh: truncation below
+// one ulp).  That leaves seven FP64 operations per vector
 // (t 3, E' 1, p' 3); the normwise error vs E' stays below a few 2^-53 C plus a few 2^-47.
 //
 // Domain (anything else returns false and the caller uses the FP64 evaluation): 1 - b2 >= 2^-16
@@ -20,6 +21,7 @@
 #pragma once
 
 #include "ff.cuh"
+#include "mass_lc.cuh"
 
 namespace gvx {
 namespace ffm {
@@ -39,7 +41,7 @@ GVX_HD BetaFF beta_ff(double bx, double by, double bz) {
   const ff g = recip(s);
   B.w = recip(add_same(make(1.0f), s));
   B.k = mul(g, B.w);
-  B.g = ok ? to_double_int(g, 0) : 0.0;
+  B.g = ok ? lc_to_double_int(renorm(g), 896u << 20) : 0.0;
   B.ok = ok;
   return B;
 }
@@ -59,7 +61,7 @@ GVX_HD bool boost_ff(const BetaFF &B, double bx, double by, double bz, double px
   const int s = e - 1023;  // components scaled into magnitudes below 2
   const double t = fma(bx, px, fma(by, py, fma(bz, pz, E)));
   const ff f = add(mul(B.k, from_double_ranged(t, s)), mul(B.w, from_double_ranged(E, s)));
-  const double fd = to_double_int(f, s);
+  const double fd = lc_to_double_int(f, (uint32_t)(896 + s) << 20);
   out[0] = fma(fd, bx, px);
   out[1] = fma(fd, by, py);
   out[2] = fma(fd, bz, pz);
@@ -124,17 +126,27 @@ GVX_HD bool boost_bwd_ff(const BetaBwdFF &B, double bx, double by, double bz, co
   const ff BP = add(T, neg(En));
   const ff TG = from_double_ranged(tg, sq), GE = from_double_ranged(q[3], sq);
   const ff GB = add(TG, neg(GE));
-  const double f = to_double_int(add(mul(B.k, T), mul(B.w, En)), sv);
+  const uint32_t rv = (uint32_t)(896 + sv) << 20, rq = (uint32_t)(896 + sq) << 20;
+  const double f = lc_to_double_int(add(mul(B.k, T), mul(B.w, En)), rv);
   const ff FQ = add(mul(B.k, TG), mul(B.w, GE));
   const ff A = mul(B.g3, add(mul(GB, add(T, mul(B.kpm1, BP))), mul(GE, T)));
-  const double a = to_double_int(renorm(A), sv + sq);
-  const double bq = to_double_int(add(mul(B.k, GB), mul(B.gf, GE)), sq);
+  const double a = lc_to_double_int(renorm(A), (uint32_t)(896 + sv + sq) << 20);
+  const double bq = lc_to_double_int(add(mul(B.k, GB), mul(B.gf, GE)), rq);
   // grad_v = L grad_out in ff (its terms cancel by at most the condition of L, gamma (1 + |beta|)):
   // q_k + fq beta_k and gamma tg, returned to double by integer operations
-  gv[0] = to_double_int(renorm(add(from_double_ranged(q[0], sq), mul(FQ, from_double_ranged(bx, 0)))), sq);
-  gv[1] = to_double_int(renorm(add(from_double_ranged(q[1], sq), mul(FQ, from_double_ranged(by, 0)))), sq);
-  gv[2] = to_double_int(renorm(add(from_double_ranged(q[2], sq), mul(FQ, from_double_ranged(bz, 0)))), sq);
-  gv[3] = to_double_int(renorm(mul(B.gf, TG)), sq);
+  {
+    // 47-bit inputs suffice here (the terms cancel by at most the condition of L): the light-cone
+    // conversions of q_k and beta_k, signs applied on the bits; outputs assembled by integer
+    // operations
+    const auto cv = [](double d, uint32_t rb) {
+      const ff m = cvt1(cvt_parts(dhi(d) & 0x7fffffffu, dlo(d), rb));
+      return (dhi(d) >> 31) ? ff{-m.hi, -m.lo} : m;
+    };
+    gv[0] = lc_to_double_int(renorm(add(cv(q[0], rq), mul(FQ, cv(bx, kRebaseOne)))), rq);
+    gv[1] = lc_to_double_int(renorm(add(cv(q[1], rq), mul(FQ, cv(by, kRebaseOne)))), rq);
+    gv[2] = lc_to_double_int(renorm(add(cv(q[2], rq), mul(FQ, cv(bz, kRebaseOne)))), rq);
+    gv[3] = lc_to_double_int(renorm(mul(B.gf, TG)), rq);
+  }
   gbeta[0] = fma(a, bx, fma(bq, p[0], f * q[0]));
   gbeta[1] = fma(a, by, fma(bq, p[1], f * q[1]));
   gbeta[2] = fma(a, bz, fma(bq, p[2], f * q[2]));
