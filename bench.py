@@ -638,7 +638,8 @@ _MASS_SRC = ("mass.cu", "mass_lc.cuh", "mass_lc_grad.cuh", "ff2.cuh", "ff_tables
 KERNEL_SOURCES = {
     "mass_f64_soa": _MASS_SRC,
     "mass_f64_aos": _MASS_SRC,
-    "boost_f64_soa": ("boost.cu", "boost_ff.cuh", "ff.cuh", "common.cuh"),
+    "boost_f64_soa": ("boost.cu", "boost_ff.cuh", "mass_lc.cuh", "ff2.cuh", "ff_tables.cuh", "ff.cuh",
+                      "common.cuh", "../gen_tables.py"),
 }
 
 
