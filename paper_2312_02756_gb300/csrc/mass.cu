@@ -87,6 +87,66 @@ __global__ void __launch_bounds__(128, 8) mass_f64_kernel(Lv a, Lv b, double *__
   }
 }
 
+// cosh and sinh of x in FP32 from one exponential: (e + 1/e)/2 and (e - 1/e)/2, e = exp(|x|);
+// below |x| = 1/4 sinh from its Taylor series to x^7 (the difference would lose relative digits).
+__device__ __forceinline__ void hyp_pair_f32(float x, float *ch, float *sh) {
+  const float ax = fabsf(x), e = expf(ax), r = 1.0f / e;
+  *ch = 0.5f * (e + r);
+  const float x2 = ax * ax;
+  const float taylor = ax * fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 5040.0f, 1.0f / 120.0f), 1.0f / 6.0f), 1.0f);
+  *sh = copysignf(ax < 0.25f ? taylor : 0.5f * (e - r), x);
+}
+
+// The FP32 pair-mass adjoint: the formulas of pair_mass_grad (pair_math.cuh) with each leg's
+// cosh and sinh from one exponential, the half-angle terms of d_eta from another, sin and cos of
+// the azimuthal half-angle from one sincosf, and the forward's mass where it is given.
+__device__ __forceinline__ void pair_mass_grad_f32(const V4<float> &x, const V4<float> &y, float g,
+                                                   bool has_ms, float ms, V4<float> &g1,
+                                                   V4<float> &g2) {
+  g1 = {0.0f, 0.0f, 0.0f, 0.0f};
+  g2 = {0.0f, 0.0f, 0.0f, 0.0f};
+  float ch1, sh1, ch2, sh2, ce, se, sp, cp, sgn;
+  hyp_pair_f32(x.y, &ch1, &sh1);
+  hyp_pair_f32(y.y, &ch2, &sh2);
+  hyp_pair_f32(0.5f * (x.y - y.y), &ce, &se);
+  sincosf(half_dphi(x.z, y.z, &sgn), &sp, &cp);
+  const float q1 = x.w * x.w, q2 = y.w * y.w;
+  const float P1 = x.x * ch1, P2 = y.x * ch2;
+  const float E1 = sqrtf(fmaf(P1, P1, q1)), E2 = sqrtf(fmaf(P2, P2, q2));
+  const float S = fmaf(se, se, sp * sp);
+  float m;
+  if (has_ms) {
+    m = ms;
+  } else {
+    const float den = fmaf(E1, E2, P1 * P2);
+    const float num = fmaf(q1, P2 * P2, fmaf(q2, P1 * P1, q1 * q2));
+    const float tm = den > 0.0f ? 2.0f * num / den : 0.0f;
+    m = sqrtf(q1 + q2 + tm + 4.0f * x.x * y.x * S);
+  }
+  if (!(m > 0.0f)) return;
+  const float scale = g / (2.0f * m);
+  const float sdeta = 2.0f * se * ce, sdphi = sgn * 2.0f * sp * cp;
+  // X_s = P_s E_o / E_s - P_o without cancellation (pair_math.cuh leg_grad)
+  const auto leg = [&](float pts, float ms_, float Ps, float Es, float qs, float chs, float shs,
+                       float pto, float Po, float Eo, float qo, float sde, float sdp) {
+    float X;
+    if (Es > 0.0f) {
+      const float den = (Ps * Eo + Po * Es) * Es;
+      X = den > 0.0f ? (Ps * Ps * qo - Po * Po * qs) / den : 0.0f;
+    } else {
+      X = (Eo + Po) > 0.0f ? qo / (Eo + Po) : 0.0f;
+    }
+    V4<float> r;
+    r.x = scale * (4.0f * pto * S + 2.0f * chs * X);
+    r.y = scale * (2.0f * pts * (pto * sde + shs * X));
+    r.z = scale * (2.0f * pts * pto * sdp);
+    r.w = Es > 0.0f ? scale * (2.0f * ms_ * (Es + Eo) / Es) : 0.0f;
+    return r;
+  };
+  g1 = leg(x.x, x.w, P1, E1, q1, ch1, sh1, y.x, P2, E2, q2, sdeta, sdphi);
+  g2 = leg(y.x, y.w, P2, E2, q2, ch2, sh2, x.x, P1, E1, q1, -sdeta, -sdphi);
+}
+
 // Where the forward's saved mass ms[i] is 0 the gradient is 0 (the convention of the adjoint),
 // so that forward and adjoint agree even where a recomputed mass would round away from 0.
 template <typename T, int LA, int LB, int LGA, int LGB>
@@ -96,7 +156,10 @@ __global__ void __launch_bounds__(256) mass_bwd_kernel(Lv a, Lv b, const T *__re
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     V4<T> g1 = {0, 0, 0, 0}, g2 = {0, 0, 0, 0};
-    if (!ms || ld_s(ms + i) != (T)0) pair_mass_grad(ld4<T, LA>(a, i), ld4<T, LB>(b, i), ld_s(gm + i), g1, g2);
+    static_assert(sizeof(T) == 4, "the FP64 adjoint is mass_bwd_f64_kernel");
+    const float msv = ms ? ld_s(ms + i) : 1.0f;
+    if (msv != 0.0f)
+      pair_mass_grad_f32(ld4<T, LA>(a, i), ld4<T, LB>(b, i), ld_s(gm + i), ms != nullptr, msv, g1, g2);
     st4<T, LGA>(ga, i, g1);
     st4<T, LGB>(gb, i, g2);
   }
