@@ -296,9 +296,11 @@ def forms(torch, gvx, steps, warmup, fp64_pairs_per_s, fp64_mass_ms, which=FORMS
         gsum = torch.as_tensor(syn.upstream(g, (n_ev, 4))).cuda()
         gp = torch.empty_like(p)
         lp, lgs, lgp = Step._lv(p, 1, 4), Step._lv(gsum, 1, 4), Step._lv(gp, 1, 4)
+        ws_b = lib.gvx_event_pair_masses_bwd_workspace(n_ev)
+        ws = torch.empty(ws_b, dtype=torch.uint8, device="cuda")
         jbwd = lambda: _lib.check(lib.gvx_event_pair_masses_bwd(
             r(lp), P(doff.data_ptr()), P(graph.pair_offsets.data_ptr()), n_ev, int(off[-1]),
-            P(gpm.data_ptr()), n_pairs, r(lgs), r(lgp), s))
+            P(gpm.data_ptr()), n_pairs, r(lgs), r(lgp), P(ws.data_ptr()), ws_b, s))
         t_jb = time_loop(torch, jbwd, stream, steps, warmup)
         status_b = gvx.device_status()
         # the fused analysis step on the same events: cuts pt >= 20, |eta| <= 2.5, 200 bins of

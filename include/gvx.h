@@ -234,16 +234,28 @@ gvx_status gvx_event_pair_masses(const gvx_lv *particles, const int64_t *offsets
  *   grad_pair_m:     n_pairs upstream gradients, packed like pair_m (n_pairs = pair_offsets[n_events]).
  *   grad_event_sum:  n_events PxPyPzE upstream gradients (SoA or AoS), or NULL for zero.
  *   grad_particles:  out, n_particles PtEtaPhiM-shaped gradients (SoA or AoS).
- * Deterministic (no atomics; a fixed summation order per particle).  Offsets or pair offsets that
- * do not match the event sizes or n_pairs are detected on the device: GVX_ERR_OFFSETS is recorded
- * in the device status word and the gradients of the affected events are not written.  All
- * pointers are device (or GPU-addressable host) memory; one launch; nothing is allocated.
+ *   workspace:       gvx_event_pair_masses_bwd_workspace(n_events) bytes of device memory,
+ *                    256-byte aligned (GVX_ERR_WORKSPACE when missing or smaller, GVX_ERR_ALIGN
+ *                    when misaligned; not needed when n_events or n_particles is 0).  Its
+ *                    contents are scratch; calls in flight at once need separate workspaces.
+ * Deterministic (a fixed summation order per particle).  Offsets or pair offsets that do not
+ * match the event sizes or n_pairs are detected on the device: GVX_ERR_OFFSETS is recorded in the
+ * device status word and the gradients of the affected events are not written.  All pointers
+ * are device (or GPU-addressable host) memory; nothing is allocated.  One 8-byte memset and two
+ * launches: the staged float-float pass, which lists in the workspace the tiles of 14 events
+ * that met a rare FP64 case (a pair or event-sum part outside the float-float domain, an event
+ * of more than 128 particles or 640 pairs), then a pass over the listed tiles alone that adds
+ * those contributions (with none listed it returns at once).
  */
 gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *offsets,
                                      const int64_t *pair_offsets, int64_t n_events,
                                      int64_t n_particles, const double *grad_pair_m,
                                      int64_t n_pairs, const gvx_lv *grad_event_sum,
-                                     gvx_lv *grad_particles, void *stream);
+                                     gvx_lv *grad_particles, void *workspace,
+                                     size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace gvx_event_pair_masses_bwd needs for n_events events (0 for none). */
+size_t gvx_event_pair_masses_bwd_workspace(int64_t n_events);
 
 /*
  * Fused per-event analysis step (FP64): particle selection, a histogram of the pair masses of

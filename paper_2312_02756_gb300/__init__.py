@@ -329,11 +329,12 @@ class _EventPairMasses(torch.autograd.Function):
         if g_sums is not None:
             g_sums = g_sums.to(torch.float64).contiguous()
             gs_arg = ctypes.byref(_lv(g_sums, ls, 4))
+        ws, ws_bytes = _bwd_workspace(n_events, particles.device)
         st = load_library().gvx_event_pair_masses_bwd(
             ctypes.byref(_lv(particles, lp, 4)), ctypes.c_void_p(offsets.data_ptr()),
             ctypes.c_void_p(pair_off.data_ptr()), n_events, _count(particles, lp),
             ctypes.c_void_p(g_pm.data_ptr()), n_pairs, gs_arg, ctypes.byref(_lv(gp, lp, 4)),
-            _stream(stream))
+            ctypes.c_void_p(ws.data_ptr()), ws_bytes, _stream(stream))
         _lib.check(st, "gvx_event_pair_masses_bwd")
         return gp, None, None, None, None, None
 
@@ -348,6 +349,13 @@ def event_pair_masses(particles: torch.Tensor, offsets: torch.Tensor, n_pairs: i
     (hand-written adjoint kernel, gvx_event_pair_masses_bwd).  Device-detected problems
     (malformed offsets, capacity) are reported by ``check_device_status``."""
     return _EventPairMasses.apply(particles, offsets, int(n_pairs), layout, sums_layout, stream)
+
+
+def _bwd_workspace(n_events, device):
+    """Scratch of gvx_event_pair_masses_bwd (the list of tiles for its FP64 pass): a fresh
+    allocation per call (the caching allocator's blocks are 512-byte aligned)."""
+    ws_bytes = load_library().gvx_event_pair_masses_bwd_workspace(n_events)
+    return torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=device), ws_bytes
 
 
 def event_pair_masses_bwd(particles, offsets, pair_offsets, grad_pair_m, grad_sums=None,
@@ -365,11 +373,12 @@ def event_pair_masses_bwd(particles, offsets, pair_offsets, grad_pair_m, grad_su
     if grad_sums is not None:
         ls = _layout_of(grad_sums, 4, sums_layout)
         gs_arg = ctypes.byref(_lv(grad_sums, ls, 4))
+    ws, ws_bytes = _bwd_workspace(offsets.numel() - 1, particles.device)
     st = load_library().gvx_event_pair_masses_bwd(
         ctypes.byref(_lv(particles, lp, 4)), ctypes.c_void_p(offsets.data_ptr()),
         ctypes.c_void_p(pair_offsets.data_ptr()), offsets.numel() - 1, n,
         ctypes.c_void_p(grad_pair_m.data_ptr()), grad_pair_m.numel(), gs_arg,
-        ctypes.byref(_lv(gp, lg, 4)), _stream(stream))
+        ctypes.byref(_lv(gp, lg, 4)), ctypes.c_void_p(ws.data_ptr()), ws_bytes, _stream(stream))
     _lib.check(st, "gvx_event_pair_masses_bwd")
     return gp
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "gvx_event_pair_masses_autotune", "gvx_event_pair_masses_graph_create",
     "gvx_graph_launch", "gvx_graph_destroy", "gvx_device_status",
     "gvx_testing_skip_first_tile", "gvx_event_pair_masses_noalloc",
-    "gvx_event_pair_masses_bwd", "gvx_event_pair_select",
+    "gvx_event_pair_masses_bwd_workspace", "gvx_event_pair_masses_bwd", "gvx_event_pair_select",
     "gvx_invariant_mass_cart", "gvx_lorentz_apply", "gvx_to_pxpypze",
 )
 
@@ -85,7 +85,8 @@ def _sigs(lib):
         "gvx_device_status": ([P, ctypes.POINTER(I32)], S),
         "gvx_testing_skip_first_tile": ([I32], None),
         "gvx_event_pair_masses_noalloc": ([LVP, P, I64, I64, P, P, I64, LVP, P], S),
-        "gvx_event_pair_masses_bwd": ([LVP, P, P, I64, I64, P, I64, LVP, LVP, P], S),
+        "gvx_event_pair_masses_bwd_workspace": ([I64], SZ),
+        "gvx_event_pair_masses_bwd": ([LVP, P, P, I64, I64, P, I64, LVP, LVP, P, SZ, P], S),
         "gvx_invariant_mass_cart": ([LVP, LVP, P, I64, I32, I32, P], S),
         "gvx_lorentz_apply": ([P, I64, LVP, LVP, I64, I32, P], S),
         "gvx_to_pxpypze": ([LVP, LVP, I64, I32, I32, P], S),

@@ -338,16 +338,24 @@ gvx_status gvx_event_pair_masses(const gvx_lv *particles, const int64_t *offsets
   return enqueue_jagged(c, shape_for(n_events), (cudaStream_t)stream);
 }
 
+size_t gvx_event_pair_masses_bwd_workspace(int64_t n_events) {
+  return n_events <= 0 ? 0 : gvx::event_pairs_bwd_workspace(n_events);
+}
+
 gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *offsets,
                                      const int64_t *pair_offsets, int64_t n_events,
                                      int64_t n_particles, const double *grad_pair_m,
                                      int64_t n_pairs, const gvx_lv *grad_event_sum,
-                                     gvx_lv *grad_particles, void *stream) {
+                                     gvx_lv *grad_particles, void *workspace,
+                                     size_t workspace_bytes, void *stream) {
   GVX_NVTX_RANGE("gvx_event_pair_masses_bwd");
   if (n_events < 0 || n_particles < 0 || n_pairs < 0) return GVX_ERR_SIZE;
   if (!offsets || !pair_offsets) return GVX_ERR_NULL;
   if ((uintptr_t)offsets % 8 || (uintptr_t)pair_offsets % 8) return GVX_ERR_ALIGN;
   if (n_events == 0 || n_particles == 0) return GVX_OK;  // no particle has a gradient
+  if (!workspace || workspace_bytes < gvx::event_pairs_bwd_workspace(n_events))
+    return GVX_ERR_WORKSPACE;
+  if ((uintptr_t)workspace % 256) return GVX_ERR_ALIGN;
   GVX_TRY(check_lv(particles, GVX_F64, 4));
   GVX_TRY(check_lv(grad_particles, GVX_F64, 4));
   if (grad_event_sum) GVX_TRY(check_lv(grad_event_sum, GVX_F64, 4));
@@ -358,7 +366,7 @@ gvx_status gvx_event_pair_masses_bwd(const gvx_lv *particles, const int64_t *off
   return from_cuda(gvx::launch_event_pairs_bwd(gvx::as_in(*particles), offsets, pair_offsets,
                                                n_events, n_particles, grad_pair_m, n_pairs,
                                                grad_event_sum ? &gs : nullptr,
-                                               gvx::as_out(*grad_particles),
+                                               gvx::as_out(*grad_particles), workspace,
                                                (cudaStream_t)stream));
 }
 

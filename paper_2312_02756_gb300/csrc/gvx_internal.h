@@ -53,9 +53,10 @@ cudaError_t launch_pair_select(const Lv &p, const int64_t *off, int64_t n_events
                                int64_t n_particles, double pt_min, double eta_max, double lo,
                                double hi, int n_bins, double target, uint64_t *counts,
                                int64_t *best_k, double *best_m, cudaStream_t s);
+size_t event_pairs_bwd_workspace(int64_t n_events);
 cudaError_t launch_event_pairs_bwd(const Lv &p, const int64_t *off, const int64_t *pair_off,
                                    int64_t n_events, int64_t n_particles, const double *gpm,
-                                   int64_t n_pairs, const Lv *gsum, const LvOut &grad,
+                                   int64_t n_pairs, const Lv *gsum, const LvOut &grad, void *ws,
                                    cudaStream_t s);
 
 // One NVTX range per compute call of the ABI, named after it (visible in Nsight timelines;

@@ -30,11 +30,17 @@
 // c, c S and c (2 sinh d_eta, 2 sin d_phi); (d) one thread per particle walks its partners in a
 // fixed order, adding the seven sums from the pair slots and the partners' staged terms, and
 // assembles and converts its gradient -- so the result does not depend on scheduling and no
-// atomics are needed.  Pairs outside the float-float domain (either particle outside the
+// atomic operation touches it.  Pairs outside the float-float domain (either particle outside the
 // forward's domain at the event scale, |d_phi|/2 within 2^-7 of pi, a scaled m^2 below 2^-80,
-// |gm| outside [2^-60, 2^20]) are marked in (c) and take the FP64 formulas in (d), summed in FP64
-// in the thread's own slot.  An event with more than kNT particles or kPC pairs is handled alone,
-// straight from global memory, with the elementwise kernels' pair adjoint.  The pair offsets are
+// |gm| outside [2^-60, 2^20]) are marked in (c) and take the FP64 formulas; so does an event-sum
+// part whose gs lies outside the float-float range, and an event with more than kNT particles or
+// kPC pairs is handled alone, straight from global memory, with the elementwise kernels' pair
+// adjoint.  These rare FP64 paths run in a second launch of the same kernel (FIX = true): the
+// first launch contains no function call (a call site costs the staged path ~12% in spills at
+// 96 registers), skips them and appends each tile that met one to a list in the caller's
+// workspace; the second launch takes only the listed tiles (none: it returns at once), repeats
+// their staging and classification and adds, per particle, the FP64 contributions to the
+// gradient the first launch wrote (big events it writes whole).  The pair offsets are
 // those the forward call wrote; each tile checks them (and the offsets) against the event sizes
 // and the pair count before it reads any pair gradient, and records GVX_ERR_OFFSETS for a tile
 // that does not match (its particles' gradients are then not written).
@@ -55,6 +61,9 @@ constexpr int kNT = 128;   // threads per CTA, and particles staged per sub-batc
 constexpr int kPC = 640;   // pairs staged per sub-batch (the events of a sub-batch average ~450)
 constexpr int kNoFast = INT_MIN;  // scale marker of a particle outside the float-float domain
 constexpr uint32_t kSlowPair = 0x7fc00000u;  // the bits of c.hi marking a pair for FP64
+// Workspace: the count of listed tiles (zeroed by the call before the first launch), then from
+// byte kWsList the list of tiles (int64) the FIX launch takes, at most one entry per tile.
+constexpr size_t kWsList = 256;
 // per staged particle: pt, eta, phi, m and the FP64 accumulator (doubles); (pt, Y), (D, E),
 // (cosh, sinh) (float4) and m (float2); the larger high word of pt and |m|, and its event's scale
 // field or kNoFast (ints); per staged pair: (c, c S) and (c 2 sinh d_eta, c 2 sin d_phi) (float4)
@@ -72,6 +81,8 @@ struct BArgs {
   bool has_gsum;
   LvOut grad;
   int32_t *status;
+  unsigned long long *fix_count;  // workspace: tiles listed for the FIX launch
+  int64_t *fix_tiles;             // workspace: their indices
 };
 
 // J^T gs in FP64 for one particle: gs = (gx, gy, gz, gE) against the rows
@@ -208,8 +219,9 @@ __device__ __forceinline__ float4 pack4(const ffm::ff &a, const ffm::ff &b) {
   return make_float4(a.hi, a.lo, b.hi, b.lo);
 }
 
-template <int LP, int LS, int LG>
+template <int LP, int LS, int LG, bool FIX>
 __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
+  bool fix = false;  // FIX == false: this thread met an FP64 path in the current tile
   using ffm::ff;
   using ffm::ff2;
   extern __shared__ double s_dyn[];
@@ -227,8 +239,15 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
   __shared__ int s_bad;
   const ffm::LcTab T{ffm::kHypTab, ffm::kSinTab};
   const int64_t n_tiles = (A.n_events + kTE - 1) / kTE;
+  // the first launch: every tile; the FIX launch: the listed ones (written by the first launch)
+  const int64_t n_iter = FIX ? (int64_t)*(volatile unsigned long long *)A.fix_count : n_tiles;
   const int k = threadIdx.x;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (int64_t it = blockIdx.x; it < n_iter; it += gridDim.x) {
+    int64_t tile = it;
+    if constexpr (FIX) {
+      tile = A.fix_tiles[it];
+      if (!GVX_IN_BOUNDS(tile, n_tiles, A.status)) continue;
+    }
     const int64_t e0 = tile * kTE;
     const int ne = (int)(A.n_events - e0 < kTE ? A.n_events - e0 : kTE);
     __syncthreads();  // the previous tile is done with the shared arrays
@@ -259,7 +278,8 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
                         s_poff[threadIdx.x + 1] - s_poff[sb] <= kPC;
       const int sbe = sb + __syncthreads_count(fits);
       if (sbe == sb) {  // one event larger than a sub-batch (particles or pairs)
-        big_event<LP, LS, LG>(A, T, e0 + sb, pbeg, s_off[sb + 1] - pbeg, s_poff[sb]);
+        if constexpr (FIX) big_event<LP, LS, LG>(A, T, e0 + sb, pbeg, s_off[sb + 1] - pbeg, s_poff[sb]);
+        else fix = true;
         sb++;
         __syncthreads();
         continue;
@@ -345,7 +365,11 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
             done = sum_part_lc(ff{pY.x, pY.y}, ff{DE.z, DE.w}, ff{mm2.x, mm2.y}, ff{cs.x, cs.y},
                                ff{cs.z, cs.w}, eta, phi, m, (uint32_t)sc - (127u << 20), gsv, T, &sp);
           }
-          if (!done) sp = sum_part(xp, gsv);
+          if constexpr (FIX) {  // only what the first launch left out
+            sp = done ? V4<double>{0.0, 0.0, 0.0, 0.0} : sum_part(xp, gsv);
+          } else if (!done) {
+            fix = true;
+          }
         }
         s_acc[p] = make_double4(sp.x, sp.y, sp.z, sp.w);
       }
@@ -423,10 +447,15 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
           if (!(GVX_IN_BOUNDS(slot0 + pidx, npq, A.status) && GVX_IN_BOUNDS(q, np, A.status)))
             continue;
           const float4 w0 = s_w0[slot0 + pidx], w1 = s_w1[slot0 + pidx];
-          if (__float_as_uint(w0.x) == kSlowPair) {  // into this thread's own slot
-            slow_pair_add(V4<double>{s_pt[p], s_eta[p], s_phi[p], s_m[p]},
-                          V4<double>{s_pt[q], s_eta[q], s_phi[q], s_m[q]},
-                          __ldg(A.gpm + s_poff[e] + pidx), s_acc + p);
+          if constexpr (FIX) {  // the marked pairs only, into this thread's own slot
+            if (__float_as_uint(w0.x) == kSlowPair)
+              slow_pair_add(V4<double>{s_pt[p], s_eta[p], s_phi[p], s_m[p]},
+                            V4<double>{s_pt[q], s_eta[q], s_phi[q], s_m[q]},
+                            __ldg(A.gpm + s_poff[e] + pidx), s_acc + p);
+            continue;
+          }
+          if (__float_as_uint(w0.x) == kSlowPair) {  // left to the FIX launch
+            fix = true;
             continue;
           }
           const float sg = j > li ? 1.0f : -1.0f;  // the slot's sd terms are for (min, max)
@@ -443,7 +472,14 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
         // the pair part from the accumulators, plus the FP64 slot (event-sum part, slow pairs)
         const double4 a = s_acc[p];
         double out[4] = {a.x, a.y, a.z, a.w};
-        if (sc != kNoFast) {
+        if constexpr (FIX) {
+          if (a.x != 0.0 || a.y != 0.0 || a.z != 0.0 || a.w != 0.0) {
+            // the first launch's value (plain coherent loads: this launch writes the array)
+            const V4<double> w = ld4<double, LG>(Lv{{A.grad.c[0], A.grad.c[1], A.grad.c[2], A.grad.c[3]},
+                                                    A.grad.layout}, pbeg + p);
+            st4<double, LG>(A.grad, pbeg + p, V4<double>{w.x + out[0], w.y + out[1], w.z + out[2], w.w + out[3]});
+          }
+        } else if (sc != kNoFast) {
           const float4 DE = s_DE[p], cs = s_cs[p];
           const float2 mm2 = s_mm[p];
           const ff E_i = {DE.z, DE.w}, ch = {cs.x, cs.y}, sh = {cs.z, cs.w}, mm = {mm2.x, mm2.y};
@@ -468,17 +504,24 @@ __global__ void __launch_bounds__(kNT, 5) event_pairs_bwd_kernel(BArgs A) {
           out[2] += ffm::lc_to_double(dphi, eoff_s);
           out[3] += ffm::lc_to_double(dm, kUnscaled);
         }
-        st4<double, LG>(A.grad, pbeg + p, V4<double>{out[0], out[1], out[2], out[3]});
+        if constexpr (!FIX) st4<double, LG>(A.grad, pbeg + p, V4<double>{out[0], out[1], out[2], out[3]});
       }
       __syncthreads();  // before the next sub-batch overwrites the staged particles
       sb = sbe;
     }
+    if constexpr (!FIX) {  // list the tile for the FIX launch if any thread met an FP64 path
+      if (__syncthreads_or(fix) && threadIdx.x == 0) {
+        const unsigned long long q = atomicAdd(A.fix_count, 1ull);  // < n_tiles: one per tile
+        if (GVX_IN_BOUNDS(q, n_tiles, A.status)) A.fix_tiles[q] = tile;
+      }
+      fix = false;
+    }
   }
 }
 
-template <int LP, int LS, int LG>
-cudaError_t launch_l(const BArgs &A, cudaStream_t s) {
-  constexpr auto k = event_pairs_bwd_kernel<LP, LS, LG>;
+template <int LP, int LS, int LG, bool FIX>
+cudaError_t launch_one(const BArgs &A, cudaStream_t s) {
+  constexpr auto k = event_pairs_bwd_kernel<LP, LS, LG, FIX>;
   cudaError_t err =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
   if (err != cudaSuccess) return err;
@@ -488,11 +531,26 @@ cudaError_t launch_l(const BArgs &A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The list count zeroed, the staged launch, then the FIX launch (which has nothing to do unless
+// the first listed tiles).
+template <int LP, int LS, int LG>
+cudaError_t launch_l(const BArgs &A, cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(A.fix_count, 0, sizeof(unsigned long long), s);
+  if (err != cudaSuccess) return err;
+  err = launch_one<LP, LS, LG, false>(A, s);
+  if (err != cudaSuccess) return err;
+  return launch_one<LP, LS, LG, true>(A, s);
+}
+
 }  // namespace
+
+size_t event_pairs_bwd_workspace(int64_t n_events) {
+  return kWsList + (size_t)((n_events + kTE - 1) / kTE) * sizeof(int64_t);
+}
 
 cudaError_t launch_event_pairs_bwd(const Lv &p, const int64_t *off, const int64_t *pair_off,
                                    int64_t n_events, int64_t n_particles, const double *gpm,
-                                   int64_t n_pairs, const Lv *gsum, const LvOut &grad,
+                                   int64_t n_pairs, const Lv *gsum, const LvOut &grad, void *ws,
                                    cudaStream_t s) {
   BArgs A;
   A.p = p;
@@ -506,6 +564,8 @@ cudaError_t launch_event_pairs_bwd(const Lv &p, const int64_t *off, const int64_
   A.gsum = gsum ? *gsum : Lv{{nullptr, nullptr, nullptr, nullptr}, GVX_SOA};
   A.grad = grad;
   A.status = device_status_word();
+  A.fix_count = (unsigned long long *)ws;
+  A.fix_tiles = (int64_t *)((char *)ws + kWsList);
   const int lp = p.layout, ls = A.gsum.layout, lg = grad.layout;
   if (lp == GVX_SOA) {
     if (ls == GVX_SOA) return lg == GVX_SOA ? launch_l<GVX_SOA, GVX_SOA, GVX_SOA>(A, s)

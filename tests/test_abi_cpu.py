@@ -88,6 +88,15 @@ def test_jagged_validation(lib):
     assert lib.gvx_event_pair_masses(*args(1000, 64, 4096, ws_need - 8)) == 7
     assert lib.gvx_event_pair_masses(*args(1000, 64, None, ws_need)) == 7
     assert lib.gvx_event_pair_masses(*args(1000, 64, 4100, ws_need)) == 5
+    # the adjoint: 256 bytes of header, then one int64 per tile of 14 events
+    wb = lib.gvx_event_pair_masses_bwd_workspace(1000)
+    assert wb == 256 + 8 * ((1000 + 13) // 14)
+    assert lib.gvx_event_pair_masses_bwd_workspace(0) == 0
+    bargs = lambda n_ev, ws, wsb: (r(p), 64, 128, n_ev, 100, 4096, 50, None, r(p), ws, wsb, None)
+    assert lib.gvx_event_pair_masses_bwd(*bargs(1000, None, wb)) == 7
+    assert lib.gvx_event_pair_masses_bwd(*bargs(1000, 4096, wb - 8)) == 7
+    assert lib.gvx_event_pair_masses_bwd(*bargs(1000, 4104, wb)) == 5
+    assert lib.gvx_event_pair_masses_bwd(*bargs(0, None, 0)) == 0  # nothing to do
     assert lib.gvx_event_pair_masses_set_shape(1000, 99) == 11
     n = lib.gvx_event_pair_masses_num_shapes()
     assert n >= 2

@@ -81,6 +81,11 @@ def _inputs(seed, n_events, extra_sizes=(0, 1, 2, 3, 65, 130)):
     p[7::31, 3] = 0.0
     gpm = syn.upstream(g, _n_pairs(off))
     gsum = syn.upstream(g, (len(counts), 4))
+    # upstream values outside the float-float ranges (FP64 pair and event-sum paths)
+    gpm[::211] *= 1e-30
+    gpm[1::307] *= 1e7
+    gsum[3::50, :] *= 1e-100
+    gsum[4::50, 2] *= 1e120
     return p, off, gpm, gsum
 
 
@@ -169,10 +174,12 @@ def test_event_pairs_bwd_rejects_mismatched_pair_offsets():
     lv = lambda t: ctypes.byref(gvx._lv(t, _lib.AOS, 4))
     tp, toff, tbad, tg = dev(p), torch.as_tensor(off).cuda(), torch.as_tensor(bad).cuda(), \
         torch.as_tensor(gpm).cuda()
+    ws_bytes = lib.gvx_event_pair_masses_bwd_workspace(len(off) - 1)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     st = lib.gvx_event_pair_masses_bwd(lv(tp), ctypes.c_void_p(toff.data_ptr()),
                                        ctypes.c_void_p(tbad.data_ptr()), len(off) - 1, len(p),
                                        ctypes.c_void_p(tg.data_ptr()), len(gpm), None, lv(grad),
-                                       gvx._stream())
+                                       ctypes.c_void_p(ws.data_ptr()), ws_bytes, gvx._stream())
     assert st == 0
     assert gvx.device_status() == 6
     g = grad.cpu().numpy()
@@ -181,5 +188,14 @@ def test_event_pairs_bwd_rejects_mismatched_pair_offsets():
     # an empty batch launches nothing and succeeds
     st = lib.gvx_event_pair_masses_bwd(lv(tp), ctypes.c_void_p(toff.data_ptr()),
                                        ctypes.c_void_p(tbad.data_ptr()), 0, 0, None, 0, None,
-                                       lv(grad), gvx._stream())
+                                       lv(grad), None, 0, gvx._stream())
     assert st == 0 and gvx.device_status() == 0
+    # a missing, short or misaligned workspace is refused before any launch
+    args = (lv(tp), ctypes.c_void_p(toff.data_ptr()), ctypes.c_void_p(toff.data_ptr()),
+            len(off) - 1, len(p), ctypes.c_void_p(tg.data_ptr()), len(gpm), None, lv(grad))
+    assert lib.gvx_event_pair_masses_bwd(*args, None, ws_bytes, gvx._stream()) == 7
+    assert lib.gvx_event_pair_masses_bwd(*args, ctypes.c_void_p(ws.data_ptr()), ws_bytes - 8,
+                                         gvx._stream()) == 7
+    assert lib.gvx_event_pair_masses_bwd(*args, ctypes.c_void_p(ws.data_ptr() + 8), ws_bytes,
+                                         gvx._stream()) == 5
+    assert gvx.device_status() == 0
